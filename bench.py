@@ -1,0 +1,467 @@
+"""Benchmark of the FP64 iterative-stencil library on one GB300 (or N replicas).
+
+One "step" is one full sweep of the headline workload: the 3D 7-point heat
+stencil (u' = u + 0.1*(sum of the 6 face neighbours - 6u), periodic) on a
+512^3 grid for T = 1000 time steps, starting from a uniform [0,1) field plus
+the sine mode k = (3,5,7).  The metric is the paper's Eq. 5: cell updates per
+second (N_x N_y N_z T / time), in GStencil/s.  The other workloads (2D 9-point
+box 16384^2, 3D 27-point box 384^3, 2D 5-point heat 256^2, the 96-grid batched
+form and the adjoint of the 256^3 variable-coefficient sweep) are reported
+under "forms", each with its own rate and roofline fraction.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank advances its own replica (weak scaling); rank 0
+prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "GStencil/s FP64 and roofline fraction at 1 GB300; batched/adjoint vs plain sweep"
+HEADLINE = dict(name="heat3d-7pt", shape=(512, 512, 512), T=1000, alpha=0.1, boundary=1,
+                sine=(3, 5, 7))
+# algorithmic FP64 flops per cell update: K-tap weighted sum = K multiplies
+# and K-1 adds; variable-coefficient step after hoisting the step-invariant
+# face coefficients = 7 products and 6 sums; adjoint step = the transposed
+# update (13) plus 3 faces x (2 differences, 1 product, 1 sum) = 25.
+FLOPS = {"heat3d-7pt": 13, "box2d-9pt": 17, "box3d-27pt": 53, "heat2d-5pt": 9,
+         "varcoef-7pt": 13, "adjoint-7pt": 13 + 25}
+NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
+
+
+# ------------------------------------------------------------------ helpers
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd.insert(1, f"--id={self.uuid}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(ngpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank
+
+
+def barrier_max(world, value):
+    """Barrier, then the max of `value` over ranks."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cuda_time(fn, stream):
+    """Milliseconds of fn() on `stream`, CUDA events on that stream."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2303_08365_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(cs, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == workload:
+            if parts[3] == cur:
+                return float(parts[2])
+    return None
+
+
+def roofline(name, cells, T, ms, launches, peak_tflops, kernel):
+    flops = FLOPS[name] * cells * T
+    achieved = flops / (ms * 1e-3) / 1e12
+    per_launch = FLOPS[name] * cells * T / max(launches, 1)
+    return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tflops, 4),
+            "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+            "traffic": recorded_traffic(kernel, name),
+            "algorithmic_flops_per_launch": per_launch,
+            "algorithmic_bytes_per_launch": 16 * cells * T / max(launches, 1),
+            "peak_source": "FP64 DFMA microbenchmark measured in this run (x2 flop/FMA); "
+                           f"nominal {NOMINAL_FP64_TFLOPS:.3f} TFLOP/s"}
+
+
+# ------------------------------------------------------------ our workloads
+
+def headline(st, steps, warmup, world, stream):
+    import torch
+    shape, T = HEADLINE["shape"], HEADLINE["T"]
+    u0 = synth.uniform(synth.SEED_HEAT3D, shape) + synth.sine_mode(shape, HEADLINE["sine"])
+    grid = torch.from_numpy(u0).cuda()
+    plan = st.Plan(shape, 1, synth.heat_weights(3, HEADLINE["alpha"]), st.PERIODIC)
+    tb, variant = plan.get_tuning()
+    for _ in range(warmup):
+        plan.run(grid, T, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(0).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    l0 = st.stencil_launch_count()
+    ms = cuda_time(lambda: [plan.run(grid, T, stream=stream) for _ in range(steps)], stream)
+    launches = st.stencil_launch_count() - l0
+    clocks = sampler.stop()
+    ms = barrier_max(world, ms)
+    # end to end through the host-buffer entry point (pinned memory), 1 step
+    host = torch.from_numpy(u0).pin_memory()
+    h2d = host.numel() * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan.run_host(host, T, stream=stream)
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    e2e_ms = barrier_max(world, e2e_ms)
+    plan.close()
+    del grid
+    torch.cuda.empty_cache()
+    return dict(ms=ms / steps, launches=launches, clocks=clocks, e2e_ms=e2e_ms, h2d=h2d, d2h=h2d,
+                Tb=tb, variant=st.stencil_variant_name(variant), u0=u0)
+
+
+def time_plan(st, plan, grid, T, reps, stream, warm=1):
+    for _ in range(warm):
+        plan.run(grid, T, stream=stream)
+    l0 = st.stencil_launch_count()
+    ms = cuda_time(lambda: [plan.run(grid, T, stream=stream) for _ in range(reps)], stream)
+    return ms / reps, (st.stencil_launch_count() - l0) // reps
+
+
+def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, reps=2):
+    import torch
+    grid = torch.from_numpy(u0).cuda()
+    plan = st.Plan(shape, radius, weights, boundary)
+    ms, launches = time_plan(st, plan, grid, T, reps, stream)
+    cells = int(np.prod(shape))
+    tb, v = plan.get_tuning()
+    plan.close()
+    del grid
+    torch.cuda.empty_cache()
+    return {"workload": f"{name} {'x'.join(map(str, shape))} T={T} "
+                        f"{'periodic' if boundary else 'dirichlet0'}",
+            "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
+            "Tb": tb, "variant": st.stencil_variant_name(v), "launches": launches,
+            "roofline": roofline(name, cells, T, ms, launches, peak, "sweep")}
+
+
+def form_batched(st, stream, peak):
+    import torch
+    items = synth.batch_items(synth.SEED_BATCH)
+    grids0 = [synth.uniform(synth.SEED_BATCH + 1000 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
+    dev = [torch.from_numpy(g).cuda() for g in grids0]
+    alphas = [a for _, _, a, _ in items]
+    steps = [T for *_, T in items]
+    updates = sum(ny * nx * T for ny, nx, _, T in items)
+    b = st.Batch(dev, alphas, steps)
+    b.run(stream)
+    assert b.status() == 0
+    l0 = st.stencil_launch_count()
+    reps = 3
+    ms = cuda_time(lambda: [b.run(stream) for _ in range(reps)], stream) / reps
+    launches = (st.stencil_launch_count() - l0) // reps
+    assert b.status() == 0
+    b.close()
+    # the plain single-grid sweep over the same grids, one after another
+    plans = [st.Plan((ny, nx), 1, synth.heat_weights(2, a), st.DIRICHLET_ZERO) for ny, nx, a, _ in items]
+
+    def plain():
+        for p, d, T in zip(plans, dev, steps):
+            p.run(d, T, stream=stream)
+    plain()
+    ms_plain = cuda_time(plain, stream)
+    for p in plans:
+        p.close()
+    del dev
+    torch.cuda.empty_cache()
+    rate = updates / (ms * 1e-3) / 1e9
+    return {"workload": f"batched 96 x heat2d-5pt, sides log-uniform [128,4096], T in [50,500], "
+                        f"{updates:.3e} updates",
+            "gstencil_per_s": round(rate, 3), "ms": round(ms, 3), "launches": launches,
+            "plain_sweep_ms": round(ms_plain, 3),
+            "plain_sweep_gstencil_per_s": round(updates / (ms_plain * 1e-3) / 1e9, 3),
+            "speedup_vs_plain": round(ms_plain / ms, 3),
+            "roofline": roofline("heat2d-5pt", updates, 1, ms, max(launches, 1), peak, "batched")}
+
+
+def form_adjoint(st, stream, peak):
+    import torch
+    shape, T, ck = (256, 256, 256), 1000, 32
+    seed = synth.SEED_ADJOINT
+    u0 = torch.from_numpy(synth.uniform(seed, shape)).cuda()
+    kappa_h = synth.lognormal(seed + 1, shape, 0.5)
+    kappa = torch.from_numpy(kappa_h).cuda()
+    target = torch.from_numpy(synth.normal(seed + 2, shape)).cuda()
+    dt = 0.1 / float(kappa_h.max())
+    plan = st.Plan.varcoef(shape, st.PERIODIC)
+    cells = int(np.prod(shape))
+    plan.adjoint(u0, kappa, dt, target, T, ckpt_every=ck, stream=stream)  # warm-up
+    l0 = st.stencil_launch_count()
+    ms = cuda_time(lambda: plan.adjoint(u0, kappa, dt, target, T, ckpt_every=ck, stream=stream), stream)
+    launches = st.stencil_launch_count() - l0
+    grid = u0.clone()
+    plan.run(grid, T, kappa, dt, stream=stream)
+    ms_fwd = cuda_time(lambda: plan.run(grid, T, kappa, dt, stream=stream), stream)
+    plan.close()
+    del u0, kappa, target, grid
+    torch.cuda.empty_cache()
+    return {"workload": "adjoint varcoef-7pt 256^3 T=1000 periodic, checkpoints every 32",
+            "ms": round(ms, 3), "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3),
+            "forward_ms": round(ms_fwd, 3),
+            "forward_gstencil_per_s": round(cells * T / (ms_fwd * 1e-3) / 1e9, 3),
+            "ratio_vs_forward": round(ms / ms_fwd, 3), "launches": launches,
+            "roofline": roofline("adjoint-7pt", cells, T, ms, launches, peak, "adjoint"),
+            "forward_roofline": roofline("varcoef-7pt", cells, T, ms_fwd, T, peak, "varcoef")}
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def cpu_baseline(u0, budget_s=12.0):
+    """The oracle as it stands, on all host cores, on a bounded number of
+    steps of the headline grid; GStencil/s."""
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    w = synth.heat_weights(3, HEADLINE["alpha"])
+    t0 = time.perf_counter()
+    oracle.run(u0, w, 1, 1, 1, nthreads=cores)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.run(u0, w, 1, 1, steps, nthreads=cores)
+    el = time.perf_counter() - t0
+    cells = u0.size
+    return {"value": round(cells * steps / el / 1e9, 5), "unit": "GStencil/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{HEADLINE['name']} 512^3 periodic, {steps} of the 1000 steps "
+                      f"({el:.1f} s), plain C loop nest, OpenMP over rows"}
+
+
+# ------------------------------------------------------------------ main
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.lib()
+    shape = HEADLINE["shape"]
+    u0 = synth.uniform(synth.SEED_HEAT3D, shape) + synth.sine_mode(shape, HEADLINE["sine"])
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    w = synth.heat_weights(3, HEADLINE["alpha"])
+    sample_steps = 2
+    for _ in range(args.warmup):
+        oracle.run(u0, w, 1, 1, 1, nthreads=cores)
+    times = []
+    u = u0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        u = oracle.run(u, w, 1, 1, sample_steps, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    el = sum(times)
+    cells = u0.size
+    value = cells * sample_steps * args.steps / el / 1e9
+    line = {"metric": METRIC, "value": round(value, 5), "unit": "GStencil/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "heat3d-7pt 512^3 periodic (each step: 2 of the 1000 time steps)",
+                       "global_batch": 1, "seq_len": HEADLINE["T"], "parallelism": "none (host cores)",
+                       "l2_flush": "input 1 GiB > L2"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "GStencil/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{sample_steps} time steps of the 512^3 grid per step"},
+            "e2e": {"value": round(value, 5), "unit": "GStencil/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", default="all", help="all | none | comma list of "
+                    "box2d,box3d,heat2d,batched,adjoint")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2303_08365_gb300 as st
+    st.lib()
+    world, rank = dist_setup(args.gpus)
+    stream = torch.cuda.current_stream()
+    peak_dfma = st.stencil_fp64_peak(300.0)
+    peak_tflops = 2 * peak_dfma / 1e12
+
+    h = headline(st, args.steps, args.warmup, world, stream)
+    shape, T = HEADLINE["shape"], HEADLINE["T"]
+    cells = int(np.prod(shape))
+    per_rank = cells * T / (h["ms"] * 1e-3) / 1e9
+    value = per_rank * world
+    e2e_value = cells * T / (h["e2e_ms"] * 1e-3) / 1e9 * world
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "GStencil/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(h["ms"], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "heat3d-7pt 512^3 T=1000 periodic, u0 = U[0,1) + sin mode (3,5,7)",
+                   "global_batch": world, "seq_len": T,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "Tb": h["Tb"], "variant": h["variant"],
+                   "l2_flush": "none needed: each launch streams 2 GiB > 129 MB L2"},
+        "roofline": roofline("heat3d-7pt", cells, T, h["ms"], h["launches"] // args.steps,
+                             peak_tflops, "sweep"),
+        "fp64_peak_tflops_measured": round(peak_tflops, 4),
+        "e2e": {"value": round(e2e_value, 4), "unit": "GStencil/s",
+                "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"]},
+        "gpu_launches": int(h["launches"]),
+        "clocks": h["clocks"],
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(h["u0"])
+    forms = {}
+    want = set(["box2d", "box3d", "heat2d", "batched", "adjoint"]) if args.forms == "all" else \
+        set() if args.forms == "none" else set(args.forms.split(","))
+    if rank == 0:
+        if "heat2d" in want:
+            shp = (256, 256)
+            forms["heat2d"] = form_const(st, "heat2d-5pt", shp, 1, synth.heat_weights(2, 0.1), 0, 100,
+                                         synth.uniform(synth.SEED_HEAT2D, shp), stream, peak_tflops,
+                                         reps=20)
+        if "box2d" in want:
+            shp = (16384, 16384)
+            forms["box2d"] = form_const(st, "box2d-9pt", shp, 1, synth.box_weights(2, 1.0 / 9.0), 1, 1000,
+                                        synth.uniform(synth.SEED_BOX2D, shp), stream, peak_tflops)
+        if "box3d" in want:
+            shp = (384, 384, 384)
+            forms["box3d"] = form_const(st, "box3d-27pt", shp, 1, synth.box_weights(3, seed=synth.SEED_BOX3D),
+                                        0, 500, synth.normal(synth.SEED_BOX3D, shp), stream, peak_tflops)
+        if "batched" in want:
+            forms["batched"] = form_batched(st, stream, peak_tflops)
+        if "adjoint" in want:
+            forms["adjoint"] = form_adjoint(st, stream, peak_tflops)
+        line["forms"] = forms
+        print(json.dumps(line))
+    barrier(world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

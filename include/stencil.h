@@ -1,0 +1,185 @@
+/*
+ * stencil.h -- C ABI of the GB300 (sm_103a) FP64 iterative-stencil library.
+ *
+ * The operation (paper Sec. 2.1, Listing 1 "Heat-2D Stencil", Eq. 3): every
+ * point of a d-dimensional grid is replaced, once per time step, by a weighted
+ * sum of itself and its neighbours at the previous step,
+ *
+ *     u^{t+1}(x) = sum_{o in [-r, r]^d} w_o * u~^t(x + o),
+ *
+ * where u~ is u extended by the boundary rule.  The update order inside a step
+ * is free (Sec. 1, first key observation), which is what makes the library's
+ * spatial and temporal tiling legal.  Arithmetic is IEEE binary64 throughout.
+ *
+ * Conventions for every entry point:
+ *   - dims are listed slowest axis first; the last axis is contiguous in
+ *     memory (row-major, C order).  ndim is 1, 2 or 3.
+ *   - weights is a dense (2r+1)^ndim array of doubles in the same axis order;
+ *     entry k along an axis is offset k - r.  A zero entry is not a tap.
+ *     The update is a correlation: u'(x) = sum_o w_o u(x+o).
+ *   - boundary: STENCIL_DIRICHLET_ZERO updates every cell and reads 0 for a
+ *     neighbour outside the grid; STENCIL_PERIODIC wraps indices.
+ *   - d_* pointers are device memory owned by the caller (for example torch
+ *     tensors): contiguous FP64, at least 8-byte aligned.  h_* pointers are host
+ *     memory owned by the caller.  The library owns plans, their ping-pong and
+ *     checkpoint buffers and their tuning records; scratch is allocated on the
+ *     first call that needs it and freed by stencil_destroy.
+ *   - cuda_stream is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are asynchronous on that stream unless stated otherwise.
+ *   - Every call returns a stencil_status.  On failure, stencil_last_error()
+ *     returns a message for the calling thread.  A plan is not thread-safe.
+ */
+#ifndef GB300_STENCIL_H
+#define GB300_STENCIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stencil_plan_s* stencil_plan;   /* opaque, library-owned */
+typedef struct stencil_batch_s* stencil_batch; /* opaque, library-owned */
+
+typedef enum {
+  STENCIL_DIRICHLET_ZERO = 0,
+  STENCIL_PERIODIC = 1
+} stencil_boundary;
+
+typedef enum {
+  STENCIL_OK = 0,
+  STENCIL_ERR_ARG = -1,          /* invalid argument (nothing was launched) */
+  STENCIL_ERR_UNSUPPORTED = -2,  /* valid but not supported by this build */
+  STENCIL_ERR_OOM = -3,          /* device or host allocation failed */
+  STENCIL_ERR_CUDA = -4,         /* a CUDA runtime or driver call failed */
+  STENCIL_ERR_TIMEOUT = -5       /* a bounded device-side wait gave up */
+} stencil_status;
+
+/* ------------------------------------------------------------------ plans */
+
+/* Creates a plan for the constant-weight stencil of Sec. 2.1 / Listing 1.
+ * ndim in {1,2,3}; dims[ndim] >= 1; radius in {1, 2}; weights as above
+ * (copied, host memory); boundary a stencil_boundary.  *out receives the
+ * plan.  Errors: STENCIL_ERR_ARG for a bad shape, radius, boundary or a
+ * non-finite weight; STENCIL_ERR_UNSUPPORTED if the grid needs more than
+ * 2^31 cells along one axis.  No device memory is allocated here. */
+int stencil_create(int ndim, const int64_t* dims, int radius, const double* weights,
+                   int boundary, stencil_plan* out);
+
+/* Creates a plan for the variable-coefficient diffusion step (an explicit
+ * step of du/dt = div(kappa grad u), the heat equation of Eq. 1 with a
+ * per-cell diffusivity):
+ *   u'_i = u_i + dt * sum_{faces n} 0.5*(kappa_i + kappa_n) * (u_n - u_i)
+ * over the 2*ndim face neighbours.  Periodic wraps; Dirichlet zero uses
+ * u_n = 0 and the face coefficient kappa_i outside the grid.  ndim in {2,3}. */
+int stencil_create_varcoef(int ndim, const int64_t* dims, int boundary, stencil_plan* out);
+
+/* Frees the plan and everything it owns (synchronises the device first). */
+void stencil_destroy(stencil_plan p);
+
+/* ------------------------------------------------------------------ sweeps */
+
+/* Advances d_grid (device, dims of the plan, in place) by T >= 0 steps.
+ * Constant-weight plans ignore d_kappa and dt.  Variable-coefficient plans
+ * need d_kappa (device, same shape) and dt > 0.  The library alternates
+ * between d_grid and a plan-owned buffer and leaves the result in d_grid.
+ * The fused step count Tb and kernel variant come from stencil_set_tuning,
+ * the autotuner record, or a default (see stencil_autotune). */
+int stencil_run(stencil_plan p, double* d_grid, int64_t T, const double* d_kappa, double dt,
+                void* cuda_stream);
+
+/* The same sweep on a HOST buffer: copies h_grid to a plan-owned device
+ * buffer, runs T steps, copies the result back into h_grid and waits for the
+ * stream.  Pinned host memory makes the copies asynchronous DMA. */
+int stencil_run_host(stencil_plan p, double* h_grid, int64_t T, const double* h_kappa,
+                     double dt, void* cuda_stream);
+
+/* Loss and gradients of the variable-coefficient sweep (the adjoint, or
+ * transposed stencil swept backward in time):
+ *   u^0 = d_u0, u^{t+1} = A(kappa) u^t, L = 0.5 * sum_i (u^T_i - target_i)^2,
+ *   lambda^T = u^T - target, lambda^t = A^T lambda^{t+1},
+ *   dL/du0 = lambda^0,
+ *   dL/dkappa_i = -(dt/2) sum_t sum_{faces n} (lambda^{t+1}_i - lambda^{t+1}_n)(u^t_i - u^t_n)
+ *   (ghost faces under Dirichlet: -dt sum_t lambda^{t+1}_i u^t_i per face),
+ * with dt held constant.  The forward states are checkpointed every
+ * ckpt_every steps (0 = about sqrt(T)) and recomputed one segment at a time
+ * in reverse, so device memory grows with sqrt(T), not T.
+ * d_grad_u0 and d_grad_kappa (device, caller-owned, same shape) are
+ * overwritten; *h_loss (host) receives L and the call waits for the stream. */
+int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,
+                    const double* d_target, int64_t T, int ckpt_every, double* d_grad_u0,
+                    double* d_grad_kappa, double* h_loss, void* cuda_stream);
+
+/* ----------------------------------------------------------- batched form */
+
+/* One independent 2D heat grid of a batch: ny x nx cells (row-major, device,
+ * in place), Eq. 3 weights (1-4*alpha at the centre, alpha at the four
+ * neighbours), T >= 0 steps. */
+typedef struct {
+  int64_t ny, nx;
+  double alpha;
+  int64_t T;
+  double* d_grid;
+} stencil_batch_item;
+
+/* Builds a batch plan: packs the items' tiles into one persistent kernel's
+ * device work list, allocates the per-item ping-pong buffers and per-tile
+ * step counters, and captures the whole advance (every item by its own T)
+ * as one CUDA graph on first run.  items is copied.  All items share the
+ * boundary rule. */
+int stencil_batch_create(const stencil_batch_item* items, int n, int boundary,
+                         stencil_batch* out);
+
+/* Advances every item of the batch by its own T, in place, by replaying the
+ * captured graph on cuda_stream.  Device-side waits are bounded; if one
+ * gives up, the batch records STENCIL_ERR_TIMEOUT, which stencil_batch_status
+ * and the next stencil_batch_run return. */
+int stencil_batch_run(stencil_batch b, void* cuda_stream);
+
+/* Waits for the batch's last run and returns its device status word. */
+int stencil_batch_status(stencil_batch b);
+
+void stencil_batch_destroy(stencil_batch b);
+
+/* Convenience: create, run once, wait, destroy. */
+int stencil_run_batched(const stencil_batch_item* items, int n, int boundary,
+                        void* cuda_stream);
+
+/* ------------------------------------------------------------- tuning */
+
+/* Fixes the fused step count Tb (1, 2, 4 or 8) and kernel variant (0 = let
+ * the library choose; see stencil_variant_name) for later runs of p.
+ * Tb = 0 returns the plan to the tuned / default choice. */
+int stencil_set_tuning(stencil_plan p, int Tb, int variant);
+
+/* Reports the Tb and variant the next stencil_run of p will use. */
+int stencil_get_tuning(stencil_plan p, int* Tb, int* variant);
+
+/* Times the candidate (Tb, variant) pairs on d_grid (device, contents are
+ * destroyed) for probe_steps steps each, after a warm-up, and keeps the
+ * fastest for p.  Synchronous.  *best_gstencils (may be NULL) receives its
+ * rate in 1e9 cell updates per second. */
+int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* cuda_stream,
+                     double* best_gstencils);
+
+/* Name of a kernel variant id ("" for an unknown id). */
+const char* stencil_variant_name(int variant);
+
+/* ---------------------------------------------------------- diagnostics */
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* stencil_last_error(void);
+
+/* Number of kernels this library has launched in this process (all plans,
+ * all streams), for launch accounting in benchmarks. */
+int64_t stencil_launch_count(void);
+
+/* FP64 fused multiply-add throughput of the current device, measured with a
+ * kernel of independent DFMA chains on every SM for about `millis` ms.
+ * *dfma_per_s receives DFMA instructions per second (2 flops each). */
+int stencil_fp64_peak(double millis, double* dfma_per_s, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_STENCIL_H */

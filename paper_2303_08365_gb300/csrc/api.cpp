@@ -1,0 +1,699 @@
+// api.cpp -- the C ABI of include/stencil.h: argument checks, plans, buffer
+// ownership, kernel selection and the host loops over time steps.
+#include "../../include/stencil.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace gbst {
+std::atomic<int64_t> g_launches{0};
+int batched_blocks_per_sm();
+}  // namespace gbst
+
+using namespace gbst;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  int code = (e == cudaErrorMemoryAllocation) ? STENCIL_ERR_OOM : STENCIL_ERR_CUDA;
+  return fail(code, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define CUDA_TRY(call, what)                  \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+// Pads a shape to three axes; rejects axes beyond the kernels' 32-bit indexing.
+int make_geom(int ndim, const int64_t* dims, Geom& g) {
+  if (ndim < 1 || ndim > 3) return fail(STENCIL_ERR_ARG, "ndim must be 1, 2 or 3 (got %d)", ndim);
+  if (!dims) return fail(STENCIL_ERR_ARG, "dims is NULL");
+  int64_t n[3] = {1, 1, 1};
+  for (int d = 0; d < ndim; ++d) {
+    if (dims[d] < 1) return fail(STENCIL_ERR_ARG, "dims[%d] = %lld < 1", d, (long long)dims[d]);
+    if (dims[d] > (int64_t)1 << 30)
+      return fail(STENCIL_ERR_UNSUPPORTED, "dims[%d] = %lld exceeds 2^30", d, (long long)dims[d]);
+    n[3 - ndim + d] = dims[d];
+  }
+  if (n[0] > 65535) return fail(STENCIL_ERR_UNSUPPORTED, "slowest axis of a 3D grid exceeds 65535");
+  if (n[1] > 65535 * 8) return fail(STENCIL_ERR_UNSUPPORTED, "second-slowest axis exceeds 524280");
+  g.nz = (int)n[0];
+  g.ny = (int)n[1];
+  g.nx = (int)n[2];
+  return STENCIL_OK;
+}
+
+}  // namespace
+
+struct stencil_plan_s {
+  int ndim = 0;
+  Geom g{1, 1, 1};
+  int radius = 0;
+  int boundary = 0;
+  bool varcoef = false;
+  Shape shape = Shape::kStar;
+  HostTaps taps;
+  // library-owned device buffers
+  double* d_tmp = nullptr;     // ping-pong partner of the caller's grid
+  double* d_stage = nullptr;   // host-entry staging (grid, then kappa)
+  double* d_coef = nullptr;    // varcoef: c0, cx, cy, cz (4 x cells)
+  double* d_adj = nullptr;     // adjoint scratch
+  size_t adj_cells = 0;
+  // tuning
+  int user_Tb = 0, user_variant = 0;
+  int tuned_Tb = 0, tuned_variant = 0;
+
+  int64_t cells() const { return g.cells(); }
+};
+
+struct stencil_batch_s {
+  int n = 0;
+  int boundary = 0;
+  std::vector<stencil_batch_item> items;
+  BatchItemDev* d_items = nullptr;
+  BatchTile* d_tiles = nullptr;
+  double* d_partner = nullptr;
+  unsigned int* d_ctl = nullptr;  // [0] arrivals, [1] generation, [2] status
+  int ntiles = 0;
+  int max_T = 0;
+  int blocks = 0;
+  int64_t updates = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool use_graph = true;
+};
+
+namespace {
+
+// Builds the compile-time tap list of the plan's shape class: every offset of
+// the class in lexicographic order (slowest axis first), with its weight
+// (possibly zero) from the dense array.
+void build_taps(stencil_plan_s* p, const double* w) {
+  const int r = p->radius, side = 2 * r + 1, nd = p->ndim;
+  int64_t total = 1;
+  for (int d = 0; d < nd; ++d) total *= side;
+  p->taps.n = 0;
+  for (int64_t k = 0; k < total; ++k) {
+    int off[3] = {0, 0, 0};
+    int64_t rem = k;
+    for (int d = nd - 1; d >= 0; --d) {
+      off[3 - nd + d] = (int)(rem % side) - r;
+      rem /= side;
+    }
+    int nonzero_axes = (off[0] != 0) + (off[1] != 0) + (off[2] != 0);
+    if (p->shape == Shape::kStar && nonzero_axes > 1) continue;
+    int i = p->taps.n++;
+    p->taps.w[i] = w[k];
+    p->taps.dz[i] = (int8_t)off[0];
+    p->taps.dy[i] = (int8_t)off[1];
+    p->taps.dx[i] = (int8_t)off[2];
+  }
+}
+
+int ensure(double** buf, size_t count, const char* what) {
+  if (*buf) return STENCIL_OK;
+  cudaError_t e = cudaMalloc((void**)buf, count * sizeof(double));
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    return cuda_fail(e, what);
+  }
+  return STENCIL_OK;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Resolved (Tb, variant) for the next run of a constant-weight plan.
+void choose(const stencil_plan_s* p, int& Tb, int& variant) {
+  if (p->user_Tb > 0 || p->user_variant > 0) {
+    Tb = p->user_Tb > 0 ? p->user_Tb : 1;
+    variant = p->user_variant > 0 ? p->user_variant : kVariantDirect;
+    return;
+  }
+  if (p->tuned_Tb > 0) {
+    Tb = p->tuned_Tb;
+    variant = p->tuned_variant;
+    return;
+  }
+  Tb = 1;
+  variant = kVariantDirect;
+}
+
+int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
+  int Tb, variant;
+  choose(p, Tb, variant);
+  if (variant != kVariantDirect || Tb != 1)
+    return fail(STENCIL_ERR_UNSUPPORTED, "variant %d with Tb=%d is not available", variant, Tb);
+  int rc = ensure(&p->d_tmp, (size_t)p->cells(), "allocating the ping-pong buffer");
+  if (rc) return rc;
+  double* a = d_grid;
+  double* b = p->d_tmp;
+  for (int64_t t = 0; t < T; ++t) {
+    cudaError_t e = launch_direct(p->ndim, p->radius, p->shape, p->boundary, p->g, p->taps, a, b, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the direct sweep");
+    std::swap(a, b);
+  }
+  if (a != d_grid)
+    CUDA_TRY(cudaMemcpyAsync(d_grid, a, (size_t)p->cells() * sizeof(double),
+                             cudaMemcpyDeviceToDevice, s),
+             "copying the result back");
+  return STENCIL_OK;
+}
+
+VarcoefBufs coef_bufs(stencil_plan_s* p) {
+  size_t n = (size_t)p->cells();
+  return VarcoefBufs{p->d_coef, p->d_coef + n, p->d_coef + 2 * n, p->d_coef + 3 * n};
+}
+
+int run_varcoef(stencil_plan_s* p, double* d_grid, int64_t T, const double* d_kappa, double dt,
+                cudaStream_t s) {
+  if (!d_kappa) return fail(STENCIL_ERR_ARG, "variable-coefficient plan needs d_kappa");
+  if (!(dt > 0.0) || !is_finite(dt)) return fail(STENCIL_ERR_ARG, "dt must be finite and > 0");
+  int rc = ensure(&p->d_tmp, (size_t)p->cells(), "allocating the ping-pong buffer");
+  if (rc) return rc;
+  rc = ensure(&p->d_coef, 4 * (size_t)p->cells(), "allocating the coefficient arrays");
+  if (rc) return rc;
+  VarcoefBufs cb = coef_bufs(p);
+  cudaError_t e = launch_varcoef_prepare(p->ndim, p->boundary, p->g, d_kappa, dt, cb, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the coefficient preparation");
+  double* a = d_grid;
+  double* b = p->d_tmp;
+  for (int64_t t = 0; t < T; ++t) {
+    e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, a, b, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the variable-coefficient step");
+    std::swap(a, b);
+  }
+  if (a != d_grid)
+    CUDA_TRY(cudaMemcpyAsync(d_grid, a, (size_t)p->cells() * sizeof(double),
+                             cudaMemcpyDeviceToDevice, s),
+             "copying the result back");
+  return STENCIL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* stencil_last_error(void) { return g_err.c_str(); }
+
+int64_t stencil_launch_count(void) { return g_launches.load(); }
+
+const char* stencil_variant_name(int v) {
+  switch (v) {
+    case kVariantAuto: return "auto";
+    case kVariantDirect: return "direct";
+    case kVariantStream: return "stream";
+    case kVariantTemporal: return "temporal";
+    case kVariantPersistent: return "persistent";
+    default: return "";
+  }
+}
+
+int stencil_create(int ndim, const int64_t* dims, int radius, const double* weights, int boundary,
+                   stencil_plan* out) {
+  g_err.clear();
+  if (!out) return fail(STENCIL_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  Geom g;
+  int rc = make_geom(ndim, dims, g);
+  if (rc) return rc;
+  if (radius < 1 || radius > 2) return fail(STENCIL_ERR_ARG, "radius must be 1 or 2 (got %d)", radius);
+  if (boundary != STENCIL_DIRICHLET_ZERO && boundary != STENCIL_PERIODIC)
+    return fail(STENCIL_ERR_ARG, "unknown boundary %d", boundary);
+  if (!weights) return fail(STENCIL_ERR_ARG, "weights is NULL");
+  const int side = 2 * radius + 1;
+  int64_t total = 1;
+  for (int d = 0; d < ndim; ++d) total *= side;
+  bool star = true;
+  for (int64_t k = 0; k < total; ++k) {
+    if (!is_finite(weights[k])) return fail(STENCIL_ERR_ARG, "weights[%lld] is not finite", (long long)k);
+    if (weights[k] == 0.0) continue;
+    int64_t rem = k;
+    int nz_axes = 0;
+    for (int d = ndim - 1; d >= 0; --d) {
+      nz_axes += (rem % side) != radius;
+      rem /= side;
+    }
+    if (nz_axes > 1) star = false;
+  }
+  auto* p = new (std::nothrow) stencil_plan_s();
+  if (!p) return fail(STENCIL_ERR_OOM, "allocating the plan");
+  p->ndim = ndim;
+  p->g = g;
+  p->radius = radius;
+  p->boundary = boundary;
+  p->shape = (star || ndim == 1) ? Shape::kStar : Shape::kBox;
+  build_taps(p, weights);
+  *out = p;
+  return STENCIL_OK;
+}
+
+int stencil_create_varcoef(int ndim, const int64_t* dims, int boundary, stencil_plan* out) {
+  g_err.clear();
+  if (!out) return fail(STENCIL_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (ndim < 2 || ndim > 3) return fail(STENCIL_ERR_ARG, "variable-coefficient plans are 2D or 3D");
+  Geom g;
+  int rc = make_geom(ndim, dims, g);
+  if (rc) return rc;
+  if (boundary != STENCIL_DIRICHLET_ZERO && boundary != STENCIL_PERIODIC)
+    return fail(STENCIL_ERR_ARG, "unknown boundary %d", boundary);
+  auto* p = new (std::nothrow) stencil_plan_s();
+  if (!p) return fail(STENCIL_ERR_OOM, "allocating the plan");
+  p->ndim = ndim;
+  p->g = g;
+  p->radius = 1;
+  p->boundary = boundary;
+  p->varcoef = true;
+  *out = p;
+  return STENCIL_OK;
+}
+
+void stencil_destroy(stencil_plan p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  cudaFree(p->d_tmp);
+  cudaFree(p->d_stage);
+  cudaFree(p->d_coef);
+  cudaFree(p->d_adj);
+  delete p;
+}
+
+int stencil_run(stencil_plan p, double* d_grid, int64_t T, const double* d_kappa, double dt,
+                void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
+  if (!d_grid) return fail(STENCIL_ERR_ARG, "d_grid is NULL");
+  if (((uintptr_t)d_grid & 7) != 0) return fail(STENCIL_ERR_ARG, "d_grid is not 8-byte aligned");
+  if (T < 0) return fail(STENCIL_ERR_ARG, "T must be >= 0");
+  if (T == 0) return STENCIL_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (p->varcoef) return run_varcoef(p, d_grid, T, d_kappa, dt, s);
+  return run_const(p, d_grid, T, s);
+}
+
+int stencil_run_host(stencil_plan p, double* h_grid, int64_t T, const double* h_kappa, double dt,
+                     void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
+  if (!h_grid) return fail(STENCIL_ERR_ARG, "h_grid is NULL");
+  if (p->varcoef && !h_kappa) return fail(STENCIL_ERR_ARG, "variable-coefficient plan needs h_kappa");
+  if (T < 0) return fail(STENCIL_ERR_ARG, "T must be >= 0");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t n = (size_t)p->cells();
+  int rc = ensure(&p->d_stage, p->varcoef ? 2 * n : n, "allocating the staging buffer");
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(p->d_stage, h_grid, n * sizeof(double), cudaMemcpyHostToDevice, s),
+           "copying the grid to the device");
+  if (p->varcoef)
+    CUDA_TRY(cudaMemcpyAsync(p->d_stage + n, h_kappa, n * sizeof(double), cudaMemcpyHostToDevice, s),
+             "copying kappa to the device");
+  rc = stencil_run(p, p->d_stage, T, p->varcoef ? p->d_stage + n : nullptr, dt, cuda_stream);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(h_grid, p->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, s),
+           "copying the result to the host");
+  CUDA_TRY(cudaStreamSynchronize(s), "waiting for the host-buffer sweep");
+  return STENCIL_OK;
+}
+
+int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,
+                    const double* d_target, int64_t T, int ckpt_every, double* d_grad_u0,
+                    double* d_grad_kappa, double* h_loss, void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
+  if (!p->varcoef) return fail(STENCIL_ERR_ARG, "stencil_adjoint needs a variable-coefficient plan");
+  if (!d_u0 || !d_kappa || !d_target || !d_grad_u0 || !d_grad_kappa || !h_loss)
+    return fail(STENCIL_ERR_ARG, "NULL buffer");
+  if (!(dt > 0.0) || !is_finite(dt)) return fail(STENCIL_ERR_ARG, "dt must be finite and > 0");
+  if (T < 0) return fail(STENCIL_ERR_ARG, "T must be >= 0");
+  if (ckpt_every < 0) return fail(STENCIL_ERR_ARG, "ckpt_every must be >= 0");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t n = (size_t)p->cells();
+  int64_t c = ckpt_every > 0 ? ckpt_every : std::max<int64_t>(1, (int64_t)llround(std::sqrt((double)T)));
+  if (T > 0 && c > T) c = T;
+  const int64_t nck = T / c + 1;        // u at t = 0, c, 2c, ... (<= T)
+  const int64_t nseg_states = c;        // u^{t0} .. u^{t0+c-1} of one segment
+  const int nblocks = 4 * sm_count();
+  // scratch: checkpoints, segment states, 2 lambda, 4 gradient accumulators,
+  // the running state pair and the loss partials
+  const size_t need = n * (size_t)(nck + nseg_states + 2 + 4 + 2) + (size_t)nblocks + 8;
+  if (p->d_adj && p->adj_cells < need) {
+    cudaFree(p->d_adj);
+    p->d_adj = nullptr;
+  }
+  int rc = ensure(&p->d_adj, need, "allocating the adjoint scratch (checkpoints)");
+  if (rc) return rc;
+  p->adj_cells = need;
+  rc = ensure(&p->d_coef, 4 * n, "allocating the coefficient arrays");
+  if (rc) return rc;
+  double* ck = p->d_adj;
+  double* seg = ck + n * nck;
+  double* lam = seg + n * nseg_states;
+  double* lam2 = lam + n;
+  double* gx = lam2 + n;
+  double* gy = gx + n;
+  double* gz = gy + n;
+  double* gg = gz + n;
+  double* cur = gg + n;
+  double* nxt = cur + n;
+  double* partials = nxt + n;
+  double* d_loss = partials + nblocks;
+  VarcoefBufs cb = coef_bufs(p);
+  cudaError_t e = launch_varcoef_prepare(p->ndim, p->boundary, p->g, d_kappa, dt, cb, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the coefficient preparation");
+  const size_t bytes = n * sizeof(double);
+  // forward sweep, keeping u at every multiple of c
+  CUDA_TRY(cudaMemcpyAsync(ck, d_u0, bytes, cudaMemcpyDeviceToDevice, s), "copying u0");
+  const double* src = ck;
+  for (int64_t t = 0; t < T; ++t) {
+    double* dst = ((t + 1) % c == 0) ? ck + n * (size_t)((t + 1) / c) : (src == cur ? nxt : cur);
+    e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, src, dst, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the forward step");
+    src = dst;
+  }
+  // loss and lambda^T = u^T - target
+  e = launch_loss_residual((int64_t)n, src, d_target, lam, partials, nblocks, d_loss, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the loss reduction");
+  CUDA_TRY(cudaMemsetAsync(gx, 0, 4 * bytes, s), "clearing the gradient accumulators");
+  // reverse sweep, one segment [t0, t1) at a time
+  const int64_t nseg = (T + c - 1) / c;
+  for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+    const int64_t t0 = sg * c, t1 = std::min(T, t0 + c);
+    const double* base = ck + n * (size_t)sg;
+    // seg[k] = u^{t0+k} for k = 1 .. t1-t0-1 (k = 0 is the checkpoint itself)
+    for (int64_t t = t0 + 1; t < t1; ++t) {
+      const double* from = (t == t0 + 1) ? base : seg + n * (size_t)(t - t0 - 1);
+      e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, from, seg + n * (size_t)(t - t0), s);
+      if (e != cudaSuccess) return cuda_fail(e, "launching the segment recompute");
+    }
+    for (int64_t t = t1 - 1; t >= t0; --t) {
+      const double* ut = (t == t0) ? base : seg + n * (size_t)(t - t0);
+      e = launch_adjoint_step(p->ndim, p->boundary, p->g, cb, lam, ut, lam2, gx, gy, gz, gg, s);
+      if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint step");
+      std::swap(lam, lam2);
+    }
+  }
+  e = launch_adjoint_finalize(p->ndim, p->boundary, p->g, dt, gx, gy, gz, gg, d_grad_kappa, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the gradient finalisation");
+  CUDA_TRY(cudaMemcpyAsync(d_grad_u0, lam, bytes, cudaMemcpyDeviceToDevice, s), "copying dL/du0");
+  CUDA_TRY(cudaMemcpyAsync(h_loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s),
+           "copying the loss");
+  CUDA_TRY(cudaStreamSynchronize(s), "waiting for the adjoint");
+  return STENCIL_OK;
+}
+
+int stencil_set_tuning(stencil_plan p, int Tb, int variant) {
+  g_err.clear();
+  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
+  if (Tb != 0 && Tb != 1 && Tb != 2 && Tb != 4 && Tb != 8)
+    return fail(STENCIL_ERR_ARG, "Tb must be 0, 1, 2, 4 or 8 (got %d)", Tb);
+  if (variant < 0 || variant >= kVariantCount)
+    return fail(STENCIL_ERR_ARG, "unknown variant %d", variant);
+  p->user_Tb = Tb;
+  p->user_variant = Tb == 0 ? 0 : variant;
+  return STENCIL_OK;
+}
+
+int stencil_get_tuning(stencil_plan p, int* Tb, int* variant) {
+  g_err.clear();
+  if (!p || !Tb || !variant) return fail(STENCIL_ERR_ARG, "NULL argument");
+  choose(p, *Tb, *variant);
+  return STENCIL_OK;
+}
+
+int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* cuda_stream,
+                     double* best_gstencils) {
+  g_err.clear();
+  if (!p || !d_grid) return fail(STENCIL_ERR_ARG, "NULL argument");
+  if (p->varcoef) return fail(STENCIL_ERR_UNSUPPORTED, "autotune covers constant-weight plans");
+  if (probe_steps < 1) return fail(STENCIL_ERR_ARG, "probe_steps must be >= 1");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  struct Cand { int Tb, variant; };
+  std::vector<Cand> cands = {{1, kVariantDirect}};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0), "creating an event");
+  CUDA_TRY(cudaEventCreate(&e1), "creating an event");
+  const int saved_Tb = p->user_Tb, saved_v = p->user_variant;
+  double best = -1.0;
+  Cand best_c = cands[0];
+  for (const Cand& c : cands) {
+    p->user_Tb = c.Tb;
+    p->user_variant = c.variant;
+    int rc = stencil_run(p, d_grid, c.Tb, nullptr, 0.0, cuda_stream);  // warm-up
+    if (rc == STENCIL_ERR_UNSUPPORTED) continue;
+    if (rc) break;
+    cudaEventRecord(e0, s);
+    rc = stencil_run(p, d_grid, probe_steps, nullptr, 0.0, cuda_stream);
+    cudaEventRecord(e1, s);
+    if (rc) break;
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    double rate = (double)p->cells() * (double)probe_steps / (ms * 1e-3) / 1e9;
+    if (rate > best) {
+      best = rate;
+      best_c = c;
+    }
+  }
+  p->user_Tb = saved_Tb;
+  p->user_variant = saved_v;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return g_err.empty() ? fail(STENCIL_ERR_CUDA, "no candidate ran") : STENCIL_ERR_CUDA;
+  p->tuned_Tb = best_c.Tb;
+  p->tuned_variant = best_c.variant;
+  if (best_gstencils) *best_gstencils = best;
+  return STENCIL_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+int stencil_batch_create(const stencil_batch_item* items, int n, int boundary, stencil_batch* out) {
+  g_err.clear();
+  if (!out) return fail(STENCIL_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!items || n < 1) return fail(STENCIL_ERR_ARG, "a batch needs at least one item");
+  if (boundary != STENCIL_DIRICHLET_ZERO && boundary != STENCIL_PERIODIC)
+    return fail(STENCIL_ERR_ARG, "unknown boundary %d", boundary);
+  int64_t total_cells = 0;
+  for (int i = 0; i < n; ++i) {
+    const stencil_batch_item& it = items[i];
+    if (it.ny < 1 || it.nx < 1 || it.ny > (1 << 30) || it.nx > (1 << 30))
+      return fail(STENCIL_ERR_ARG, "item %d: bad shape %lld x %lld", i, (long long)it.ny, (long long)it.nx);
+    if (it.T < 0 || it.T > (1 << 30)) return fail(STENCIL_ERR_ARG, "item %d: bad T", i);
+    if (!is_finite(it.alpha)) return fail(STENCIL_ERR_ARG, "item %d: alpha not finite", i);
+    if (!it.d_grid || ((uintptr_t)it.d_grid & 7)) return fail(STENCIL_ERR_ARG, "item %d: bad d_grid", i);
+    total_cells += it.ny * it.nx;
+  }
+  auto* b = new (std::nothrow) stencil_batch_s();
+  if (!b) return fail(STENCIL_ERR_OOM, "allocating the batch");
+  b->n = n;
+  b->boundary = boundary;
+  b->items.assign(items, items + n);
+  auto cleanup = [&](int rc) {
+    stencil_batch_destroy(b);
+    return rc;
+  };
+  cudaError_t e = cudaMalloc(&b->d_partner, (size_t)total_cells * sizeof(double));
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "allocating the partner buffers"));
+  std::vector<BatchItemDev> hi(n);
+  int64_t off = 0;
+  for (int i = 0; i < n; ++i) {
+    const stencil_batch_item& it = items[i];
+    hi[i].a = it.d_grid;
+    hi[i].b = b->d_partner + off;
+    hi[i].ny = (int)it.ny;
+    hi[i].nx = (int)it.nx;
+    hi[i].T = (int)it.T;
+    hi[i].c0 = 1.0 - 4.0 * it.alpha;  // Eq. 3 centre weight
+    hi[i].c1 = it.alpha;
+    off += it.ny * it.nx;
+    b->max_T = std::max(b->max_T, (int)it.T);
+    b->updates += it.ny * it.nx * it.T;
+  }
+  // tiles, sorted by the item's T (largest first; ties by item, then position)
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return items[a].T > items[c].T; });
+  std::vector<BatchTile> tiles;
+  const int th = batched_tile_h(), tw = batched_tile_w();
+  for (int i : order) {
+    if (items[i].T == 0) continue;
+    for (int y0 = 0; y0 < (int)items[i].ny; y0 += th)
+      for (int x0 = 0; x0 < (int)items[i].nx; x0 += tw) tiles.push_back(BatchTile{i, y0, x0});
+  }
+  // items with T = 0 still need no work; keep at least one entry for the launch
+  b->ntiles = (int)tiles.size();
+  e = cudaMalloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "allocating the item table"));
+  e = cudaMemcpy(b->d_items, hi.data(), sizeof(BatchItemDev) * (size_t)n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "copying the item table"));
+  e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(1, tiles.size()));
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "allocating the tile list"));
+  if (!tiles.empty()) {
+    e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "copying the tile list"));
+  }
+  e = cudaMalloc(&b->d_ctl, 4 * sizeof(unsigned int));
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "allocating the barrier words"));
+  e = cudaMemset(b->d_ctl, 0, 4 * sizeof(unsigned int));
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "clearing the barrier words"));
+  int per_sm = batched_blocks_per_sm();
+  if (per_sm < 1) return cleanup(fail(STENCIL_ERR_CUDA, "the batched kernel does not fit on an SM"));
+  b->blocks = sm_count() * std::min(per_sm, 4);
+  *out = b;
+  return STENCIL_OK;
+}
+
+static int batch_enqueue(stencil_batch b, cudaStream_t s) {
+  BatchLaunch L;
+  L.items = b->d_items;
+  L.tiles = b->d_tiles;
+  L.ntiles = b->ntiles;
+  L.max_T = b->max_T;
+  L.boundary = b->boundary;
+  L.barrier = b->d_ctl;
+  L.status = (int*)(b->d_ctl + 2);
+  L.spin_limit = 2000000000LL;  // 2 s of wall time per barrier wait
+  CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing the barrier words");
+  cudaError_t e = launch_batched(L, b->blocks, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the batched kernel");
+  return STENCIL_OK;
+}
+
+int stencil_batch_run(stencil_batch b, void* cuda_stream) {
+  g_err.clear();
+  if (!b) return fail(STENCIL_ERR_ARG, "batch is NULL");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  b->last_stream = s;
+  if (b->use_graph && !b->exec) {
+    if (!b->capture_stream)
+      CUDA_TRY(cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking), "creating a stream");
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      int rc = batch_enqueue(b, b->capture_stream);
+      ok = cudaStreamEndCapture(b->capture_stream, &graph) == cudaSuccess && rc == STENCIL_OK;
+      g_launches.fetch_sub(1, std::memory_order_relaxed);  // captured, not launched
+    }
+    if (ok) ok = cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      cudaGetLastError();
+      b->exec = nullptr;
+      b->use_graph = false;  // fall back to direct cooperative launches
+    }
+  }
+  if (b->exec) {
+    CUDA_TRY(cudaGraphLaunch(b->exec, s), "launching the batch graph");
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return STENCIL_OK;
+  }
+  return batch_enqueue(b, s);
+}
+
+int stencil_batch_status(stencil_batch b) {
+  g_err.clear();
+  if (!b) return fail(STENCIL_ERR_ARG, "batch is NULL");
+  CUDA_TRY(cudaStreamSynchronize(b->last_stream), "waiting for the batch");
+  int st = 0;
+  CUDA_TRY(cudaMemcpy(&st, b->d_ctl + 2, sizeof(int), cudaMemcpyDeviceToHost), "reading the status");
+  if (st != 0) return fail(st, "the batched kernel reported status %d (a bounded wait gave up)", st);
+  return STENCIL_OK;
+}
+
+void stencil_batch_destroy(stencil_batch b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  cudaFree(b->d_items);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_partner);
+  cudaFree(b->d_ctl);
+  delete b;
+}
+
+int stencil_run_batched(const stencil_batch_item* items, int n, int boundary, void* cuda_stream) {
+  stencil_batch b = nullptr;
+  int rc = stencil_batch_create(items, n, boundary, &b);
+  if (rc) return rc;
+  rc = stencil_batch_run(b, cuda_stream);
+  if (rc == STENCIL_OK) rc = stencil_batch_status(b);
+  std::string keep = g_err;
+  stencil_batch_destroy(b);
+  g_err = keep;
+  return rc;
+}
+
+// ------------------------------------------------------------ measurement
+
+int stencil_fp64_peak(double millis, double* dfma_per_s, void* cuda_stream) {
+  g_err.clear();
+  if (!dfma_per_s || !(millis > 0)) return fail(STENCIL_ERR_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int blocks = sm_count() * 8;
+  double* out = nullptr;
+  CUDA_TRY(cudaMalloc(&out, sizeof(double) * blocks * 256), "allocating the output");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int iters = 256;
+  double rate = 0.0;
+  int rc = STENCIL_OK;
+  for (int round = 0; round < 8; ++round) {
+    cudaEventRecord(e0, s);
+    cudaError_t e = launch_fp64_peak(blocks, iters, out, s);
+    cudaEventRecord(e1, s);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "launching the peak kernel"); break; }
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    rate = (double)blocks * 256.0 * 8.0 * iters / (ms * 1e-3);
+    if (ms >= millis * 0.5) break;
+    double scale = millis / std::max(0.01, (double)ms);
+    iters = (int)std::min(1.0e8, iters * scale);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (rc) return rc;
+  *dfma_per_s = rate;
+  return STENCIL_OK;
+}
+
+}  // extern "C"

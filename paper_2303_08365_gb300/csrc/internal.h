@@ -1,0 +1,130 @@
+// internal.h -- declarations shared by the C-ABI layer (api.cpp) and the
+// CUDA translation units of the stencil library.  Not installed, not part of
+// the ABI; nothing here is visible outside libstencil_gb300.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+namespace gbst {
+
+// Largest tap set: a radius-2 box in 3D.
+constexpr int kMaxTaps = 125;
+
+// Stencil classes the plan recognises from the non-zero pattern of the
+// weights.  The class fixes the compile-time tap list of the kernels.
+enum class Shape : int {
+  kStar = 0,  // taps only on the axes through the centre (2*d*r + 1 taps)
+  kBox = 1,   // every offset in [-r, r]^d ((2r+1)^d taps)
+};
+
+// Boundary rule (same values as stencil_boundary).
+enum Boundary : int { kDirichlet = 0, kPeriodic = 1 };
+
+// Kernel variants selectable through stencil_set_tuning.  Ids are ABI-stable.
+enum Variant : int {
+  kVariantAuto = 0,
+  kVariantDirect = 1,     // one cell per thread per plane, taps from L1
+  kVariantStream = 2,     // slowest-axis streaming through a TMA-fed SMEM ring
+  kVariantTemporal = 3,   // Tb fused steps per HBM round trip (overlapped tiles)
+  kVariantPersistent = 4, // one persistent launch with a device-wide barrier per step
+  kVariantCount = 5
+};
+
+// Tap list for a launch, passed by value (kernel parameter space lives in the
+// constant bank, so the weights are constant-bank operands of the FMAs).
+template <int NT>
+struct TapList {
+  double w[NT];
+  int8_t dz[NT], dy[NT], dx[NT];
+};
+
+// Grid geometry padded to three axes (leading axes of length 1).
+struct Geom {
+  int nz, ny, nx;
+  int64_t cells() const { return (int64_t)nz * ny * nx; }
+};
+
+// Host-side description of the taps (any count up to kMaxTaps).
+struct HostTaps {
+  int n = 0;
+  double w[kMaxTaps];
+  int8_t dz[kMaxTaps], dy[kMaxTaps], dx[kMaxTaps];
+};
+
+// Launchers implemented in the .cu files.  Each returns a cudaError_t from
+// the launch (cudaSuccess when nothing failed) and enqueues on `stream`.
+cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const Geom& g,
+                          const HostTaps& taps, const double* src, double* dst,
+                          cudaStream_t stream);
+
+// Variable-coefficient diffusion: coefficient preparation, one forward step,
+// one fused adjoint step, gradient finalisation and the loss reduction.
+struct VarcoefBufs {
+  // per-cell coefficients: centre c0 = 1 - sum of face coefficients, and the
+  // coefficient of the +x, +y, +z face of each cell (dt * face diffusivity)
+  double* c0;
+  double* cx;
+  double* cy;
+  double* cz;
+};
+cudaError_t launch_varcoef_prepare(int ndim, int boundary, const Geom& g, const double* kappa,
+                                   double dt, VarcoefBufs b, cudaStream_t stream);
+cudaError_t launch_varcoef_step(int ndim, int boundary, const Geom& g, VarcoefBufs b,
+                                const double* src, double* dst, cudaStream_t stream);
+// lam_out = A^T lam_in, and for every +face f=(i,n): G_f += (u_n - u_i)(lam_i - lam_n)
+// (lam = lam_in = lambda^{t+1}, u = u^t); ghost faces: Gg_i -= k_i * u_i * lam_i
+// where k_i is the number of ghost faces of cell i (Dirichlet only).
+cudaError_t launch_adjoint_step(int ndim, int boundary, const Geom& g, VarcoefBufs b,
+                                const double* lam_in, const double* u, double* lam_out,
+                                double* gx, double* gy, double* gz, double* gg,
+                                cudaStream_t stream);
+// grad_kappa_i = (dt/2) * sum_{faces f of i} G_f + dt * Gg_i
+cudaError_t launch_adjoint_finalize(int ndim, int boundary, const Geom& g, double dt,
+                                    const double* gx, const double* gy, const double* gz,
+                                    const double* gg, double* grad_kappa, cudaStream_t stream);
+// lam = u - target, and block partial sums of 0.5*(u - target)^2 into partials
+// (nblocks entries); then a single-block pass sums the partials in order.
+cudaError_t launch_loss_residual(int64_t n, const double* u, const double* target, double* lam,
+                                 double* partials, int nblocks, double* loss_out,
+                                 cudaStream_t stream);
+
+// Batched persistent sweep over many 2D heat grids.
+struct BatchTile {
+  int item;     // index into the item table
+  int y0, x0;   // tile origin
+};
+struct BatchItemDev {
+  double* a;     // the caller's grid (time level parity 0)
+  double* b;     // library-owned partner buffer (parity 1)
+  int ny, nx;
+  int T;
+  double c0, c1; // Eq. 3 weights: 1 - 4*alpha and alpha
+};
+struct BatchLaunch {
+  const BatchItemDev* items;
+  const BatchTile* tiles;
+  int ntiles;
+  int max_T;
+  int boundary;
+  unsigned int* barrier;  // two words: arrival count, generation
+  int* status;            // 0 ok, else a stencil_status
+  long long spin_limit;   // bounded waits: iterations before giving up
+};
+cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, cudaStream_t stream);
+int batched_block_size();
+int batched_tile_h();
+int batched_tile_w();
+
+// FP64 peak microbenchmark: `iters` rounds of 8 independent DFMA chains in
+// blocks x 256 threads; out receives one double per thread.
+cudaError_t launch_fp64_peak(int blocks, int iters, double* out, cudaStream_t stream);
+
+// Launch accounting (every kernel launch of the library adds one).
+extern std::atomic<int64_t> g_launches;
+
+}  // namespace gbst

@@ -1,0 +1,85 @@
+"""GPU parity of the batched persistent sweep: every item equals the same
+grid advanced alone by stencil_run, bitwise (same tap order and FMA chain),
+and the oracle within 1e-12; uneven sizes, ragged tiles and T = 0 items."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import normwise_rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+DIRICHLET, PERIODIC = 0, 1
+
+
+@pytest.fixture(scope="module")
+def st():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2303_08365_gb300 import build
+    build.build()
+    import paper_2303_08365_gb300 as st
+    return st
+
+
+def single(st, u0, alpha, T, boundary):
+    import torch
+    g = torch.from_numpy(u0.copy()).cuda()
+    p = st.Plan(u0.shape, 1, synth.heat_weights(2, alpha), boundary)
+    p.run(g, T)
+    out = g.cpu().numpy()
+    p.close()
+    return out
+
+
+@pytest.mark.parametrize("boundary", [DIRICHLET, PERIODIC])
+def test_small_batch_matches_single_and_oracle(st, boundary):
+    import torch
+    items = [(37, 91, 0.11, 13), (128, 64, 0.2, 6), (5, 3, 0.05, 9), (200, 130, 0.24, 0),
+             (1, 1, 0.1, 4), (70, 250, 0.15, 21)]
+    grids = [synth.uniform(50 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
+    dev = [torch.from_numpy(g.copy()).cuda() for g in grids]
+    b = st.Batch(dev, [a for _, _, a, _ in items], [T for *_, T in items], boundary)
+    b.run()
+    assert b.status() == 0
+    for g0, d, (ny, nx, a, T) in zip(grids, dev, items):
+        got = d.cpu().numpy()
+        assert np.array_equal(got, single(st, g0, a, T, boundary))
+        ref = oracle.run(g0, synth.heat_weights(2, a), 1, boundary, T)
+        assert normwise_rel(got, ref) <= TOL
+    b.close()
+
+
+def test_replay_advances_again(st):
+    import torch
+    g0 = synth.uniform(9, (64, 80))
+    d = torch.from_numpy(g0.copy()).cuda()
+    b = st.Batch([d], [0.1], [7])
+    b.run()
+    b.run()
+    assert b.status() == 0
+    assert np.array_equal(d.cpu().numpy(), single(st, g0, 0.1, 14, DIRICHLET))
+    b.close()
+
+
+@pytest.mark.slow
+def test_full_96_item_batch(st):
+    """The 96-grid workload: every item bitwise equal to its single-grid run;
+    a few small items against the oracle."""
+    import torch
+    items = synth.batch_items(synth.SEED_BATCH)
+    grids = [synth.uniform(synth.SEED_BATCH + 1000 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
+    dev = [torch.from_numpy(g).cuda() for g in grids]
+    b = st.Batch(dev, [a for _, _, a, _ in items], [T for *_, T in items])
+    b.run()
+    assert b.status() == 0
+    order = sorted(range(len(items)), key=lambda i: items[i][0] * items[i][1])
+    for i in order[:4] + order[-2:]:
+        ny, nx, a, T = items[i]
+        assert np.array_equal(dev[i].cpu().numpy(), single(st, grids[i], a, T, DIRICHLET)), i
+    for i in order[:3]:
+        ny, nx, a, T = items[i]
+        ref = oracle.run(grids[i], synth.heat_weights(2, a), 1, DIRICHLET, T, nthreads=0)
+        assert normwise_rel(dev[i].cpu().numpy(), ref) <= TOL
+    b.close()

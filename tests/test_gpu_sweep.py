@@ -1,0 +1,216 @@
+"""GPU parity of the constant-weight sweep against the CPU oracle.
+
+Bar: normwise relative error max|g - o| / max|o| <= 1e-12 after T steps (the
+GPU fuses multiply-adds and orders the taps differently; every workload is a
+non-expansive map, so rounding does not grow beyond ~T ulp).  Small and
+ragged grids are compared element by element over the whole grid; the
+full-size workloads are compared on sampled windows computed from their
+light cones, and through closed forms at the full step count.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import normwise_rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+PERIODIC, DIRICHLET = 1, 0
+
+
+@pytest.fixture(scope="module")
+def st():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2303_08365_gb300 import build
+    build.build()
+    import paper_2303_08365_gb300 as st
+    return st
+
+
+def gpu_run(st, u0, w, radius, boundary, T, Tb=0, variant=0):
+    import torch
+    g = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+    p = st.Plan(u0.shape, radius, w, boundary)
+    if Tb:
+        p.set_tuning(Tb, variant)
+    p.run(g, T)
+    torch.cuda.synchronize()
+    out = g.cpu().numpy()
+    p.close()
+    return out
+
+
+def weights_for(kind, ndim, radius, seed):
+    side = 2 * radius + 1
+    if kind == "heat":
+        return synth.heat_weights(ndim, 0.1)
+    if kind == "box_eq":
+        return synth.box_weights(ndim, 1.0 / side ** ndim)
+    if kind == "box_rand":
+        v = synth.uniform(seed, (side,) * ndim)
+        return v / v.sum()
+    if kind == "star_rand":
+        w = np.zeros((side,) * ndim)
+        v = synth.uniform(seed, (2 * ndim * radius + 1,))
+        v /= v.sum()
+        c = (radius,) * ndim
+        w[c] = v[0]
+        k = 1
+        for d in range(ndim):
+            for o in range(-radius, radius + 1):
+                if o == 0:
+                    continue
+                idx = list(c)
+                idx[d] += o
+                w[tuple(idx)] = v[k]
+                k += 1
+        return w
+    raise ValueError(kind)
+
+
+SMALL = [
+    # shape, radius, boundary, kind, T
+    ((256, 256), 1, DIRICHLET, "heat", 100),      # the 256^2 heat workload, full size
+    ((37, 53), 1, DIRICHLET, "heat", 17),
+    ((37, 53), 1, PERIODIC, "box_eq", 9),
+    ((61, 45), 1, PERIODIC, "box_rand", 12),
+    ((29, 33), 2, DIRICHLET, "box_rand", 7),
+    ((29, 33), 2, PERIODIC, "star_rand", 8),
+    ((13, 17, 19), 1, PERIODIC, "heat", 11),
+    ((13, 17, 19), 1, DIRICHLET, "box_rand", 10),
+    ((9, 40, 70), 1, DIRICHLET, "star_rand", 6),
+    ((11, 12, 13), 2, PERIODIC, "star_rand", 5),
+    ((7, 9, 11), 2, DIRICHLET, "box_rand", 4),
+    ((1000,), 1, PERIODIC, "star_rand", 25),
+    ((777,), 2, DIRICHLET, "star_rand", 13),
+    ((1, 1), 1, PERIODIC, "heat", 3),
+    ((1, 7), 1, DIRICHLET, "heat", 4),
+    ((3, 2), 2, PERIODIC, "box_rand", 5),   # axes shorter than the radius
+    ((2, 1, 3), 1, PERIODIC, "box_rand", 4),
+]
+
+
+@pytest.mark.parametrize("shape,radius,boundary,kind,T", SMALL)
+def test_parity_whole_grid(st, shape, radius, boundary, kind, T):
+    ndim = len(shape)
+    w = weights_for(kind, ndim, radius, 100 + len(shape) + radius)
+    u0 = synth.uniform(7, shape) if kind != "box_rand" else synth.normal(7, shape)
+    ref = oracle.run(u0, w, radius, boundary, T, nthreads=0)
+    got = gpu_run(st, u0, w, radius, boundary, T)
+    assert normwise_rel(got, ref) <= TOL
+
+
+def test_zero_steps_is_identity(st):
+    u0 = synth.uniform(3, (20, 30))
+    got = gpu_run(st, u0, synth.heat_weights(2, 0.1), 1, DIRICHLET, 0)
+    assert np.array_equal(got, u0)
+
+
+def test_odd_and_even_step_counts_compose(st):
+    import torch
+    u0 = synth.uniform(4, (33, 65))
+    w = synth.heat_weights(2, 0.2)
+    g = torch.from_numpy(u0.copy()).cuda()
+    p = st.Plan(u0.shape, 1, w, DIRICHLET)
+    p.run(g, 3)
+    p.run(g, 4)
+    a = g.cpu().numpy()
+    g2 = torch.from_numpy(u0.copy()).cuda()
+    p.run(g2, 7)
+    assert np.array_equal(a, g2.cpu().numpy())
+
+
+def test_host_entry_matches_device_entry(st):
+    u0 = synth.uniform(5, (48, 40, 36))
+    w = synth.heat_weights(3, 0.1)
+    dev = gpu_run(st, u0, w, 1, PERIODIC, 9)
+    h = u0.copy()
+    p = st.Plan(u0.shape, 1, w, PERIODIC)
+    p.run_host(h, 9)
+    p.close()
+    assert np.array_equal(h, dev)
+
+
+# Full-size workloads: sampled windows from the light cone at a short step
+# count, in the launch configuration the benchmark times.
+FULL = [
+    ((512, 512, 512), 1, PERIODIC, "heat", 3, synth.SEED_HEAT3D),
+    ((16384, 16384), 1, PERIODIC, "box_eq", 3, synth.SEED_BOX2D),
+    ((384, 384, 384), 1, DIRICHLET, "box_rand", 3, synth.SEED_BOX3D),
+]
+
+
+def window_boxes(shape):
+    """Corner, edge and interior windows (ragged sizes)."""
+    boxes = []
+    for pos in ("lo", "mid", "hi"):
+        lo, hi = [], []
+        for n in shape:
+            w = 5 if len(shape) == 3 else 9
+            a = {"lo": 0, "mid": n // 2 - 3, "hi": n - w}[pos]
+            lo.append(a)
+            hi.append(a + w)
+        boxes.append((tuple(lo), tuple(hi)))
+    return boxes
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape,radius,boundary,kind,T,seed", FULL)
+def test_parity_full_size_windows(st, shape, radius, boundary, kind, T, seed):
+    import torch
+    ndim = len(shape)
+    w = weights_for(kind, ndim, radius, seed)
+    u0 = synth.normal(seed, shape) if kind == "box_rand" else synth.uniform(seed, shape)
+    g = torch.from_numpy(u0).cuda()
+    p = st.Plan(shape, radius, w, boundary)
+    p.run(g, T)
+    torch.cuda.synchronize()
+    for lo, hi in window_boxes(shape):
+        ref = oracle.run_window(u0, w, radius, boundary, T, lo, hi)
+        sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+        got = g[sl].cpu().numpy()
+        assert normwise_rel(got, ref) <= TOL, (lo, hi)
+    p.close()
+
+
+@pytest.mark.slow
+def test_full_size_512_cube_sine_mode_closed_form(st):
+    """512^3 periodic heat, T=1000: by linearity run(r + m) - run(r) = lam^T m
+    for the sine mode k=(3,5,7); the mean is conserved."""
+    import torch
+    shape = (512, 512, 512)
+    w = synth.heat_weights(3, 0.1)
+    T = 1000
+    lam = 1.0 - 0.4 * sum(math.sin(math.pi * k / 512) ** 2 for k in (3, 5, 7))
+    r = torch.from_numpy(synth.uniform(synth.SEED_HEAT3D, shape)).cuda()
+    m = torch.from_numpy(synth.sine_mode(shape, (3, 5, 7))).cuda()
+    a = r + m
+    b = r.clone()
+    p = st.Plan(shape, 1, w, PERIODIC)
+    mean0 = float(r.mean())
+    p.run(a, T)
+    p.run(b, T)
+    torch.cuda.synchronize()
+    d = (a - b) - (lam ** T) * m
+    assert float(d.abs().max()) <= TOL * float(a.abs().max())
+    assert abs(float(b.mean()) - mean0) <= 1e-12
+    assert float(b.min()) >= float(r.min()) - 1e-12 and float(b.max()) <= float(r.max()) + 1e-12
+    p.close()
+
+
+def test_launch_count_advances(st):
+    import torch
+    before = st.stencil_launch_count()
+    u0 = synth.uniform(1, (16, 16))
+    gpu_run(st, u0, synth.heat_weights(2, 0.1), 1, DIRICHLET, 5)
+    assert st.stencil_launch_count() >= before + 5
+    torch.cuda.synchronize()
+
+
+def test_fp64_peak_is_plausible(st):
+    r = st.stencil_fp64_peak(50.0)
+    assert 1e11 < r < 1e13
