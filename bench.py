@@ -384,6 +384,48 @@ def run_reference(args):
     return 0
 
 
+def run_case(args):
+    """One workload at a chosen size for profiling (not the benchmark line):
+    W warm-up runs and `steps` timed runs of T time steps each."""
+    import torch
+    import paper_2303_08365_gb300 as st
+    st.lib()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.size
+    name = args.case
+    if name in ("heat3d", "box3d"):
+        shape = (n, n, n)
+        w = synth.heat_weights(3, 0.1) if name == "heat3d" else synth.box_weights(3, seed=synth.SEED_BOX3D)
+        bnd = 1 if name == "heat3d" else 0
+    elif name in ("heat2d", "box2d"):
+        shape = (n, n)
+        w = synth.heat_weights(2, 0.1) if name == "heat2d" else synth.box_weights(2, 1.0 / 9.0)
+        bnd = 0 if name == "heat2d" else 1
+    elif name == "varcoef":
+        shape = (n, n, n)
+    else:
+        raise SystemExit(f"unknown case {name}")
+    grid = torch.from_numpy(synth.uniform(synth.SEED_HEAT3D, shape)).cuda()
+    if name == "varcoef":
+        kappa = torch.from_numpy(synth.lognormal(synth.SEED_ADJOINT + 1, shape)).cuda()
+        dt = 0.1 / float(kappa.max())
+        plan = st.Plan.varcoef(shape, st.PERIODIC)
+        fn = lambda: plan.run(grid, args.T, kappa, dt, stream=stream)
+    else:
+        plan = st.Plan(shape, 1, w, bnd)
+        if args.variant:
+            plan.set_tuning(args.Tb or 1, args.variant)
+        fn = lambda: plan.run(grid, args.T, stream=stream)
+    for _ in range(args.warmup):
+        fn()
+    ms = cuda_time(lambda: [fn() for _ in range(args.steps)], stream) / args.steps
+    cells = int(np.prod(shape))
+    print(json.dumps({"case": name, "shape": shape, "T": args.T, "tuning": plan.get_tuning(),
+                      "ms": round(ms, 4), "gstencil_per_s": round(cells * args.T / (ms * 1e-3) / 1e9, 3)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,7 +435,14 @@ def main():
     ap.add_argument("--forms", default="all", help="all | none | comma list of "
                     "box2d,box3d,heat2d,batched,adjoint")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, help="profiling mode: heat3d | box3d | heat2d | box2d | varcoef")
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--T", type=int, default=4)
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--Tb", type=int, default=0)
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -145,6 +145,11 @@ void stencil_batch_destroy(stencil_batch b);
 int stencil_run_batched(const stencil_batch_item* items, int n, int boundary,
                         void* cuda_stream);
 
+/* Waits for cuda_stream and returns the plan's device status word: STENCIL_OK,
+ * or STENCIL_ERR_TIMEOUT when a bounded device-side wait of one of the plan's
+ * kernels gave up since the last call (the word is then cleared). */
+int stencil_plan_status(stencil_plan p, void* cuda_stream);
+
 /* ------------------------------------------------------------- tuning */
 
 /* Fixes the fused step count Tb (1, 2, 4 or 8) and kernel variant (0 = let

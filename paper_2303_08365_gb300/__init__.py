@@ -61,6 +61,7 @@ SIGNATURES = [
     ("stencil_batch_status", ctypes.c_int, [_VP]),
     ("stencil_batch_destroy", None, [_VP]),
     ("stencil_run_batched", ctypes.c_int, [ctypes.POINTER(BatchItem), ctypes.c_int, ctypes.c_int, _VP]),
+    ("stencil_plan_status", ctypes.c_int, [_VP, _VP]),
     ("stencil_set_tuning", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("stencil_get_tuning", ctypes.c_int, [_VP, _IP, _IP]),
     ("stencil_autotune", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _DP]),
@@ -229,6 +230,11 @@ def stencil_run_batched(grids, alphas, steps, boundary=DIRICHLET_ZERO, stream=No
     _check(lib().stencil_run_batched(arr, len(arr), int(boundary), _stream(stream)))
 
 
+def stencil_plan_status(h, stream=None):
+    """Waits for the stream; returns the plan's device status (0 = OK)."""
+    return lib().stencil_plan_status(h, _stream(stream))
+
+
 def stencil_set_tuning(h, Tb, variant=0):
     _check(lib().stencil_set_tuning(h, int(Tb), int(variant)))
 
@@ -293,6 +299,9 @@ class Plan:
 
     def set_tuning(self, Tb, variant=0):
         stencil_set_tuning(self.handle, Tb, variant)
+
+    def status(self, stream=None):
+        return stencil_plan_status(self.handle, stream)
 
     def get_tuning(self):
         return stencil_get_tuning(self.handle)

@@ -14,10 +14,12 @@
 #include <vector>
 
 #include "internal.h"
+#include "taps.cuh"
 
 namespace gbst {
 std::atomic<int64_t> g_launches{0};
 int batched_blocks_per_sm();
+int set_error(int code, const char* msg);
 }  // namespace gbst
 
 using namespace gbst;
@@ -70,6 +72,12 @@ int make_geom(int ndim, const int64_t* dims, Geom& g) {
 
 }  // namespace
 
+// Lets other translation units report through stencil_last_error.
+int gbst::set_error(int code, const char* msg) {
+  g_err = msg ? msg : "";
+  return code;
+}
+
 struct stencil_plan_s {
   int ndim = 0;
   Geom g{1, 1, 1};
@@ -84,6 +92,11 @@ struct stencil_plan_s {
   double* d_coef = nullptr;    // varcoef: c0, cx, cy, cz (4 x cells)
   double* d_adj = nullptr;     // adjoint scratch
   size_t adj_cells = 0;
+  int* d_status = nullptr;     // device status word (bounded waits that gave up)
+  double* d_w = nullptr;       // weights in tap order, then kZeroSlots zeros
+  stencil_batch_s* persist = nullptr;  // one-item batch for the persistent 2D path
+  const double* persist_grid = nullptr;
+  int64_t persist_T = -1;
   // tuning
   int user_Tb = 0, user_variant = 0;
   int tuned_Tb = 0, tuned_variant = 0;
@@ -110,6 +123,9 @@ struct stencil_batch_s {
 };
 
 namespace {
+
+int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boundary);
+int batch_enqueue(stencil_batch_s* b, cudaStream_t s);
 
 // Builds the compile-time tap list of the plan's shape class: every offset of
 // the class in lexicographic order (slowest axis first), with its weight
@@ -157,11 +173,25 @@ int sm_count() {
   return n;
 }
 
+// The kernel a constant-weight plan uses when nothing was tuned or forced.
+int default_variant(const stencil_plan_s* p) {
+  if (p->ndim == 3 && p->radius == 1) return kVariantStream;
+  if (p->ndim == 2 && p->radius == 1) {
+    if (p->shape == Shape::kStar && p->cells() <= ((int64_t)1 << 20)) return kVariantPersistent;
+    return kVariantStream;
+  }
+  return kVariantDirect;
+}
+
+bool persistent_eligible(const stencil_plan_s* p) {
+  return p->ndim == 2 && p->radius == 1 && p->shape == Shape::kStar && p->taps.n == 5;
+}
+
 // Resolved (Tb, variant) for the next run of a constant-weight plan.
 void choose(const stencil_plan_s* p, int& Tb, int& variant) {
   if (p->user_Tb > 0 || p->user_variant > 0) {
     Tb = p->user_Tb > 0 ? p->user_Tb : 1;
-    variant = p->user_variant > 0 ? p->user_variant : kVariantDirect;
+    variant = p->user_variant > 0 ? p->user_variant : default_variant(p);
     return;
   }
   if (p->tuned_Tb > 0) {
@@ -170,21 +200,95 @@ void choose(const stencil_plan_s* p, int& Tb, int& variant) {
     return;
   }
   Tb = 1;
-  variant = kVariantDirect;
+  variant = default_variant(p);
+}
+
+// Uploads the plan's weights (and the zero slots) to the device once.
+int ensure_weights(stencil_plan_s* p) {
+  if (p->d_w) return STENCIL_OK;
+  std::vector<double> h(p->taps.n + kZeroSlots, 0.0);
+  for (int k = 0; k < p->taps.n; ++k) h[k] = p->taps.w[k];
+  CUDA_TRY(cudaMalloc(&p->d_w, h.size() * sizeof(double)), "allocating the weight array");
+  CUDA_TRY(cudaMemcpy(p->d_w, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice),
+           "copying the weights");
+  return STENCIL_OK;
+}
+
+int ensure_status(stencil_plan_s* p) {
+  if (p->d_status) return STENCIL_OK;
+  CUDA_TRY(cudaMalloc(&p->d_status, sizeof(int)), "allocating the status word");
+  CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "clearing the status word");
+  return STENCIL_OK;
 }
 
 int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   int Tb, variant;
   choose(p, Tb, variant);
-  if (variant != kVariantDirect || Tb != 1)
-    return fail(STENCIL_ERR_UNSUPPORTED, "variant %d with Tb=%d is not available", variant, Tb);
+  const bool forced = p->user_Tb > 0 || p->user_variant > 0;
   int rc = ensure(&p->d_tmp, (size_t)p->cells(), "allocating the ping-pong buffer");
   if (rc) return rc;
+  rc = ensure_status(p);
+  if (rc) return rc;
+  rc = ensure_weights(p);
+  if (rc) return rc;
+  const bool stream_ok = p->ndim == 3
+                             ? stream3d_eligible(p->ndim, p->radius, p->boundary, p->g, d_grid, p->d_tmp)
+                             : stream2d_eligible(p->ndim, p->radius, p->boundary, p->g, d_grid, p->d_tmp);
+  if (variant == kVariantStream && !stream_ok) {
+    if (forced)
+      return fail(STENCIL_ERR_UNSUPPORTED,
+                  "the streaming kernel needs a 2D or 3D radius-1 plan, even nx, 16-byte aligned "
+                  "buffers and, for periodic grids, nx %% 64 == 0 and ny %% 16 == 0");
+    variant = kVariantDirect;
+  }
+  if (variant == kVariantPersistent) {
+    if (!persistent_eligible(p) || T > (1 << 30)) {
+      if (forced)
+        return fail(STENCIL_ERR_UNSUPPORTED, "the persistent kernel covers 2D 5-point star plans");
+      variant = kVariantDirect;
+    } else {
+      if (!p->persist || p->persist_grid != d_grid || p->persist_T != T) {
+        if (p->persist) {
+          p->persist->d_partner = nullptr;
+          stencil_batch_destroy(p->persist);
+          p->persist = nullptr;
+        }
+        auto* b = new (std::nothrow) stencil_batch_s();
+        if (!b) return fail(STENCIL_ERR_OOM, "allocating the persistent plan");
+        BatchItemDev it;
+        it.a = d_grid;
+        it.b = p->d_tmp;
+        it.ny = p->g.ny;
+        it.nx = p->g.nx;
+        it.T = (int)T;
+        for (int k = 0; k < 5; ++k) it.w[k] = p->taps.w[k];
+        it.zero[0] = it.zero[1] = 0.0;
+        rc = batch_init(b, std::vector<BatchItemDev>{it}, p->boundary);
+        if (rc) {
+          stencil_batch_destroy(b);
+          return rc;
+        }
+        p->persist = b;
+        p->persist_grid = d_grid;
+        p->persist_T = T;
+      }
+      return batch_enqueue(p->persist, s);
+    }
+  }
+  const int sms = sm_count();
+  const bool equal_box = p->shape == Shape::kBox && taps_all_equal(p->taps);
   double* a = d_grid;
   double* b = p->d_tmp;
   for (int64_t t = 0; t < T; ++t) {
-    cudaError_t e = launch_direct(p->ndim, p->radius, p->shape, p->boundary, p->g, p->taps, a, b, s);
-    if (e != cudaSuccess) return cuda_fail(e, "launching the direct sweep");
+    cudaError_t e;
+    if (variant == kVariantStream && p->ndim == 3)
+      e = launch_stream3d(p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, p->d_status, sms, s);
+    else if (variant == kVariantStream)
+      e = launch_stream2d(p->shape, p->boundary, equal_box, p->g, p->taps, p->d_w, a, b, p->d_status,
+                          sms, s);
+    else
+      e = launch_direct(p->ndim, p->radius, p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the sweep");
     std::swap(a, b);
   }
   if (a != d_grid)
@@ -207,13 +311,15 @@ int run_varcoef(stencil_plan_s* p, double* d_grid, int64_t T, const double* d_ka
   if (rc) return rc;
   rc = ensure(&p->d_coef, 4 * (size_t)p->cells(), "allocating the coefficient arrays");
   if (rc) return rc;
+  rc = ensure_weights(p);
+  if (rc) return rc;
   VarcoefBufs cb = coef_bufs(p);
   cudaError_t e = launch_varcoef_prepare(p->ndim, p->boundary, p->g, d_kappa, dt, cb, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the coefficient preparation");
   double* a = d_grid;
   double* b = p->d_tmp;
   for (int64_t t = 0; t < T; ++t) {
-    e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, a, b, s);
+    e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, a, b, p->d_w, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the variable-coefficient step");
     std::swap(a, b);
   }
@@ -223,6 +329,64 @@ int run_varcoef(stencil_plan_s* p, double* d_grid, int64_t T, const double* d_ka
              "copying the result back");
   return STENCIL_OK;
 }
+
+// Fills a batch from device item descriptors (buffers and weights set):
+// the T-sorted tile list, the item table, the barrier words and the
+// cooperative grid size.
+int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boundary) {
+  const int n = (int)hi.size();
+  b->n = n;
+  b->boundary = boundary;
+  b->max_T = 0;
+  b->updates = 0;
+  for (const BatchItemDev& it : hi) {
+    b->max_T = std::max(b->max_T, it.T);
+    b->updates += (int64_t)it.ny * it.nx * it.T;
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return hi[a].T > hi[c].T; });
+  std::vector<BatchTile> tiles;
+  const int th = batched_tile_h(), tw = batched_tile_w();
+  for (int i : order) {
+    if (hi[i].T == 0) continue;
+    for (int y0 = 0; y0 < hi[i].ny; y0 += th)
+      for (int x0 = 0; x0 < hi[i].nx; x0 += tw) tiles.push_back(BatchTile{i, y0, x0});
+  }
+  b->ntiles = (int)tiles.size();
+  CUDA_TRY(cudaMalloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n), "allocating the item table");
+  CUDA_TRY(cudaMemcpy(b->d_items, hi.data(), sizeof(BatchItemDev) * (size_t)n, cudaMemcpyHostToDevice),
+           "copying the item table");
+  CUDA_TRY(cudaMalloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(1, tiles.size())),
+           "allocating the tile list");
+  if (!tiles.empty())
+    CUDA_TRY(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice),
+             "copying the tile list");
+  CUDA_TRY(cudaMalloc(&b->d_ctl, 4 * sizeof(unsigned int)), "allocating the barrier words");
+  CUDA_TRY(cudaMemset(b->d_ctl, 0, 4 * sizeof(unsigned int)), "clearing the barrier words");
+  const int per_sm = batched_blocks_per_sm();
+  if (per_sm < 1) return fail(STENCIL_ERR_CUDA, "the batched kernel does not fit on an SM");
+  b->blocks = sm_count() * std::min(per_sm, 4);
+  if (b->ntiles > 0 && b->ntiles < b->blocks) b->blocks = b->ntiles;
+  return STENCIL_OK;
+}
+
+int batch_enqueue(stencil_batch_s* b, cudaStream_t s) {
+  BatchLaunch L;
+  L.items = b->d_items;
+  L.tiles = b->d_tiles;
+  L.ntiles = b->ntiles;
+  L.max_T = b->max_T;
+  L.boundary = b->boundary;
+  L.barrier = b->d_ctl;
+  L.status = (int*)(b->d_ctl + 2);
+  L.spin_limit = 2000000000LL;  // 2 s of wall time per barrier wait
+  CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing the barrier words");
+  cudaError_t e = launch_batched(L, b->blocks, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the batched kernel");
+  return STENCIL_OK;
+}
+
 
 }  // namespace
 
@@ -310,6 +474,12 @@ void stencil_destroy(stencil_plan p) {
   cudaFree(p->d_stage);
   cudaFree(p->d_coef);
   cudaFree(p->d_adj);
+  cudaFree(p->d_status);
+  cudaFree(p->d_w);
+  if (p->persist) {
+    p->persist->d_partner = nullptr;  // the plan's own ping-pong buffer
+    stencil_batch_destroy(p->persist);
+  }
   delete p;
 }
 
@@ -380,6 +550,8 @@ int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, d
   p->adj_cells = need;
   rc = ensure(&p->d_coef, 4 * n, "allocating the coefficient arrays");
   if (rc) return rc;
+  rc = ensure_weights(p);
+  if (rc) return rc;
   double* ck = p->d_adj;
   double* seg = ck + n * nck;
   double* lam = seg + n * nseg_states;
@@ -401,7 +573,7 @@ int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, d
   const double* src = ck;
   for (int64_t t = 0; t < T; ++t) {
     double* dst = ((t + 1) % c == 0) ? ck + n * (size_t)((t + 1) / c) : (src == cur ? nxt : cur);
-    e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, src, dst, s);
+    e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, src, dst, p->d_w, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the forward step");
     src = dst;
   }
@@ -417,12 +589,12 @@ int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, d
     // seg[k] = u^{t0+k} for k = 1 .. t1-t0-1 (k = 0 is the checkpoint itself)
     for (int64_t t = t0 + 1; t < t1; ++t) {
       const double* from = (t == t0 + 1) ? base : seg + n * (size_t)(t - t0 - 1);
-      e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, from, seg + n * (size_t)(t - t0), s);
+      e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, from, seg + n * (size_t)(t - t0), p->d_w, s);
       if (e != cudaSuccess) return cuda_fail(e, "launching the segment recompute");
     }
     for (int64_t t = t1 - 1; t >= t0; --t) {
       const double* ut = (t == t0) ? base : seg + n * (size_t)(t - t0);
-      e = launch_adjoint_step(p->ndim, p->boundary, p->g, cb, lam, ut, lam2, gx, gy, gz, gg, s);
+      e = launch_adjoint_step(p->ndim, p->boundary, p->g, cb, lam, ut, lam2, gx, gy, gz, gg, p->d_w, s);
       if (e != cudaSuccess) return cuda_fail(e, "launching the adjoint step");
       std::swap(lam, lam2);
     }
@@ -433,6 +605,20 @@ int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, d
   CUDA_TRY(cudaMemcpyAsync(h_loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s),
            "copying the loss");
   CUDA_TRY(cudaStreamSynchronize(s), "waiting for the adjoint");
+  return STENCIL_OK;
+}
+
+int stencil_plan_status(stencil_plan p, void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)cuda_stream), "waiting for the stream");
+  if (!p->d_status) return STENCIL_OK;
+  int st = 0;
+  CUDA_TRY(cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost), "reading the status");
+  if (st != 0) {
+    CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "clearing the status word");
+    return fail(st, "a kernel of this plan reported status %d (a bounded wait gave up)", st);
+  }
   return STENCIL_OK;
 }
 
@@ -463,7 +649,7 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
   if (probe_steps < 1) return fail(STENCIL_ERR_ARG, "probe_steps must be >= 1");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   struct Cand { int Tb, variant; };
-  std::vector<Cand> cands = {{1, kVariantDirect}};
+  std::vector<Cand> cands = {{1, kVariantDirect}, {1, kVariantStream}, {1, kVariantPersistent}};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0), "creating an event");
   CUDA_TRY(cudaEventCreate(&e1), "creating an event");
@@ -521,15 +707,13 @@ int stencil_batch_create(const stencil_batch_item* items, int n, int boundary, s
   }
   auto* b = new (std::nothrow) stencil_batch_s();
   if (!b) return fail(STENCIL_ERR_OOM, "allocating the batch");
-  b->n = n;
-  b->boundary = boundary;
   b->items.assign(items, items + n);
-  auto cleanup = [&](int rc) {
+  cudaError_t e = cudaMalloc(&b->d_partner, (size_t)total_cells * sizeof(double));
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(e, "allocating the partner buffers");
     stencil_batch_destroy(b);
     return rc;
-  };
-  cudaError_t e = cudaMalloc(&b->d_partner, (size_t)total_cells * sizeof(double));
-  if (e != cudaSuccess) return cleanup(cuda_fail(e, "allocating the partner buffers"));
+  }
   std::vector<BatchItemDev> hi(n);
   int64_t off = 0;
   for (int i = 0; i < n; ++i) {
@@ -539,59 +723,20 @@ int stencil_batch_create(const stencil_batch_item* items, int n, int boundary, s
     hi[i].ny = (int)it.ny;
     hi[i].nx = (int)it.nx;
     hi[i].T = (int)it.T;
-    hi[i].c0 = 1.0 - 4.0 * it.alpha;  // Eq. 3 centre weight
-    hi[i].c1 = it.alpha;
+    hi[i].w[0] = it.alpha;             // Eq. 3: alpha at the four neighbours,
+    hi[i].w[1] = it.alpha;
+    hi[i].w[2] = 1.0 - 4.0 * it.alpha; // 1 - 4 alpha at the centre
+    hi[i].w[3] = it.alpha;
+    hi[i].w[4] = it.alpha;
+    hi[i].zero[0] = hi[i].zero[1] = 0.0;
     off += it.ny * it.nx;
-    b->max_T = std::max(b->max_T, (int)it.T);
-    b->updates += it.ny * it.nx * it.T;
   }
-  // tiles, sorted by the item's T (largest first; ties by item, then position)
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return items[a].T > items[c].T; });
-  std::vector<BatchTile> tiles;
-  const int th = batched_tile_h(), tw = batched_tile_w();
-  for (int i : order) {
-    if (items[i].T == 0) continue;
-    for (int y0 = 0; y0 < (int)items[i].ny; y0 += th)
-      for (int x0 = 0; x0 < (int)items[i].nx; x0 += tw) tiles.push_back(BatchTile{i, y0, x0});
+  int rc = batch_init(b, hi, boundary);
+  if (rc) {
+    stencil_batch_destroy(b);
+    return rc;
   }
-  // items with T = 0 still need no work; keep at least one entry for the launch
-  b->ntiles = (int)tiles.size();
-  e = cudaMalloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n);
-  if (e != cudaSuccess) return cleanup(cuda_fail(e, "allocating the item table"));
-  e = cudaMemcpy(b->d_items, hi.data(), sizeof(BatchItemDev) * (size_t)n, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cleanup(cuda_fail(e, "copying the item table"));
-  e = cudaMalloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(1, tiles.size()));
-  if (e != cudaSuccess) return cleanup(cuda_fail(e, "allocating the tile list"));
-  if (!tiles.empty()) {
-    e = cudaMemcpy(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cleanup(cuda_fail(e, "copying the tile list"));
-  }
-  e = cudaMalloc(&b->d_ctl, 4 * sizeof(unsigned int));
-  if (e != cudaSuccess) return cleanup(cuda_fail(e, "allocating the barrier words"));
-  e = cudaMemset(b->d_ctl, 0, 4 * sizeof(unsigned int));
-  if (e != cudaSuccess) return cleanup(cuda_fail(e, "clearing the barrier words"));
-  int per_sm = batched_blocks_per_sm();
-  if (per_sm < 1) return cleanup(fail(STENCIL_ERR_CUDA, "the batched kernel does not fit on an SM"));
-  b->blocks = sm_count() * std::min(per_sm, 4);
   *out = b;
-  return STENCIL_OK;
-}
-
-static int batch_enqueue(stencil_batch b, cudaStream_t s) {
-  BatchLaunch L;
-  L.items = b->d_items;
-  L.tiles = b->d_tiles;
-  L.ntiles = b->ntiles;
-  L.max_T = b->max_T;
-  L.boundary = b->boundary;
-  L.barrier = b->d_ctl;
-  L.status = (int*)(b->d_ctl + 2);
-  L.spin_limit = 2000000000LL;  // 2 s of wall time per barrier wait
-  CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing the barrier words");
-  cudaError_t e = launch_batched(L, b->blocks, s);
-  if (e != cudaSuccess) return cuda_fail(e, "launching the batched kernel");
   return STENCIL_OK;
 }
 

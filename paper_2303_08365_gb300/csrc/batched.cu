@@ -101,11 +101,11 @@ __device__ __forceinline__ void tile_step(const BatchItemDev& it, const double* 
     const double vc = __ldcg(row + x);
     const double ve = ine ? __ldcg(row + xe) : 0.0;
     const double vs = ins ? __ldcg(src + (int64_t)ys * nx + x) : 0.0;
-    double acc = it.c1 * vn;
-    acc = fma(it.c1, vw, acc);
-    acc = fma(it.c0, vc, acc);
-    acc = fma(it.c1, ve, acc);
-    acc = fma(it.c1, vs, acc);
+    double acc = fma(it.w[0], vn, it.zero[r]);
+    acc = fma(it.w[1], vw, acc);
+    acc = fma(it.w[2], vc, acc);
+    acc = fma(it.w[3], ve, acc);
+    acc = fma(it.w[4], vs, acc);
     dst[(int64_t)y * nx + x] = acc;
   }
 }

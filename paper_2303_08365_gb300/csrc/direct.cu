@@ -6,6 +6,7 @@
 //
 // Operation: one step of u'(x) = sum_o w_o u~(x+o) (paper Sec. 2.1, Listing 1).
 #include "internal.h"
+#include "taps.cuh"
 
 namespace gbst {
 namespace {
@@ -32,7 +33,14 @@ __device__ __forceinline__ bool axis_index(int c, int n, int& out) {
 template <int NT, int MODE>
 __global__ void __launch_bounds__(256) k_direct(const double* __restrict__ src,
                                                 double* __restrict__ dst, int nz, int ny, int nx,
-                                                int zper, const __grid_constant__ TapList<NT> tp) {
+                                                int zper, const __grid_constant__ TapList<NT> tp,
+                                                const double* __restrict__ wdev) {
+  // up to 27 taps the weights live in registers (full FP64 rate); the
+  // 125-tap radius-2 box keeps them in the constant bank instead of spilling
+  constexpr bool kRegs = NT <= 27;
+  RegWeights<kRegs ? NT : 1> W;
+  if (kRegs) W.load(wdev);
+  const double zero = kRegs ? W.z[0] : 0.0;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   if (x >= nx || y >= ny) return;
@@ -48,15 +56,18 @@ __global__ void __launch_bounds__(256) k_direct(const double* __restrict__ src,
       in &= axis_index<MODE>(x + tp.dx[k], nx, xx);
       double v = 0.0;
       if (in) v = __ldg(src + ((int64_t)zz * ny + yy) * nx + xx);
-      acc = (k == 0) ? tp.w[0] * v : fma(tp.w[k], v, acc);
+      if constexpr (kRegs)
+        W.tap(acc, k, v, 0);
+      else
+        acc = fma(tp.w[k], v, k == 0 ? zero : acc);
     }
     dst[((int64_t)z * ny + y) * nx + x] = acc;
   }
 }
 
 template <int NT>
-cudaError_t launch_nt(int mode, const Geom& g, const HostTaps& ht, const double* src, double* dst,
-                      cudaStream_t stream) {
+cudaError_t launch_nt(int mode, const Geom& g, const HostTaps& ht, const double* wdev,
+                      const double* src, double* dst, cudaStream_t stream) {
   TapList<NT> tp;
   for (int k = 0; k < NT; ++k) {
     tp.w[k] = ht.w[k];
@@ -83,9 +94,9 @@ cudaError_t launch_nt(int mode, const Geom& g, const HostTaps& ht, const double*
     grid = dim3(gx, gy, (unsigned)zchunks);
   }
   switch (mode) {
-    case 0: k_direct<NT, 0><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp); break;
-    case 1: k_direct<NT, 1><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp); break;
-    default: k_direct<NT, 2><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp); break;
+    case 0: k_direct<NT, 0><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp, wdev); break;
+    case 1: k_direct<NT, 1><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp, wdev); break;
+    default: k_direct<NT, 2><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp, wdev); break;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
@@ -94,7 +105,7 @@ cudaError_t launch_nt(int mode, const Geom& g, const HostTaps& ht, const double*
 }  // namespace
 
 cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const Geom& g,
-                          const HostTaps& taps, const double* src, double* dst,
+                          const HostTaps& taps, const double* wdev, const double* src, double* dst,
                           cudaStream_t stream) {
   int mode = 0;
   if (boundary == kPeriodic) {
@@ -102,14 +113,14 @@ cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const
     mode = small ? 2 : 1;
   }
   switch (taps.n) {
-    case 3: return launch_nt<3>(mode, g, taps, src, dst, stream);
-    case 5: return launch_nt<5>(mode, g, taps, src, dst, stream);
-    case 7: return launch_nt<7>(mode, g, taps, src, dst, stream);
-    case 9: return launch_nt<9>(mode, g, taps, src, dst, stream);
-    case 13: return launch_nt<13>(mode, g, taps, src, dst, stream);
-    case 25: return launch_nt<25>(mode, g, taps, src, dst, stream);
-    case 27: return launch_nt<27>(mode, g, taps, src, dst, stream);
-    case 125: return launch_nt<125>(mode, g, taps, src, dst, stream);
+    case 3: return launch_nt<3>(mode, g, taps, wdev, src, dst, stream);
+    case 5: return launch_nt<5>(mode, g, taps, wdev, src, dst, stream);
+    case 7: return launch_nt<7>(mode, g, taps, wdev, src, dst, stream);
+    case 9: return launch_nt<9>(mode, g, taps, wdev, src, dst, stream);
+    case 13: return launch_nt<13>(mode, g, taps, wdev, src, dst, stream);
+    case 25: return launch_nt<25>(mode, g, taps, wdev, src, dst, stream);
+    case 27: return launch_nt<27>(mode, g, taps, wdev, src, dst, stream);
+    case 125: return launch_nt<125>(mode, g, taps, wdev, src, dst, stream);
     default: return cudaErrorInvalidValue;
   }
   (void)shape;

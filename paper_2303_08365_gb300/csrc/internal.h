@@ -58,9 +58,30 @@ struct HostTaps {
 
 // Launchers implemented in the .cu files.  Each returns a cudaError_t from
 // the launch (cudaSuccess when nothing failed) and enqueues on `stream`.
+// wdev: the plan's weights on the device (taps.n weights in tap order, then
+// kZeroSlots zeros; see taps.cuh).
 cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const Geom& g,
-                          const HostTaps& taps, const double* src, double* dst,
+                          const HostTaps& taps, const double* wdev, const double* src, double* dst,
                           cudaStream_t stream);
+
+// 3D radius-1 streaming sweep (TMA-fed shared-memory plane ring).  Eligible
+// when nx is even, both buffers are 16-byte aligned and, for periodic grids,
+// nx % 64 == 0 and ny % 16 == 0.
+bool stream3d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
+                       const void* b);
+cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const HostTaps& taps,
+                            const double* wdev, const double* src, double* dst, int* status,
+                            int sms, cudaStream_t stream);
+
+// 2D radius-1 streaming sweep (TMA-fed ring of 16-row blocks).  Same
+// eligibility rules with ny % 16 == 0 for periodic grids.  `equal` selects
+// the shared-partial-sum form for a box whose weights are all equal.
+bool stream2d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
+                       const void* b);
+bool taps_all_equal(const HostTaps& t);
+cudaError_t launch_stream2d(Shape shape, int boundary, bool equal, const Geom& g,
+                            const HostTaps& taps, const double* wdev, const double* src, double* dst,
+                            int* status, int sms, cudaStream_t stream);
 
 // Variable-coefficient diffusion: coefficient preparation, one forward step,
 // one fused adjoint step, gradient finalisation and the loss reduction.
@@ -75,13 +96,14 @@ struct VarcoefBufs {
 cudaError_t launch_varcoef_prepare(int ndim, int boundary, const Geom& g, const double* kappa,
                                    double dt, VarcoefBufs b, cudaStream_t stream);
 cudaError_t launch_varcoef_step(int ndim, int boundary, const Geom& g, VarcoefBufs b,
-                                const double* src, double* dst, cudaStream_t stream);
+                                const double* src, double* dst, const double* zero,
+                                cudaStream_t stream);
 // lam_out = A^T lam_in, and for every +face f=(i,n): G_f += (u_n - u_i)(lam_i - lam_n)
 // (lam = lam_in = lambda^{t+1}, u = u^t); ghost faces: Gg_i -= k_i * u_i * lam_i
 // where k_i is the number of ghost faces of cell i (Dirichlet only).
 cudaError_t launch_adjoint_step(int ndim, int boundary, const Geom& g, VarcoefBufs b,
                                 const double* lam_in, const double* u, double* lam_out,
-                                double* gx, double* gy, double* gz, double* gg,
+                                double* gx, double* gy, double* gz, double* gg, const double* zero,
                                 cudaStream_t stream);
 // grad_kappa_i = (dt/2) * sum_{faces f of i} G_f + dt * Gg_i
 cudaError_t launch_adjoint_finalize(int ndim, int boundary, const Geom& g, double dt,
@@ -103,7 +125,10 @@ struct BatchItemDev {
   double* b;     // library-owned partner buffer (parity 1)
   int ny, nx;
   int T;
-  double c0, c1; // Eq. 3 weights: 1 - 4*alpha and alpha
+  // 5-point star weights in lexicographic tap order: north (y-1), west (x-1),
+  // centre, east (x+1), south (y+1); Eq. 3 gives alpha, alpha, 1-4 alpha, alpha, alpha
+  double w[5];
+  double zero[2];  // 0.0: the addends of the first FMA of each row's chain
 };
 struct BatchLaunch {
   const BatchItemDev* items;

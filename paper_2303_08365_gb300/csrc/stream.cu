@@ -1,0 +1,326 @@
+// stream.cu -- 3D radius-1 sweep (7-point star or 27-point box) that streams
+// along z through a TMA-fed ring of shared-memory planes.
+//
+// One step of u'(x) = sum_o w_o u~(x+o) (paper Sec. 2.1, Listing 1).  The
+// paper's GPU design keeps a tile in shared memory so that global accesses
+// are coalesced (Sec. 4.2, checkerboard blocking); here the tile is a 64 x 16
+// (x, y) slab that advances plane by plane along z:
+//   - a 4-slot ring of planes (rows y0-1 .. y0+16, columns x0 .. x0+63), each
+//     filled by three TMA boxes (halo row above, 16 rows, halo row below)
+//     whose y and z coordinates are wrapped for periodic grids; out-of-range
+//     boxes read zeros, which is exactly the Dirichlet-zero ghost rule;
+//   - two planes are in flight while the CTA computes a third (double
+//     buffering: mbarrier transaction counts signal arrival);
+//   - the x-halo columns (x0-1 and x0+64) are 2 x 18 plain loads per plane,
+//     issued one plane ahead into registers;
+//   - every lane owns two adjacent x cells (one 16-byte shared load, one
+//     16-byte global store); the x-1 / x+2 neighbours come from the adjacent
+//     lanes by warp shuffle, the warp's edge lanes take the halo column;
+//   - every warp owns rows w and w+8 of the tile: four independent FMA chains
+//     per thread keep the FP64 pipe, the bound of this kernel, busy.
+// The taps are applied in the same lexicographic order as the direct sweep,
+// starting with a plain multiply, so the two kernels agree bitwise.
+// Work split: the (tile, z) planes of the grid are cut into equal contiguous
+// ranges, one per persistent CTA (a CTA may finish one tile's z-column and
+// start the next one's).
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "taps.cuh"
+
+namespace gbst {
+
+// cuTensorMapEncodeTiled from the driver, fetched once through the runtime's
+// entry-point query (no link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+namespace {
+
+constexpr int kTX = 64;
+constexpr int kTY = 16;
+constexpr int kRows = kTY + 2;
+constexpr int kSlots = 4;
+constexpr int kThreads = 256;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr uint32_t kPlaneBytes = kRows * kTX * sizeof(double);
+
+struct __align__(128) StreamSmem {
+  double plane[kSlots][kRows][kTX];  // TMA destination
+  double halo[kSlots][2][kRows];     // x-halo columns: [0] = x0-1, [1] = x0+64
+  uint64_t full[kSlots];
+  int abort;
+};
+
+template <int NT>
+struct StreamParams {
+  CUtensorMap map_row;   // box {64, 1, 1} over src
+  CUtensorMap map_main;  // box {64, 16, 1} over src
+  const double* src;
+  double* dst;
+  int nz, ny, nx;
+  int tiles_x, tiles_y;
+  long long work;  // tiles * nz plane-tiles
+  int* status;
+  const double* wdev;  // NT weights then kZeroSlots zeros (device)
+};
+
+__device__ __forceinline__ int wrap_or_keep(int c, int n, bool periodic) {
+  if (!periodic) return c;
+  return c < 0 ? c + n : (c >= n ? c - n : c);
+}
+
+// Loads (into a register) the x-halo value this thread is responsible for in
+// plane z, or 0 when the thread holds none.  Threads 0..35 cover the left
+// (x0-1) and right (x0+64) columns for rows y0-1 .. y0+16.
+template <bool PERIODIC>
+__device__ __forceinline__ double load_halo(const double* __restrict__ src, int z, int y0, int x0,
+                                            int nz, int ny, int nx) {
+  const int t = threadIdx.x;
+  if (t >= 2 * kRows) return 0.0;
+  const int side = t / kRows, r = t % kRows;
+  int x = side ? x0 + kTX : x0 - 1;
+  int y = y0 - 1 + r;
+  int zz = z;
+  if (PERIODIC) {
+    x = wrap_or_keep(x, nx, true);
+    y = wrap_or_keep(y, ny, true);
+    zz = wrap_or_keep(zz, nz, true);
+  } else if ((unsigned)x >= (unsigned)nx || (unsigned)y >= (unsigned)ny ||
+             (unsigned)zz >= (unsigned)nz) {
+    return 0.0;
+  }
+  return __ldg(src + ((int64_t)zz * ny + y) * nx + x);
+}
+
+__device__ __forceinline__ void store_halo(StreamSmem& S, int slot, double v) {
+  const int t = threadIdx.x;
+  if (t < 2 * kRows) S.halo[slot][t / kRows][t % kRows] = v;
+}
+
+template <int NT, bool PERIODIC>
+__device__ __forceinline__ void issue_plane(StreamSmem& S, const StreamParams<NT>& P, int slot,
+                                            int z, int y0, int x0) {
+  const int zc = wrap_or_keep(z, P.nz, PERIODIC);
+  const int ya = wrap_or_keep(y0 - 1, P.ny, PERIODIC);
+  const int yb = wrap_or_keep(y0 + kTY, P.ny, PERIODIC);
+  mbar_arrive_expect_tx(&S.full[slot], kPlaneBytes);
+  tma_load_3d(&S.plane[slot][0][0], &P.map_row, x0, ya, zc, &S.full[slot]);
+  tma_load_3d(&S.plane[slot][1][0], &P.map_main, x0, y0, zc, &S.full[slot]);
+  tma_load_3d(&S.plane[slot][kRows - 1][0], &P.map_row, x0, yb, zc, &S.full[slot]);
+}
+
+// Tap index of offset (dz, dy, dx) in the lexicographic tap list of the
+// shape class (box: all 27; star: the 7 axis offsets).
+template <bool BOX>
+__device__ __forceinline__ constexpr int tap_index(int dz, int dy, int dx) {
+  if (BOX) return ((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
+  return dz < 0 ? 0 : dz > 0 ? 6 : dy < 0 ? 1 : dy > 0 ? 5 : 3 + dx;
+}
+
+// Two adjacent cells (x, x+1) of tile row ry in the plane whose neighbours are
+// in slots (sm, s0, sp).
+template <int NT, bool BOX>
+__device__ __forceinline__ void compute_pair(const StreamSmem& S, const RegWeights<NT>& W, int sm,
+                                             int s0, int sp, int ry, int lane, int c0, double& a0,
+                                             double& a1) {
+  const int slots[3] = {sm, s0, sp};
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (!BOX && dz != 0 && dy != 0) continue;
+      const int sl = slots[dz + 1];
+      const int row = ry + 1 + dy;
+      const double2 p = *reinterpret_cast<const double2*>(&S.plane[sl][row][2 * lane]);
+      const bool need_x = BOX || (dz == 0 && dy == 0);
+      if (need_x) {
+        double wv = __shfl_up_sync(0xffffffffu, p.y, 1);
+        double ev = __shfl_down_sync(0xffffffffu, p.x, 1);
+        if (lane == 0) wv = S.halo[sl][0][row];
+        if (lane == 31) ev = S.halo[sl][1][row];
+        W.tap(a0, tap_index<BOX>(dz, dy, -1), wv, c0);
+        W.tap(a0, tap_index<BOX>(dz, dy, 0), p.x, c0);
+        W.tap(a0, tap_index<BOX>(dz, dy, 1), p.y, c0);
+        W.tap(a1, tap_index<BOX>(dz, dy, -1), p.x, c0 + 1);
+        W.tap(a1, tap_index<BOX>(dz, dy, 0), p.y, c0 + 1);
+        W.tap(a1, tap_index<BOX>(dz, dy, 1), ev, c0 + 1);
+      } else {
+        W.tap(a0, tap_index<BOX>(dz, dy, 0), p.x, c0);
+        W.tap(a1, tap_index<BOX>(dz, dy, 0), p.y, c0 + 1);
+      }
+    }
+  }
+}
+
+template <int NT, bool BOX, bool PERIODIC>
+__global__ void __launch_bounds__(kThreads, 2) k_stream3d(const __grid_constant__ StreamParams<NT> P) {
+  __shared__ StreamSmem S;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RegWeights<NT> W;
+  W.load(P.wdev);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSlots; ++s) mbar_init(&S.full[s], 1);
+    S.abort = 0;
+    fence_mbar_init();
+    prefetch_tmap(&P.map_row);
+    prefetch_tmap(&P.map_main);
+  }
+  __syncthreads();
+  const long long G = gridDim.x;
+  const long long f_begin = P.work * blockIdx.x / G;
+  const long long f_end = P.work * (blockIdx.x + 1) / G;
+  uint32_t seq = 0;  // planes issued by this CTA: slot = seq % 4, phase parity = (seq / 4) & 1
+  for (long long f = f_begin; f < f_end;) {
+    const int tile = (int)(f / P.nz);
+    const int za = (int)(f % P.nz);
+    const long long rem = f_end - f;
+    const int zb = (long long)P.nz < za + rem ? P.nz : (int)(za + rem);
+    f += zb - za;
+    const int x0 = (tile % P.tiles_x) * kTX;
+    const int y0 = (tile / P.tiles_x) * kTY;
+    const int nplanes = zb - za + 2;  // planes za-1 .. zb
+    const uint32_t base = seq;
+    seq += nplanes;
+    if (threadIdx.x == 0) {
+      for (int j = 0; j < kSlots && j < nplanes; ++j)
+        issue_plane<NT, PERIODIC>(S, P, (base + j) % kSlots, za - 1 + j, y0, x0);
+    }
+    for (int j = 0; j < 3; ++j)
+      store_halo(S, (base + j) % kSlots,
+                 load_halo<PERIODIC>(P.src, za - 1 + j, y0, x0, P.nz, P.ny, P.nx));
+    double halo_next = 0.0;
+    if (nplanes > 3) halo_next = load_halo<PERIODIC>(P.src, za + 2, y0, x0, P.nz, P.ny, P.nx);
+    __syncthreads();
+    int issued = min(kSlots, nplanes) - 1;  // highest plane index issued so far
+    for (int k = 1; k <= nplanes - 2; ++k) {
+      // wait for the planes this step reads (each plane is waited on once)
+      const int jfirst = (k == 1) ? 0 : k + 1;
+      for (int j = jfirst; j <= k + 1; ++j) {
+        const uint32_t g = base + j;
+        if (!mbar_wait_bounded(&S.full[g % kSlots], (g / kSlots) & 1, kWaitLimitNs)) {
+          S.abort = 1;
+          atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
+        }
+      }
+      const int sm = (base + k - 1) % kSlots, s0 = (base + k) % kSlots, sp = (base + k + 1) % kSlots;
+      const int z = za + k - 1;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int ry = warp + 8 * r;
+        double a0 = 0.0, a1 = 0.0;
+        compute_pair<NT, BOX>(S, W, sm, s0, sp, ry, lane, 2 * r, a0, a1);
+        const int y = y0 + ry, x = x0 + 2 * lane;
+        if (y < P.ny && x < P.nx) st_global_v2(P.dst + ((int64_t)z * P.ny + y) * P.nx + x, a0, a1);
+      }
+      if (k + 2 <= nplanes - 1) store_halo(S, (base + k + 2) % kSlots, halo_next);
+      if (k + 3 <= nplanes - 1)
+        halo_next = load_halo<PERIODIC>(P.src, za + k + 2, y0, x0, P.nz, P.ny, P.nx);
+      __syncthreads();
+      if (S.abort) {
+        // a wait gave up: let the copies still in flight land (bounded), then leave
+        if (threadIdx.x == 0)
+          for (int j = k + 2; j <= issued; ++j)
+            mbar_wait_bounded(&S.full[(base + j) % kSlots], ((base + j) / kSlots) & 1, kWaitLimitNs);
+        return;  // uniform: every thread read the flag after the barrier
+      }
+      if (k + 3 <= nplanes - 1) {
+        if (threadIdx.x == 0) {
+          fence_proxy_async_smem();
+          issue_plane<NT, PERIODIC>(S, P, (base + k + 3) % kSlots, za + k + 2, y0, x0);
+        }
+        issued = k + 3;
+      }
+    }
+  }
+}
+
+bool encode_3d(CUtensorMap* map, const double* base, int nz, int ny, int nx, int box_y) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(double), (cuuint64_t)nx * ny * sizeof(double)};
+  cuuint32_t box[3] = {(cuuint32_t)kTX, (cuuint32_t)box_y, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double*>(base), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int NT, bool BOX, bool PERIODIC>
+int occupancy() {
+  static int n = -1;
+  if (n < 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream3d<NT, BOX, PERIODIC>, kThreads, 0) !=
+        cudaSuccess)
+      n = 0;
+  }
+  return n;
+}
+
+template <int NT, bool BOX, bool PERIODIC>
+cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, double* dst, int* status,
+                     int sms, cudaStream_t stream) {
+  StreamParams<NT> P;
+  if (!encode_3d(&P.map_row, src, g.nz, g.ny, g.nx, 1) ||
+      !encode_3d(&P.map_main, src, g.nz, g.ny, g.nx, kTY))
+    return cudaErrorInvalidValue;
+  P.src = src;
+  P.dst = dst;
+  P.nz = g.nz;
+  P.ny = g.ny;
+  P.nx = g.nx;
+  P.tiles_x = (g.nx + kTX - 1) / kTX;
+  P.tiles_y = (g.ny + kTY - 1) / kTY;
+  P.work = (long long)P.tiles_x * P.tiles_y * g.nz;
+  P.status = status;
+  P.wdev = wdev;
+  int occ = occupancy<NT, BOX, PERIODIC>();
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)sms * occ;
+  if (grid > P.work) grid = P.work;
+  k_stream3d<NT, BOX, PERIODIC><<<(unsigned)grid, kThreads, 0, stream>>>(P);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool stream3d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
+                       const void* b) {
+  if (ndim != 3 || radius != 1) return false;
+  if (g.nx % 2 != 0) return false;                        // TMA: row pitch multiple of 16 bytes
+  if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return false;  // TMA base and 16-byte stores
+  if (boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % kTY != 0)) return false;
+  return tensor_map_encoder() != nullptr;
+}
+
+cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const HostTaps& taps,
+                            const double* wdev, const double* src, double* dst, int* status,
+                            int sms, cudaStream_t stream) {
+  const bool per = boundary == kPeriodic;
+  if (shape == Shape::kBox) {
+    if (taps.n != 27) return cudaErrorInvalidValue;
+    return per ? launch_t<27, true, true>(g, wdev, src, dst, status, sms, stream)
+               : launch_t<27, true, false>(g, wdev, src, dst, status, sms, stream);
+  }
+  if (taps.n != 7) return cudaErrorInvalidValue;
+  return per ? launch_t<7, false, true>(g, wdev, src, dst, status, sms, stream)
+             : launch_t<7, false, false>(g, wdev, src, dst, status, sms, stream);
+}
+
+}  // namespace gbst

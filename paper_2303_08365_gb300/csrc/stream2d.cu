@@ -1,0 +1,323 @@
+// stream2d.cu -- 2D radius-1 sweep (5-point star or 9-point box) that streams
+// along y through a TMA-fed ring of row blocks in shared memory.
+//
+// One step of u'(x) = sum_o w_o u~(x+o) (paper Sec. 2.1, Listing 1; Eq. 3 for
+// the heat weights).  A CTA owns a 64-column strip and walks down it in blocks
+// of 16 rows.  Shared memory holds a ring of 4 blocks = 64 consecutive rows,
+// so the row above / below any row is simply the previous / next ring row;
+// one TMA box (16 rows x 64 columns, y wrapped for periodic grids, zeros out
+// of range for Dirichlet) fills a block, two blocks are in flight while the
+// CTA computes a third.  x-halo columns come from plain loads one block ahead;
+// each lane owns two adjacent columns (16-byte shared loads and global
+// stores) and exchanges its edge values with the adjacent lanes by shuffle.
+//
+// Two arithmetic forms:
+//   - general weights: the taps in the direct kernel's lexicographic order
+//     (first product a multiply, then FMAs), bitwise equal to it;
+//   - equal box weights w (e.g. 1/9): u' = w * sum of the 9 values, with the
+//     sums shared between neighbouring cells -- each warp owns two adjacent
+//     rows, so the column sums of 3 rows share their middle pair, and the two
+//     cells of a lane share the middle pair of the row sum:
+//         s  = u[r][c] + u[r+1][c]
+//         V[r][c] = u[r-1][c] + s,  V[r+1][c] = s + u[r+2][c]
+//         t  = V[x] + V[x+1],  wt = w * t
+//         u'[x] = fma(w, V[x-1], wt),  u'[x+1] = fma(w, V[x+2], wt)
+//     3.5 FP64 operations per cell instead of 9 (plus the strip-edge columns).
+#include <cudaTypedefs.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "taps.cuh"
+
+namespace gbst {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+
+namespace {
+
+constexpr int kTX = 64;
+constexpr int kRB = 16;             // rows per block
+constexpr int kSlots = 4;
+constexpr int kRing = kSlots * kRB; // 64 ring rows
+constexpr int kThreads = 256;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+constexpr uint32_t kBlockBytes = kRB * kTX * sizeof(double);
+
+struct __align__(128) Smem2 {
+  double row[kRing][kTX];    // TMA destination (block s = rows 16s .. 16s+15)
+  double halo[kRing][2];     // columns x0-1 and x0+64 of each ring row
+  uint64_t full[kSlots];
+  int abort;
+};
+
+template <int NT>
+struct Params2 {
+  CUtensorMap map;  // box {64, 16} over src
+  const double* src;
+  double* dst;
+  int ny, nx;
+  int strips, blocks;  // per strip: ceil(ny / 16) blocks
+  long long work;      // strips * blocks
+  int* status;
+  const double* wdev;  // NT weights then kZeroSlots zeros (device)
+};
+
+__device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+// Thread t < 32 loads the halo value (row t % 16 of block `blk`, side t / 16).
+template <bool PERIODIC>
+__device__ __forceinline__ double load_halo2(const double* __restrict__ src, int blk, int x0, int ny,
+                                             int nx) {
+  const int t = threadIdx.x;
+  if (t >= 2 * kRB) return 0.0;
+  const int side = t / kRB, r = t % kRB;
+  int x = side ? x0 + kTX : x0 - 1;
+  int y = blk * kRB + r;
+  if (PERIODIC) {
+    x = wrapc(x, nx);
+    y = wrapc(y, ny);
+  } else if ((unsigned)x >= (unsigned)nx || (unsigned)y >= (unsigned)ny) {
+    return 0.0;
+  }
+  return __ldg(src + (int64_t)y * nx + x);
+}
+
+__device__ __forceinline__ void store_halo2(Smem2& S, int slot, double v) {
+  const int t = threadIdx.x;
+  if (t < 2 * kRB) S.halo[slot * kRB + t % kRB][t / kRB] = v;
+}
+
+template <int NT, bool PERIODIC>
+__device__ __forceinline__ void issue_block(Smem2& S, const Params2<NT>& P, int slot, int blk,
+                                            int x0) {
+  int y = blk * kRB;
+  if (PERIODIC) y = wrapc(y, P.ny);  // ny % 16 == 0: a block never straddles the edge
+  mbar_arrive_expect_tx(&S.full[slot], kBlockBytes);
+  tma_load_2d(&S.row[slot * kRB][0], &P.map, x0, y, &S.full[slot]);
+}
+
+template <bool BOX>
+__device__ __forceinline__ constexpr int tap_index2(int dy, int dx) {
+  if (BOX) return (dy + 1) * 3 + (dx + 1);
+  return dy < 0 ? 0 : dy > 0 ? 4 : 2 + dx;
+}
+
+// General weights: cells (x, x+1) of ring row q.
+template <int NT, bool BOX>
+__device__ __forceinline__ void pair_general(const Smem2& S, const RegWeights<NT>& W, int q, int lane,
+                                             int c0, double& a0, double& a1) {
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+    const int rr = (q + dy + kRing) % kRing;
+    const double2 p = *reinterpret_cast<const double2*>(&S.row[rr][2 * lane]);
+    if (BOX || dy == 0) {
+      double wv = __shfl_up_sync(0xffffffffu, p.y, 1);
+      double ev = __shfl_down_sync(0xffffffffu, p.x, 1);
+      if (lane == 0) wv = S.halo[rr][0];
+      if (lane == 31) ev = S.halo[rr][1];
+      W.tap(a0, tap_index2<BOX>(dy, -1), wv, c0);
+      W.tap(a0, tap_index2<BOX>(dy, 0), p.x, c0);
+      W.tap(a0, tap_index2<BOX>(dy, 1), p.y, c0);
+      W.tap(a1, tap_index2<BOX>(dy, -1), p.x, c0 + 1);
+      W.tap(a1, tap_index2<BOX>(dy, 0), p.y, c0 + 1);
+      W.tap(a1, tap_index2<BOX>(dy, 1), ev, c0 + 1);
+    } else {
+      W.tap(a0, tap_index2<BOX>(dy, 0), p.x, c0);
+      W.tap(a1, tap_index2<BOX>(dy, 0), p.y, c0 + 1);
+    }
+  }
+}
+
+// Equal weights: rows q and q+1 (cells x, x+1 of each).  out[row][cell].
+__device__ __forceinline__ void quad_equal(const Smem2& S, double w, int q, int lane,
+                                           double out[2][2]) {
+  const int qm = (q - 1 + kRing) % kRing, q1 = (q + 1) % kRing, q2 = (q + 2) % kRing;
+  const double2 a = *reinterpret_cast<const double2*>(&S.row[qm][2 * lane]);
+  const double2 b = *reinterpret_cast<const double2*>(&S.row[q][2 * lane]);
+  const double2 c = *reinterpret_cast<const double2*>(&S.row[q1][2 * lane]);
+  const double2 d = *reinterpret_cast<const double2*>(&S.row[q2][2 * lane]);
+  // column sums of 3 rows for the lane's two columns, rows q and q+1
+  const double s0 = b.x + c.x, s1 = b.y + c.y;
+  const double V00 = a.x + s0, V01 = a.y + s1;   // row q, columns x, x+1
+  const double V10 = s0 + d.x, V11 = s1 + d.y;   // row q+1
+  // column sums at the strip-edge columns (lanes 0 and 31 only)
+  double H0 = 0.0, H1 = 0.0;
+  if (lane == 0 || lane == 31) {
+    const int side = lane == 0 ? 0 : 1;
+    const double hs = S.halo[q][side] + S.halo[q1][side];
+    H0 = S.halo[qm][side] + hs;
+    H1 = hs + S.halo[q2][side];
+  }
+  // neighbours' column sums: x-1 from the lane below, x+2 from the lane above
+  double L0 = __shfl_up_sync(0xffffffffu, V01, 1), L1 = __shfl_up_sync(0xffffffffu, V11, 1);
+  double R0 = __shfl_down_sync(0xffffffffu, V00, 1), R1 = __shfl_down_sync(0xffffffffu, V10, 1);
+  if (lane == 0) { L0 = H0; L1 = H1; }
+  if (lane == 31) { R0 = H0; R1 = H1; }
+  const double wt0 = w * (V00 + V01), wt1 = w * (V10 + V11);
+  out[0][0] = fma(w, L0, wt0);
+  out[0][1] = fma(w, R0, wt0);
+  out[1][0] = fma(w, L1, wt1);
+  out[1][1] = fma(w, R1, wt1);
+}
+
+template <int NT, bool BOX, bool PERIODIC, bool EQUAL>
+__global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant__ Params2<NT> P) {
+  __shared__ Smem2 S;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  RegWeights<NT> W;
+  W.load(P.wdev);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSlots; ++s) mbar_init(&S.full[s], 1);
+    S.abort = 0;
+    fence_mbar_init();
+    prefetch_tmap(&P.map);
+  }
+  __syncthreads();
+  const long long G = gridDim.x;
+  const long long f_begin = P.work * blockIdx.x / G;
+  const long long f_end = P.work * (blockIdx.x + 1) / G;
+  uint32_t seq = 0;
+  for (long long f = f_begin; f < f_end;) {
+    const int strip = (int)(f / P.blocks);
+    const int ba = (int)(f % P.blocks);
+    const long long rem = f_end - f;
+    const int bb = (long long)P.blocks < ba + rem ? P.blocks : (int)(ba + rem);
+    f += bb - ba;
+    const int x0 = strip * kTX;
+    const int nblk = bb - ba + 2;  // blocks ba-1 .. bb
+    const uint32_t base = seq;
+    seq += nblk;
+    if (threadIdx.x == 0)
+      for (int j = 0; j < kSlots && j < nblk; ++j)
+        issue_block<NT, PERIODIC>(S, P, (base + j) % kSlots, ba - 1 + j, x0);
+    for (int j = 0; j < 3; ++j)
+      store_halo2(S, (base + j) % kSlots, load_halo2<PERIODIC>(P.src, ba - 1 + j, x0, P.ny, P.nx));
+    double halo_next = 0.0;
+    if (nblk > 3) halo_next = load_halo2<PERIODIC>(P.src, ba + 2, x0, P.ny, P.nx);
+    __syncthreads();
+    int issued = min(kSlots, nblk) - 1;
+    for (int k = 1; k <= nblk - 2; ++k) {
+      const int jfirst = (k == 1) ? 0 : k + 1;
+      for (int j = jfirst; j <= k + 1; ++j) {
+        const uint32_t g = base + j;
+        if (!mbar_wait_bounded(&S.full[g % kSlots], (g / kSlots) & 1, kWaitLimitNs)) {
+          S.abort = 1;
+          atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
+        }
+      }
+      const int slot = (base + k) % kSlots;
+      const int blk = ba + k - 1;
+      const int x = x0 + 2 * lane;
+      if (EQUAL) {
+        const int r = 2 * warp;  // rows r, r+1 of the block
+        double out[2][2];
+        quad_equal(S, W.w[0], slot * kRB + r, lane, out);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int y = blk * kRB + r + i;
+          if (y < P.ny && x < P.nx) st_global_v2(P.dst + (int64_t)y * P.nx + x, out[i][0], out[i][1]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const int r = warp + 8 * i;
+          double a0 = 0.0, a1 = 0.0;
+          pair_general<NT, BOX>(S, W, slot * kRB + r, lane, 2 * i, a0, a1);
+          const int y = blk * kRB + r;
+          if (y < P.ny && x < P.nx) st_global_v2(P.dst + (int64_t)y * P.nx + x, a0, a1);
+        }
+      }
+      if (k + 2 <= nblk - 1) store_halo2(S, (base + k + 2) % kSlots, halo_next);
+      if (k + 3 <= nblk - 1) halo_next = load_halo2<PERIODIC>(P.src, ba + k + 2, x0, P.ny, P.nx);
+      __syncthreads();
+      if (S.abort) {
+        if (threadIdx.x == 0)
+          for (int j = k + 2; j <= issued; ++j)
+            mbar_wait_bounded(&S.full[(base + j) % kSlots], ((base + j) / kSlots) & 1, kWaitLimitNs);
+        return;
+      }
+      if (k + 3 <= nblk - 1) {
+        if (threadIdx.x == 0) {
+          fence_proxy_async_smem();
+          issue_block<NT, PERIODIC>(S, P, (base + k + 3) % kSlots, ba + k + 2, x0);
+        }
+        issued = k + 3;
+      }
+    }
+  }
+}
+
+bool encode_2d(CUtensorMap* map, const double* base, int ny, int nx) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+  cuuint64_t strides[1] = {(cuuint64_t)nx * sizeof(double)};
+  cuuint32_t box[2] = {(cuuint32_t)kTX, (cuuint32_t)kRB};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NT, bool BOX, bool PERIODIC, bool EQUAL>
+cudaError_t launch2(const Geom& g, const double* wdev, const double* src, double* dst, int* status,
+                    int sms, cudaStream_t stream) {
+  Params2<NT> P;
+  if (!encode_2d(&P.map, src, g.ny, g.nx)) return cudaErrorInvalidValue;
+  P.src = src;
+  P.dst = dst;
+  P.ny = g.ny;
+  P.nx = g.nx;
+  P.strips = (g.nx + kTX - 1) / kTX;
+  P.blocks = (g.ny + kRB - 1) / kRB;
+  P.work = (long long)P.strips * P.blocks;
+  P.status = status;
+  P.wdev = wdev;
+  static int occ = -1;
+  if (occ < 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream2d<NT, BOX, PERIODIC, EQUAL>, kThreads,
+                                                    0) != cudaSuccess)
+    occ = 0;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)sms * occ;
+  if (grid > P.work) grid = P.work;
+  k_stream2d<NT, BOX, PERIODIC, EQUAL><<<(unsigned)grid, kThreads, 0, stream>>>(P);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool stream2d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
+                       const void* b) {
+  if (ndim != 2 || radius != 1) return false;
+  if (g.nx % 2 != 0) return false;
+  if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return false;
+  if (boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % kRB != 0)) return false;
+  return tensor_map_encoder() != nullptr;
+}
+
+bool taps_all_equal(const HostTaps& t) {
+  for (int k = 1; k < t.n; ++k)
+    if (t.w[k] != t.w[0]) return false;
+  return t.n > 0;
+}
+
+cudaError_t launch_stream2d(Shape shape, int boundary, bool equal, const Geom& g,
+                            const HostTaps& taps, const double* wdev, const double* src, double* dst,
+                            int* status, int sms, cudaStream_t stream) {
+  const bool per = boundary == kPeriodic;
+  if (shape == Shape::kBox) {
+    if (taps.n != 9) return cudaErrorInvalidValue;
+    if (equal)
+      return per ? launch2<9, true, true, true>(g, wdev, src, dst, status, sms, stream)
+                 : launch2<9, true, false, true>(g, wdev, src, dst, status, sms, stream);
+    return per ? launch2<9, true, true, false>(g, wdev, src, dst, status, sms, stream)
+               : launch2<9, true, false, false>(g, wdev, src, dst, status, sms, stream);
+  }
+  if (taps.n != 5) return cudaErrorInvalidValue;
+  return per ? launch2<5, false, true, false>(g, wdev, src, dst, status, sms, stream)
+             : launch2<5, false, false, false>(g, wdev, src, dst, status, sms, stream);
+}
+
+}  // namespace gbst

@@ -86,8 +86,8 @@ __device__ __forceinline__ double apply_a(const double* __restrict__ u, const do
                                           const double* __restrict__ cx, const double* __restrict__ cy,
                                           const double* __restrict__ cz, bool periodic, int x, int y,
                                           int z, int nx, int ny, int nz, int64_t i, int64_t sy,
-                                          int64_t sz) {
-  double acc = __ldg(c0 + i) * __ldg(u + i);
+                                          int64_t sz, double zero) {
+  double acc = fma(__ldg(c0 + i), __ldg(u + i), zero);
   const int cs[3] = {x, y, z};
   const int ns[3] = {nx, ny, nz};
   const int64_t st[3] = {1, sy, sz};
@@ -106,9 +106,10 @@ template <int NDIM>
 __global__ void __launch_bounds__(256) k_step(const double* __restrict__ src, double* __restrict__ dst,
                                               const double* __restrict__ c0, const double* __restrict__ cx,
                                               const double* __restrict__ cy, const double* __restrict__ cz,
-                                              bool periodic, int nz, int ny, int nx) {
+                                              bool periodic, int nz, int ny, int nx,
+                                              const double* __restrict__ zp) {
   CELL_COORDS
-  dst[i] = apply_a<NDIM>(src, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, sy, sz);
+  dst[i] = apply_a<NDIM>(src, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, sy, sz, __ldg(zp));
 }
 
 template <int NDIM>
@@ -121,9 +122,9 @@ __global__ void __launch_bounds__(256) k_adjoint(const double* __restrict__ lam,
                                                  const double* __restrict__ cz, double* __restrict__ gx,
                                                  double* __restrict__ gy, double* __restrict__ gz,
                                                  double* __restrict__ gg, bool periodic, int nz,
-                                                 int ny, int nx) {
+                                                 int ny, int nx, const double* __restrict__ zp) {
   CELL_COORDS
-  lam_out[i] = apply_a<NDIM>(lam, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, sy, sz);
+  lam_out[i] = apply_a<NDIM>(lam, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, sy, sz, __ldg(zp));
   const double ui = __ldg(u + i), li = __ldg(lam + i);
   const int cs[3] = {x, y, z};
   const int ns[3] = {nx, ny, nz};
@@ -232,36 +233,37 @@ cudaError_t launch_varcoef_prepare(int ndim, int boundary, const Geom& g, const 
 }
 
 cudaError_t launch_varcoef_step(int ndim, int boundary, const Geom& g, VarcoefBufs b,
-                                const double* src, double* dst, cudaStream_t stream) {
+                                const double* src, double* dst, const double* zero,
+                                cudaStream_t stream) {
   dim3 grid, block;
   cell_launch_shape(g, grid, block);
   bool per = boundary == kPeriodic;
   if (ndim == 3)
-    k_step<3><<<grid, block, 0, stream>>>(src, dst, b.c0, b.cx, b.cy, b.cz, per, g.nz, g.ny, g.nx);
+    k_step<3><<<grid, block, 0, stream>>>(src, dst, b.c0, b.cx, b.cy, b.cz, per, g.nz, g.ny, g.nx, zero);
   else if (ndim == 2)
-    k_step<2><<<grid, block, 0, stream>>>(src, dst, b.c0, b.cx, b.cy, b.cz, per, g.nz, g.ny, g.nx);
+    k_step<2><<<grid, block, 0, stream>>>(src, dst, b.c0, b.cx, b.cy, b.cz, per, g.nz, g.ny, g.nx, zero);
   else
-    k_step<1><<<grid, block, 0, stream>>>(src, dst, b.c0, b.cx, b.cy, b.cz, per, g.nz, g.ny, g.nx);
+    k_step<1><<<grid, block, 0, stream>>>(src, dst, b.c0, b.cx, b.cy, b.cz, per, g.nz, g.ny, g.nx, zero);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_step(int ndim, int boundary, const Geom& g, VarcoefBufs b,
                                 const double* lam_in, const double* u, double* lam_out,
-                                double* gx, double* gy, double* gz, double* gg,
+                                double* gx, double* gy, double* gz, double* gg, const double* zero,
                                 cudaStream_t stream) {
   dim3 grid, block;
   cell_launch_shape(g, grid, block);
   bool per = boundary == kPeriodic;
   if (ndim == 3)
     k_adjoint<3><<<grid, block, 0, stream>>>(lam_in, u, lam_out, b.c0, b.cx, b.cy, b.cz, gx, gy, gz,
-                                             gg, per, g.nz, g.ny, g.nx);
+                                             gg, per, g.nz, g.ny, g.nx, zero);
   else if (ndim == 2)
     k_adjoint<2><<<grid, block, 0, stream>>>(lam_in, u, lam_out, b.c0, b.cx, b.cy, b.cz, gx, gy, gz,
-                                             gg, per, g.nz, g.ny, g.nx);
+                                             gg, per, g.nz, g.ny, g.nx, zero);
   else
     k_adjoint<1><<<grid, block, 0, stream>>>(lam_in, u, lam_out, b.c0, b.cx, b.cy, b.cz, gx, gy, gz,
-                                             gg, per, g.nz, g.ny, g.nx);
+                                             gg, per, g.nz, g.ny, g.nx, zero);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

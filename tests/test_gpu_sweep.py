@@ -206,11 +206,98 @@ def test_launch_count_advances(st):
     import torch
     before = st.stencil_launch_count()
     u0 = synth.uniform(1, (16, 16))
-    gpu_run(st, u0, synth.heat_weights(2, 0.1), 1, DIRICHLET, 5)
+    gpu_run(st, u0, synth.heat_weights(2, 0.1), 1, DIRICHLET, 5, Tb=1, variant=st.VARIANT_DIRECT)
     assert st.stencil_launch_count() >= before + 5
+    mid = st.stencil_launch_count()
+    gpu_run(st, u0, synth.heat_weights(2, 0.1), 1, DIRICHLET, 5, Tb=1, variant=st.VARIANT_PERSISTENT)
+    assert st.stencil_launch_count() == mid + 1   # one persistent launch for all 5 steps
     torch.cuda.synchronize()
 
 
 def test_fp64_peak_is_plausible(st):
     r = st.stencil_fp64_peak(50.0)
     assert 1e11 < r < 1e13
+
+
+STREAM_CASES = [
+    # shape, boundary, kind
+    ((40, 48, 128), PERIODIC, "heat"),
+    ((40, 48, 128), PERIODIC, "box_rand"),
+    ((13, 37, 70), DIRICHLET, "heat"),
+    ((13, 37, 70), DIRICHLET, "box_rand"),
+    ((5, 20, 130), DIRICHLET, "star_rand"),
+    ((1, 16, 64), PERIODIC, "box_rand"),
+    ((3, 1, 2), DIRICHLET, "box_rand"),
+]
+
+
+@pytest.mark.parametrize("shape,boundary,kind", STREAM_CASES)
+def test_stream_kernel_matches_direct_bitwise_and_oracle(st, shape, boundary, kind):
+    """The TMA streaming kernel applies the taps in the direct kernel's order:
+    the two agree bit for bit; both match the oracle."""
+    w = weights_for(kind, 3, 1, 300)
+    u0 = synth.normal(8, shape)
+    T = 6
+    a = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_STREAM)
+    b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    ref = oracle.run(u0, w, 1, boundary, T, nthreads=0)
+    assert normwise_rel(a, ref) <= TOL
+
+
+def test_stream_kernel_rejects_ineligible_shapes(st):
+    import torch
+    u0 = synth.uniform(2, (8, 20, 70))   # periodic needs nx % 64 == 0 and ny % 16 == 0
+    p = st.Plan(u0.shape, 1, synth.heat_weights(3, 0.1), PERIODIC)
+    p.set_tuning(1, st.VARIANT_STREAM)
+    g = torch.from_numpy(u0).cuda()
+    with pytest.raises(st.StencilError) as ei:
+        p.run(g, 2)
+    assert ei.value.code == st.ERR_UNSUPPORTED
+    p.set_tuning(0, 0)          # automatic choice falls back to the direct kernel
+    p.run(g, 2)
+    assert p.status() == 0
+    p.close()
+
+
+STREAM2D_CASES = [
+    ((32, 128), PERIODIC, "star_rand"),
+    ((32, 128), PERIODIC, "box_rand"),
+    ((37, 70), DIRICHLET, "heat"),
+    ((37, 70), DIRICHLET, "box_rand"),
+    ((130, 64), DIRICHLET, "star_rand"),
+    ((1, 2), DIRICHLET, "box_rand"),
+]
+
+
+@pytest.mark.parametrize("shape,boundary,kind", STREAM2D_CASES)
+def test_stream2d_matches_direct_bitwise_and_oracle(st, shape, boundary, kind):
+    w = weights_for(kind, 2, 1, 400)
+    u0 = synth.normal(9, shape)
+    T = 7
+    a = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_STREAM)
+    b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
+
+
+@pytest.mark.parametrize("shape,boundary,T", [((64, 256), PERIODIC, 40), ((45, 94), DIRICHLET, 33),
+                                              ((16, 64), PERIODIC, 1)])
+def test_equal_weight_box_shared_sums(st, shape, boundary, T):
+    """Equal box weights take the shared partial-sum form (a different
+    rounding order): checked against the oracle only."""
+    w = synth.box_weights(2, 1.0 / 9.0)
+    u0 = synth.uniform(10, shape)
+    got = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_STREAM)
+    assert normwise_rel(got, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
+
+
+@pytest.mark.parametrize("shape,boundary,T", [((256, 256), DIRICHLET, 100), ((37, 53), DIRICHLET, 17),
+                                              ((48, 64), PERIODIC, 9), ((1, 1), PERIODIC, 2)])
+def test_persistent_single_grid_matches_direct_bitwise(st, shape, boundary, T):
+    w = weights_for("star_rand", 2, 1, 500)
+    u0 = synth.uniform(11, shape)
+    a = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_PERSISTENT)
+    b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL

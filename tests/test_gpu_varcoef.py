@@ -93,21 +93,27 @@ def test_full_size_finite_differences(st):
     U0, K, TG = cuda(u0), cuda(kappa), cuda(target)
     loss, gu, gk = p.adjoint(U0, K, dt, TG, T, ckpt_every=32)
 
-    def L(u, k):
+    def final(u, k):
         x = u.clone()
         p.run(x, T, k, dt)
-        return 0.5 * float(((x - TG) ** 2).sum())
+        return x
 
-    assert abs(L(U0, K) - loss) <= 1e-12 * loss
+    def dL(up, um):
+        # L(+) - L(-) summed element by element as (u+ - u-)(u+ + u- - 2 target)/2,
+        # so the difference is not lost in the rounding of two ~1e7 sums
+        return 0.5 * float(((up - um) * (up + um - 2.0 * TG)).sum())
+
+    base = final(U0, K)
+    assert abs(0.5 * float(((base - TG) ** 2).sum()) - loss) <= 1e-12 * loss
     du = cuda(synth.normal(seed + 10, shape))
     dk = cuda(synth.normal(seed + 11, shape)) * K
     h = 1e-3
-    fd_u = (L(U0 + h * du, K) - L(U0 - h * du, K)) / (2 * h)
+    fd_u = dL(final(U0 + h * du, K), final(U0 - h * du, K)) / (2 * h)
     an_u = float((gu * du).sum())
     assert abs(fd_u - an_u) <= 1e-8 * abs(an_u)
-    h = 1e-6
-    fd_k = (L(U0, K + h * dk) - L(U0, K - h * dk)) / (2 * h)
+    h = 1e-5
+    fd_k = dL(final(U0, K + h * dk), final(U0, K - h * dk)) / (2 * h)
     an_k = float((gk * dk).sum())
-    assert abs(fd_k - an_k) <= 1e-5 * abs(an_k)
+    assert abs(fd_k - an_k) <= 1e-6 * abs(an_k)
     p.close()
     torch.cuda.synchronize()
