@@ -170,6 +170,36 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
 /* Name of a kernel variant id ("" for an unknown id). */
 const char* stencil_variant_name(int variant);
 
+/* ------------------------------------------------ allocation-free entry */
+
+/* Largest grid, in cells, that stencil_run_2d_static accepts. */
+#define STENCIL_STATIC_MAX_CELLS (1 << 20)
+
+/* The paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory at the moment they want a sweep -- for example code
+ * whose GPU memory is owned by another allocator's pool (a framework cache
+ * that has already reserved the HBM, so a cudaMalloc behind its back fails),
+ * or a latency-critical loop that must not take the device-wide
+ * synchronisation of cudaMalloc / cudaFree.
+ *
+ * Advances d_grid (device, ny x nx row-major doubles, in place) by T steps of
+ * the 2D 5-point star stencil given by the dense 3x3 weights (host; the four
+ * corner weights must be 0), with the given boundary rule, in one launch of
+ * the persistent kernel.  It allocates nothing: the partner grid, tile list
+ * and barrier words live in one array of about 10 MB (9.5 MiB) that every GPU loading
+ * the library reserves until the process exits.
+ *   - ny * nx must not exceed STENCIL_STATIC_MAX_CELLS (STENCIL_ERR_UNSUPPORTED
+ *     otherwise, with a message naming the limit).
+ *   - Every call shares that array and it keeps the last call's contents (the
+ *     barrier words are cleared before each launch): calls whose work
+ *     overlaps on the GPU race and must be serialised by the caller.
+ *   - The first call on a device looks up the array's device address and the
+ *     kernel's occupancy with that device current; make that first call before
+ *     any stream capture begins.
+ * Asynchronous on cuda_stream; errors are reported by stencil_last_error. */
+int stencil_run_2d_static(int64_t ny, int64_t nx, const double* weights, int boundary,
+                          double* d_grid, int64_t T, void* cuda_stream);
+
 /* ---------------------------------------------------------- diagnostics */
 
 /* Message for the last failing call on this thread ("" if none). */

@@ -69,6 +69,8 @@ SIGNATURES = [
     ("stencil_last_error", ctypes.c_char_p, []),
     ("stencil_launch_count", ctypes.c_int64, []),
     ("stencil_fp64_peak", ctypes.c_int, [ctypes.c_double, _DP, _VP]),
+    ("stencil_run_2d_static", ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _DP, ctypes.c_int, _VP,
+                                             ctypes.c_int64, _VP]),
 ]
 
 _lib = None
@@ -254,6 +256,15 @@ def stencil_autotune(h, scratch_grid, probe_steps, stream=None):
 
 def stencil_variant_name(v):
     return lib().stencil_variant_name(int(v)).decode()
+
+
+def stencil_run_2d_static(grid, weights, boundary, T, stream=None):
+    """Allocation-free 2D 5-point sweep of a small grid (see include/stencil.h)."""
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+    if w.size != 9:
+        raise ValueError("weights must be a dense 3x3 array")
+    _check(lib().stencil_run_2d_static(int(grid.shape[0]), int(grid.shape[1]), w.ctypes.data_as(_DP),
+                                       int(boundary), _dev_ptr(grid, "grid"), int(T), _stream(stream)))
 
 
 def stencil_launch_count():
