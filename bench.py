@@ -41,6 +41,12 @@ HEADLINE = dict(name="heat3d-7pt", shape=(512, 512, 512), T=1000, alpha=0.1, bou
 FLOPS = {"heat3d-7pt": 13, "box2d-9pt": 17, "box3d-27pt": 53, "heat2d-5pt": 9,
          "varcoef-7pt": 13, "adjoint-7pt": 13 + 25}
 NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
+# FP64 instructions the kernels issue per cell update (one pipe slot each):
+# K for a K-tap chain; 4.25 for the equal-weight 9-point box with shared
+# partial sums (17 warp instructions per 2 rows x 64 columns, strip edges
+# included); adjoint: forward 7 + recompute 7 + transposed step 7 + 3 faces x 3.
+INSTR = {"heat3d-7pt": 7, "box3d-27pt": 27, "box2d-9pt": 4.25, "heat2d-5pt": 5,
+         "varcoef-7pt": 7, "adjoint-7pt": 7 + 7 + 7 + 9}
 
 
 # ------------------------------------------------------------------ helpers
@@ -122,11 +128,8 @@ def barrier_max(world, value):
     """Barrier, then the max of `value` over ranks."""
     if world == 1:
         return value
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2303_08365_gb300 import shard
+    return shard.max_over_ranks(value)
 
 
 def barrier(world):
@@ -148,22 +151,30 @@ def cuda_time(fn, stream):
     return e0.elapsed_time(e1)
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {"stream3d": ["stream.cu", "ptx.cuh", "taps.cuh"],
+                  "stream2d": ["stream2d.cu", "ptx.cuh", "taps.cuh"],
+                  "temporal": ["temporal.cu", "taps.cuh"],
+                  "direct": ["direct.cu", "taps.cuh"],
+                  "batched": ["batched.cu"],
+                  "varcoef": ["varcoef.cu"],
+                  "adjoint": ["varcoef.cu"]}
+
+
+def kernel_source_hash(kernel):
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2303_08365_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(cs, f), "rb").read())
+    for f in KERNEL_SOURCES.get(kernel, []):
+        h.update(open(os.path.join(cs, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the kernel's current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
-    cur = kernel_source_hash()
+    cur = kernel_source_hash(kernel)
     for ln in open(path):
         parts = ln.split()
         if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == workload:
@@ -172,12 +183,24 @@ def recorded_traffic(kernel, workload):
     return None
 
 
+def variant_kernel(variant, ndim):
+    """The kernel family a variant name runs (for the traffic record)."""
+    if variant == "stream":
+        return "stream3d" if ndim == 3 else "stream2d"
+    if variant == "persistent":
+        return "batched"
+    return variant
+
+
 def roofline(name, cells, T, ms, launches, peak_tflops, kernel):
     flops = FLOPS[name] * cells * T
     achieved = flops / (ms * 1e-3) / 1e12
     per_launch = FLOPS[name] * cells * T / max(launches, 1)
+    instr_rate = INSTR[name] * cells * T / (ms * 1e-3)       # FP64 instructions per second
     return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tflops, 4),
             "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+            "fp64_instr_per_cell": INSTR[name],
+            "fp64_pipe_frac": round(instr_rate / (peak_tflops * 1e12 / 2), 4),
             "traffic": recorded_traffic(kernel, name),
             "algorithmic_flops_per_launch": per_launch,
             "algorithmic_bytes_per_launch": 16 * cells * T / max(launches, 1),
@@ -248,13 +271,20 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
                         f"{'periodic' if boundary else 'dirichlet0'}",
             "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
             "Tb": tb, "variant": st.stencil_variant_name(v), "launches": launches,
-            "roofline": roofline(name, cells, T, ms, launches, peak, "sweep")}
+            "roofline": roofline(name, cells, T, ms, launches, peak,
+                                 variant_kernel(st.stencil_variant_name(v), len(shape)))}
 
 
-def form_batched(st, stream, peak):
+def form_batched(st, stream, peak, rank=0, world=1):
+    """The 96-grid batch; with N ranks each advances its own shard (greedy
+    packing on cells x T) and the rate is all updates / the slowest rank."""
     import torch
-    items = synth.batch_items(synth.SEED_BATCH)
-    grids0 = [synth.uniform(synth.SEED_BATCH + 1000 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
+    from paper_2303_08365_gb300 import shard
+    all_items = synth.batch_items(synth.SEED_BATCH)
+    mine = shard.rank_items(all_items, rank, world)
+    items = [all_items[i] for i in mine]
+    total_updates = sum(ny * nx * T for ny, nx, _, T in all_items)
+    grids0 = [synth.uniform(synth.SEED_BATCH + 1000 + i, all_items[i][:2]) for i in mine]
     dev = [torch.from_numpy(g).cuda() for g in grids0]
     alphas = [a for _, _, a, _ in items]
     steps = [T for *_, T in items]
@@ -268,6 +298,8 @@ def form_batched(st, stream, peak):
     launches = (st.stencil_launch_count() - l0) // reps
     assert b.status() == 0
     b.close()
+    ms = shard.max_over_ranks(ms)
+    updates = total_updates
     # the plain single-grid sweep over the same grids, one after another
     plans = [st.Plan((ny, nx), 1, synth.heat_weights(2, a), st.DIRICHLET_ZERO) for ny, nx, a, _ in items]
 
@@ -275,14 +307,14 @@ def form_batched(st, stream, peak):
         for p, d, T in zip(plans, dev, steps):
             p.run(d, T, stream=stream)
     plain()
-    ms_plain = cuda_time(plain, stream)
+    ms_plain = shard.max_over_ranks(cuda_time(plain, stream))
     for p in plans:
         p.close()
     del dev
     torch.cuda.empty_cache()
     rate = updates / (ms * 1e-3) / 1e9
     return {"workload": f"batched 96 x heat2d-5pt, sides log-uniform [128,4096], T in [50,500], "
-                        f"{updates:.3e} updates",
+                        f"{updates:.3e} updates" + (f", sharded over {world} ranks" if world > 1 else ""),
             "gstencil_per_s": round(rate, 3), "ms": round(ms, 3), "launches": launches,
             "plain_sweep_ms": round(ms_plain, 3),
             "plain_sweep_gstencil_per_s": round(updates / (ms_plain * 1e-3) / 1e9, 3),
@@ -402,16 +434,35 @@ def run_case(args):
         shape = (n, n)
         w = synth.heat_weights(2, 0.1) if name == "heat2d" else synth.box_weights(2, 1.0 / 9.0)
         bnd = 0 if name == "heat2d" else 1
-    elif name == "varcoef":
+    elif name in ("varcoef", "adjoint"):
         shape = (n, n, n)
+    elif name == "batched":
+        # a reduced batch of the 96-grid workload's kind: sides log-uniform in [64, n]
+        items = synth.batch_items(synth.SEED_BATCH, count=24, side_lo=64, side_hi=n, t_lo=args.T,
+                                  t_hi=args.T)
+        dev = [torch.from_numpy(synth.uniform(synth.SEED_BATCH + 1000 + i, (ny, nx))).cuda()
+               for i, (ny, nx, _, _) in enumerate(items)]
+        b = st.Batch(dev, [a for _, _, a, _ in items], [T for *_, T in items])
+        for _ in range(args.warmup):
+            b.run(stream)
+        ms = cuda_time(lambda: [b.run(stream) for _ in range(args.steps)], stream) / args.steps
+        assert b.status() == 0
+        upd = sum(ny * nx * T for ny, nx, _, T in items)
+        print(json.dumps({"case": name, "items": len(items), "updates": upd, "ms": round(ms, 4),
+                          "gstencil_per_s": round(upd / (ms * 1e-3) / 1e9, 3)}))
+        return 0
     else:
         raise SystemExit(f"unknown case {name}")
     grid = torch.from_numpy(synth.uniform(synth.SEED_HEAT3D, shape)).cuda()
-    if name == "varcoef":
+    if name in ("varcoef", "adjoint"):
         kappa = torch.from_numpy(synth.lognormal(synth.SEED_ADJOINT + 1, shape)).cuda()
         dt = 0.1 / float(kappa.max())
         plan = st.Plan.varcoef(shape, st.PERIODIC)
-        fn = lambda: plan.run(grid, args.T, kappa, dt, stream=stream)
+        if name == "varcoef":
+            fn = lambda: plan.run(grid, args.T, kappa, dt, stream=stream)
+        else:
+            target = torch.from_numpy(synth.normal(synth.SEED_ADJOINT + 2, shape)).cuda()
+            fn = lambda: plan.adjoint(grid, kappa, dt, target, args.T, ckpt_every=0, stream=stream)
     else:
         plan = st.Plan(shape, 1, w, bnd)
         if args.variant:
@@ -435,7 +486,8 @@ def main():
     ap.add_argument("--forms", default="all", help="all | none | comma list of "
                     "box2d,box3d,heat2d,batched,adjoint")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default=None, help="profiling mode: heat3d | box3d | heat2d | box2d | varcoef")
+    ap.add_argument("--case", default=None,
+                    help="profiling mode: heat3d | box3d | heat2d | box2d | varcoef | adjoint | batched")
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--T", type=int, default=4)
     ap.add_argument("--variant", type=int, default=0)
@@ -473,7 +525,7 @@ def main():
                    "Tb": h["Tb"], "variant": h["variant"],
                    "l2_flush": "none needed: each launch streams 2 GiB > 129 MB L2"},
         "roofline": roofline("heat3d-7pt", cells, T, h["ms"], h["launches"] // args.steps,
-                             peak_tflops, "sweep"),
+                             peak_tflops, variant_kernel(h["variant"], 3)),
         "fp64_peak_tflops_measured": round(peak_tflops, 4),
         "e2e": {"value": round(e2e_value, 4), "unit": "GStencil/s",
                 "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"]},
@@ -485,6 +537,8 @@ def main():
     forms = {}
     want = set(["box2d", "box3d", "heat2d", "batched", "adjoint"]) if args.forms == "all" else \
         set() if args.forms == "none" else set(args.forms.split(","))
+    if "batched" in want:
+        forms["batched"] = form_batched(st, stream, peak_tflops, rank, world)
     if rank == 0:
         if "heat2d" in want:
             shp = (256, 256)
@@ -499,8 +553,6 @@ def main():
             shp = (384, 384, 384)
             forms["box3d"] = form_const(st, "box3d-27pt", shp, 1, synth.box_weights(3, seed=synth.SEED_BOX3D),
                                         0, 500, synth.normal(synth.SEED_BOX3D, shp), stream, peak_tflops)
-        if "batched" in want:
-            forms["batched"] = form_batched(st, stream, peak_tflops)
         if "adjoint" in want:
             forms["adjoint"] = form_adjoint(st, stream, peak_tflops)
         line["forms"] = forms

@@ -110,6 +110,15 @@ int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, d
                     const double* d_target, int64_t T, int ckpt_every, double* d_grad_u0,
                     double* d_grad_kappa, double* h_loss, void* cuda_stream);
 
+/* The same reverse sweep for any upstream gradient: given lambda^T = dL/du^T
+ * (device, same shape) for some scalar L of u^T, writes dL/du0 = lambda^0
+ * and dL/dkappa (formulas above) into d_grad_u0 and d_grad_kappa.
+ * Asynchronous on cuda_stream (the vector-Jacobian product behind the
+ * torch.autograd.Function of the binding). */
+int stencil_adjoint_vjp(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,
+                        int64_t T, int ckpt_every, const double* d_lambda_T, double* d_grad_u0,
+                        double* d_grad_kappa, void* cuda_stream);
+
 /* ----------------------------------------------------------- batched form */
 
 /* One independent 2D heat grid of a batch: ny x nx cells (row-major, device,

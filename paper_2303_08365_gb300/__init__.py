@@ -55,6 +55,8 @@ SIGNATURES = [
     ("stencil_run_host", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_double, _VP]),
     ("stencil_adjoint", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP, ctypes.c_int64, ctypes.c_int,
                                        _VP, _VP, _DP, _VP]),
+    ("stencil_adjoint_vjp", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
+                                           _VP, _VP, _VP, _VP]),
     ("stencil_batch_create", ctypes.c_int, [ctypes.POINTER(BatchItem), ctypes.c_int, ctypes.c_int,
                                             ctypes.POINTER(_VP)]),
     ("stencil_batch_run", ctypes.c_int, [_VP, _VP]),
@@ -196,6 +198,15 @@ def stencil_adjoint(h, u0, kappa, dt, target, T, ckpt_every, grad_u0, grad_kappa
                                  _dev_ptr(grad_kappa, "grad_kappa", shape), ctypes.byref(loss),
                                  _stream(stream)))
     return loss.value
+
+
+def stencil_adjoint_vjp(h, u0, kappa, dt, T, ckpt_every, lambda_T, grad_u0, grad_kappa, stream=None):
+    """dL/du0 and dL/dkappa for a given dL/du^T (lambda_T); asynchronous."""
+    shape = u0.shape
+    _check(lib().stencil_adjoint_vjp(h, _dev_ptr(u0, "u0"), _dev_ptr(kappa, "kappa", shape), float(dt),
+                                     int(T), int(ckpt_every), _dev_ptr(lambda_T, "lambda_T", shape),
+                                     _dev_ptr(grad_u0, "grad_u0", shape),
+                                     _dev_ptr(grad_kappa, "grad_kappa", shape), _stream(stream)))
 
 
 def _batch_items(grids, alphas, steps):

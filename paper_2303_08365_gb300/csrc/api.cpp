@@ -275,21 +275,41 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
       return batch_enqueue(p->persist, s);
     }
   }
+  if (variant == kVariantTemporal && !temporal_supported(p->ndim, p->radius, Tb)) {
+    if (forced)
+      return fail(STENCIL_ERR_UNSUPPORTED,
+                  "temporal blocking covers radius-1 plans with Tb in {2, 4} (3D) or {2, 4, 8} (2D)");
+    variant = default_variant(p) == kVariantStream && stream_ok ? kVariantStream : kVariantDirect;
+  }
+  if (variant != kVariantTemporal) Tb = 1;
+  if (variant != kVariantDirect && variant != kVariantStream && variant != kVariantTemporal)
+    return fail(STENCIL_ERR_UNSUPPORTED, "variant %s is not available", stencil_variant_name(variant));
   const int sms = sm_count();
   const bool equal_box = p->shape == Shape::kBox && taps_all_equal(p->taps);
+  // the single-step kernel for the steps that do not fill a whole Tb block
+  const int single = stream_ok ? kVariantStream : kVariantDirect;
   double* a = d_grid;
   double* b = p->d_tmp;
-  for (int64_t t = 0; t < T; ++t) {
+  int64_t t = 0;
+  while (t < T) {
     cudaError_t e;
-    if (variant == kVariantStream && p->ndim == 3)
-      e = launch_stream3d(p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, p->d_status, sms, s);
-    else if (variant == kVariantStream)
-      e = launch_stream2d(p->shape, p->boundary, equal_box, p->g, p->taps, p->d_w, a, b, p->d_status,
-                          sms, s);
-    else
-      e = launch_direct(p->ndim, p->radius, p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, s);
+    int steps = 1;
+    if (variant == kVariantTemporal && T - t >= Tb) {
+      e = launch_temporal(p->ndim, p->shape, p->boundary, Tb, p->g, p->d_w, a, b, sms, s);
+      steps = Tb;
+    } else {
+      const int v = variant == kVariantTemporal ? single : variant;
+      if (v == kVariantStream && p->ndim == 3)
+        e = launch_stream3d(p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, p->d_status, sms, s);
+      else if (v == kVariantStream)
+        e = launch_stream2d(p->shape, p->boundary, equal_box, p->g, p->taps, p->d_w, a, b, p->d_status,
+                            sms, s);
+      else
+        e = launch_direct(p->ndim, p->radius, p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "launching the sweep");
     std::swap(a, b);
+    t += steps;
   }
   if (a != d_grid)
     CUDA_TRY(cudaMemcpyAsync(d_grid, a, (size_t)p->cells() * sizeof(double),
@@ -520,18 +540,20 @@ int stencil_run_host(stencil_plan p, double* h_grid, int64_t T, const double* h_
   return STENCIL_OK;
 }
 
-int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,
-                    const double* d_target, int64_t T, int ckpt_every, double* d_grad_u0,
-                    double* d_grad_kappa, double* h_loss, void* cuda_stream) {
-  g_err.clear();
-  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
-  if (!p->varcoef) return fail(STENCIL_ERR_ARG, "stencil_adjoint needs a variable-coefficient plan");
-  if (!d_u0 || !d_kappa || !d_target || !d_grad_u0 || !d_grad_kappa || !h_loss)
-    return fail(STENCIL_ERR_ARG, "NULL buffer");
+}  // extern "C"
+
+namespace {
+
+// The adjoint sweep shared by stencil_adjoint (loss form: lambda^T = u^T - target,
+// loss reduced on the device) and stencil_adjoint_vjp (lambda^T given).
+int adjoint_core(stencil_plan_s* p, const double* d_u0, const double* d_kappa, double dt,
+                 const double* d_target, const double* d_lambda_T, int64_t T, int ckpt_every,
+                 double* d_grad_u0, double* d_grad_kappa, double* h_loss, cudaStream_t s) {
+  if (!p->varcoef) return fail(STENCIL_ERR_ARG, "the adjoint needs a variable-coefficient plan");
+  if (!d_u0 || !d_kappa || !d_grad_u0 || !d_grad_kappa) return fail(STENCIL_ERR_ARG, "NULL buffer");
   if (!(dt > 0.0) || !is_finite(dt)) return fail(STENCIL_ERR_ARG, "dt must be finite and > 0");
   if (T < 0) return fail(STENCIL_ERR_ARG, "T must be >= 0");
   if (ckpt_every < 0) return fail(STENCIL_ERR_ARG, "ckpt_every must be >= 0");
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t n = (size_t)p->cells();
   int64_t c = ckpt_every > 0 ? ckpt_every : std::max<int64_t>(1, (int64_t)llround(std::sqrt((double)T)));
   if (T > 0 && c > T) c = T;
@@ -577,9 +599,13 @@ int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, d
     if (e != cudaSuccess) return cuda_fail(e, "launching the forward step");
     src = dst;
   }
-  // loss and lambda^T = u^T - target
-  e = launch_loss_residual((int64_t)n, src, d_target, lam, partials, nblocks, d_loss, s);
-  if (e != cudaSuccess) return cuda_fail(e, "launching the loss reduction");
+  if (d_target) {
+    // loss and lambda^T = u^T - target
+    e = launch_loss_residual((int64_t)n, src, d_target, lam, partials, nblocks, d_loss, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the loss reduction");
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(lam, d_lambda_T, bytes, cudaMemcpyDeviceToDevice, s), "copying lambda^T");
+  }
   CUDA_TRY(cudaMemsetAsync(gx, 0, 4 * bytes, s), "clearing the gradient accumulators");
   // reverse sweep, one segment [t0, t1) at a time
   const int64_t nseg = (T + c - 1) / c;
@@ -602,10 +628,36 @@ int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, d
   e = launch_adjoint_finalize(p->ndim, p->boundary, p->g, dt, gx, gy, gz, gg, d_grad_kappa, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the gradient finalisation");
   CUDA_TRY(cudaMemcpyAsync(d_grad_u0, lam, bytes, cudaMemcpyDeviceToDevice, s), "copying dL/du0");
-  CUDA_TRY(cudaMemcpyAsync(h_loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s),
-           "copying the loss");
-  CUDA_TRY(cudaStreamSynchronize(s), "waiting for the adjoint");
+  if (d_target) {
+    CUDA_TRY(cudaMemcpyAsync(h_loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s),
+             "copying the loss");
+    CUDA_TRY(cudaStreamSynchronize(s), "waiting for the adjoint");
+  }
   return STENCIL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,
+                    const double* d_target, int64_t T, int ckpt_every, double* d_grad_u0,
+                    double* d_grad_kappa, double* h_loss, void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
+  if (!d_target || !h_loss) return fail(STENCIL_ERR_ARG, "NULL target or loss");
+  return adjoint_core(p, d_u0, d_kappa, dt, d_target, nullptr, T, ckpt_every, d_grad_u0, d_grad_kappa,
+                      h_loss, (cudaStream_t)cuda_stream);
+}
+
+int stencil_adjoint_vjp(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,
+                        int64_t T, int ckpt_every, const double* d_lambda_T, double* d_grad_u0,
+                        double* d_grad_kappa, void* cuda_stream) {
+  g_err.clear();
+  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
+  if (!d_lambda_T) return fail(STENCIL_ERR_ARG, "d_lambda_T is NULL");
+  return adjoint_core(p, d_u0, d_kappa, dt, nullptr, d_lambda_T, T, ckpt_every, d_grad_u0, d_grad_kappa,
+                      nullptr, (cudaStream_t)cuda_stream);
 }
 
 int stencil_plan_status(stencil_plan p, void* cuda_stream) {
@@ -649,7 +701,8 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
   if (probe_steps < 1) return fail(STENCIL_ERR_ARG, "probe_steps must be >= 1");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   struct Cand { int Tb, variant; };
-  std::vector<Cand> cands = {{1, kVariantDirect}, {1, kVariantStream}, {1, kVariantPersistent}};
+  std::vector<Cand> cands = {{1, kVariantDirect}, {1, kVariantStream}, {1, kVariantPersistent},
+                             {2, kVariantTemporal}, {4, kVariantTemporal}, {8, kVariantTemporal}};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0), "creating an event");
   CUDA_TRY(cudaEventCreate(&e1), "creating an event");

@@ -31,16 +31,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Device-wide barrier for a cooperative launch (all blocks co-resident).
-// bar[0] counts arrivals, bar[1] is the generation.  Returns false when the
-// wait gave up or another block already reported an error.
+// bar[0] counts arrivals, bar[1] is the generation.  Thread 0 of each block
+// reads the generation, releases the block's writes (fence), arrives, and
+// spins with acquire loads until the last arriver bumps the generation.
+// The wait is bounded by wall time; returns false when it gave up or
+// another block already reported an error.
 __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, long long limit_ns,
                              int* status) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned int* vgen = bar + 1;
-    const unsigned int gen = *vgen;
+    unsigned int gen;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
     __threadfence();
     const unsigned int arrived = atomicAdd(bar, 1u);
     if (arrived == nblocks - 1) {
@@ -49,13 +52,17 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, long long 
       atomicAdd(bar + 1, 1u);
     } else {
       const unsigned long long t0 = global_ns();
-      while (*vgen == gen) {
-        if (*(volatile int*)status != 0) break;
-        if ((long long)(global_ns() - t0) > limit_ns) {
-          atomicCAS(status, 0, (int)-5 /* STENCIL_ERR_TIMEOUT */);
-          break;
+      for (unsigned int spin = 0;; ++spin) {
+        unsigned int g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+        if (g != gen) break;
+        if ((spin & 63) == 63) {
+          if (*(volatile int*)status != 0) break;
+          if ((long long)(global_ns() - t0) > limit_ns) {
+            atomicCAS(status, 0, (int)-5 /* STENCIL_ERR_TIMEOUT */);
+            break;
+          }
         }
-        __nanosleep(64);
       }
     }
     __threadfence();

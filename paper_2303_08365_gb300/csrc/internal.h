@@ -83,6 +83,13 @@ cudaError_t launch_stream2d(Shape shape, int boundary, bool equal, const Geom& g
                             const HostTaps& taps, const double* wdev, const double* src, double* dst,
                             int* status, int sms, cudaStream_t stream);
 
+// Temporal blocking: Tb fused steps per launch (3D: Tb in {2, 4}; 2D: Tb in
+// {2, 4, 8}), radius 1, any shape and boundary.
+bool temporal_supported(int ndim, int radius, int Tb);
+cudaError_t launch_temporal(int ndim, Shape shape, int boundary, int Tb, const Geom& g,
+                            const double* wdev, const double* src, double* dst, int sms,
+                            cudaStream_t stream);
+
 // Variable-coefficient diffusion: coefficient preparation, one forward step,
 // one fused adjoint step, gradient finalisation and the loss reduction.
 struct VarcoefBufs {

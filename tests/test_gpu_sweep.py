@@ -301,3 +301,62 @@ def test_persistent_single_grid_matches_direct_bitwise(st, shape, boundary, T):
     b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
     assert np.array_equal(a, b)
     assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
+
+
+TEMPORAL_CASES = [
+    # shape, boundary, kind, Tb, T
+    ((20, 40, 128), PERIODIC, "heat", 2, 7),
+    ((20, 40, 128), PERIODIC, "box_rand", 4, 9),
+    ((17, 37, 70), DIRICHLET, "heat", 4, 8),
+    ((17, 37, 70), DIRICHLET, "box_rand", 2, 5),
+    ((5, 3, 9), PERIODIC, "box_rand", 4, 6),      # axes shorter than the halo
+    ((50, 300), PERIODIC, "heat", 8, 19),
+    ((50, 300), DIRICHLET, "box_rand", 4, 12),
+    ((33, 61), DIRICHLET, "star_rand", 2, 3),
+    ((7, 5), PERIODIC, "box_eq", 8, 16),
+]
+
+
+@pytest.mark.parametrize("shape,boundary,kind,Tb,T", TEMPORAL_CASES)
+def test_temporal_blocking_matches_single_steps_bitwise(st, shape, boundary, kind, Tb, T):
+    """Tb fused steps per launch (overlapped tiles, Sec. 4.1's temporal tiling)
+    apply the same per-cell FMA chain as single steps: bitwise equal to the
+    direct kernel, remainder steps included, and within 1e-12 of the oracle."""
+    ndim = len(shape)
+    w = weights_for(kind, ndim, 1, 600 + Tb)
+    if kind == "box_eq":
+        w = synth.box_weights(ndim, 1.0 / 3 ** ndim)
+    u0 = synth.normal(12, shape)
+    a = gpu_run(st, u0, w, 1, boundary, T, Tb=Tb, variant=st.VARIANT_TEMPORAL)
+    b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
+
+
+def test_temporal_unsupported_tb_is_rejected(st):
+    import torch
+    p = st.Plan((8, 8, 8), 1, synth.heat_weights(3, 0.1), PERIODIC)
+    p.set_tuning(8, st.VARIANT_TEMPORAL)   # 3D supports Tb 2 and 4
+    g = torch.from_numpy(synth.uniform(1, (8, 8, 8))).cuda()
+    with pytest.raises(st.StencilError) as ei:
+        p.run(g, 8)
+    assert ei.value.code == st.ERR_UNSUPPORTED
+    p.close()
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(st):
+    import torch
+    shape = (24, 48, 128)
+    w = synth.heat_weights(3, 0.1)
+    p = st.Plan(shape, 1, w, PERIODIC)
+    scratch = torch.from_numpy(synth.uniform(3, shape)).cuda()
+    rate = p.autotune(scratch, 4)
+    assert rate > 0
+    tb, v = p.get_tuning()
+    assert (tb, v) in [(1, st.VARIANT_DIRECT), (1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
+                       (4, st.VARIANT_TEMPORAL)]
+    u0 = synth.uniform(4, shape)
+    g = torch.from_numpy(u0.copy()).cuda()
+    p.run(g, 10)
+    assert normwise_rel(g.cpu().numpy(), oracle.run(u0, w, 1, PERIODIC, 10, nthreads=0)) <= TOL
+    p.close()

@@ -117,3 +117,34 @@ def test_full_size_finite_differences(st):
     assert abs(fd_k - an_k) <= 1e-6 * abs(an_k)
     p.close()
     torch.cuda.synchronize()
+
+
+def test_autograd_function_matches_adjoint_and_oracle(st):
+    """StencilAdjointFn: backward of 0.5||u^T - target||^2 through torch
+    autograd equals the loss-form adjoint bitwise, and a linear functional
+    sum(w * u^T) gives the oracle's gradients."""
+    import torch
+    from paper_2303_08365_gb300.autograd import diffuse
+    shape = (12, 10, 14)
+    u0, kappa, target, dt = inputs(shape, 41)
+    T, ck = 23, 5
+    p = st.Plan.varcoef(shape, PERIODIC)
+    U = cuda(u0).requires_grad_(True)
+    K = cuda(kappa).requires_grad_(True)
+    TG = cuda(target)
+    uT = diffuse(U, K, p, dt, T, ck)
+    loss = 0.5 * ((uT - TG) ** 2).sum()
+    loss.backward()
+    ref_loss, gu, gk = p.adjoint(cuda(u0), cuda(kappa), dt, TG, T, ckpt_every=ck)
+    assert abs(float(loss) - ref_loss) <= 1e-12 * ref_loss
+    assert bool((U.grad == gu).all()) and bool((K.grad == gk).all())
+    # linear functional L = sum(w u^T): lambda^T = w; the oracle sees target = u^T - w
+    w = synth.normal(77, shape)
+    U.grad = None
+    K.grad = None
+    (diffuse(U, K, p, dt, T, ck) * cuda(w)).sum().backward()
+    uT_o = oracle.varcoef_run(u0, kappa, dt, PERIODIC, T)
+    _, rgu, rgk = oracle.varcoef_adjoint(u0, kappa, dt, uT_o - w, PERIODIC, T)
+    assert normwise_rel(U.grad.cpu().numpy(), rgu) <= TOL
+    assert normwise_rel(K.grad.cpu().numpy(), rgk) <= TOL
+    p.close()
