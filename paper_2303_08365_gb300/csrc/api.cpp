@@ -93,7 +93,7 @@ struct stencil_plan_s {
   double* d_adj = nullptr;     // adjoint scratch
   size_t adj_cells = 0;
   int* d_status = nullptr;     // device status word (bounded waits that gave up)
-  double* d_w = nullptr;       // weights in tap order, then kZeroSlots zeros
+  double* d_w = nullptr;       // weights in tap order, then kZeroSlots zeros and kOneSlots ones
   stencil_batch_s* persist = nullptr;  // one-item batch for the persistent 2D path
   const double* persist_grid = nullptr;
   int64_t persist_T = -1;
@@ -206,8 +206,9 @@ void choose(const stencil_plan_s* p, int& Tb, int& variant) {
 // Uploads the plan's weights (and the zero slots) to the device once.
 int ensure_weights(stencil_plan_s* p) {
   if (p->d_w) return STENCIL_OK;
-  std::vector<double> h(p->taps.n + kZeroSlots, 0.0);
+  std::vector<double> h(p->taps.n + kExtraSlots, 0.0);
   for (int k = 0; k < p->taps.n; ++k) h[k] = p->taps.w[k];
+  for (int k = 0; k < kOneSlots; ++k) h[p->taps.n + kZeroSlots + k] = 1.0;
   CUDA_TRY(cudaMalloc(&p->d_w, h.size() * sizeof(double)), "allocating the weight array");
   CUDA_TRY(cudaMemcpy(p->d_w, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice),
            "copying the weights");

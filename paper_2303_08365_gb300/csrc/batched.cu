@@ -42,14 +42,14 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, long long 
   __shared__ int ok;
   if (threadIdx.x == 0) {
     ok = 1;
-    unsigned int gen;
+    unsigned int gen, arrived;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
-    __threadfence();
-    const unsigned int arrived = atomicAdd(bar, 1u);
+    // arrival: releases this block's writes (ordered by the CTA barrier above)
+    // and, for the last arriver, acquires every other block's
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
     if (arrived == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
     } else {
       const unsigned long long t0 = global_ns();
       for (unsigned int spin = 0;; ++spin) {
@@ -65,7 +65,6 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, long long 
         }
       }
     }
-    __threadfence();
     if (*(volatile int*)status != 0) ok = 0;
   }
   __syncthreads();

@@ -59,7 +59,7 @@ struct HostTaps {
 // Launchers implemented in the .cu files.  Each returns a cudaError_t from
 // the launch (cudaSuccess when nothing failed) and enqueues on `stream`.
 // wdev: the plan's weights on the device (taps.n weights in tap order, then
-// kZeroSlots zeros; see taps.cuh).
+// zero and one slots; see taps.cuh).
 cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const Geom& g,
                           const HostTaps& taps, const double* wdev, const double* src, double* dst,
                           cudaStream_t stream);

@@ -59,7 +59,7 @@ struct Params2 {
   int strips, blocks;  // per strip: ceil(ny / 16) blocks
   long long work;      // strips * blocks
   int* status;
-  const double* wdev;  // NT weights then kZeroSlots zeros (device)
+  const double* wdev;  // NT weights, then the zero and one slots of taps.cuh (device)
 };
 
 __device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
@@ -129,7 +129,10 @@ __device__ __forceinline__ void pair_general(const Smem2& S, const RegWeights<NT
 }
 
 // Equal weights: rows q and q+1 (cells x, x+1 of each).  out[row][cell].
-__device__ __forceinline__ void quad_equal(const Smem2& S, double w, int q, int lane,
+// Every addition is an FMA against a register holding 1.0 (same rounding,
+// full FP64 rate); the common weight comes from the register copies W.w[k].
+template <int NT>
+__device__ __forceinline__ void quad_equal(const Smem2& S, const RegWeights<NT>& W, int q, int lane,
                                            double out[2][2]) {
   const int qm = (q - 1 + kRing) % kRing, q1 = (q + 1) % kRing, q2 = (q + 2) % kRing;
   const double2 a = *reinterpret_cast<const double2*>(&S.row[qm][2 * lane]);
@@ -137,27 +140,28 @@ __device__ __forceinline__ void quad_equal(const Smem2& S, double w, int q, int 
   const double2 c = *reinterpret_cast<const double2*>(&S.row[q1][2 * lane]);
   const double2 d = *reinterpret_cast<const double2*>(&S.row[q2][2 * lane]);
   // column sums of 3 rows for the lane's two columns, rows q and q+1
-  const double s0 = b.x + c.x, s1 = b.y + c.y;
-  const double V00 = a.x + s0, V01 = a.y + s1;   // row q, columns x, x+1
-  const double V10 = s0 + d.x, V11 = s1 + d.y;   // row q+1
+  const double s0 = W.add(b.x, c.x, 0), s1 = W.add(b.y, c.y, 1);
+  const double V00 = W.add(a.x, s0, 2), V01 = W.add(a.y, s1, 3);   // row q, columns x, x+1
+  const double V10 = W.add(s0, d.x, 0), V11 = W.add(s1, d.y, 1);   // row q+1
   // column sums at the strip-edge columns (lanes 0 and 31 only)
   double H0 = 0.0, H1 = 0.0;
   if (lane == 0 || lane == 31) {
     const int side = lane == 0 ? 0 : 1;
-    const double hs = S.halo[q][side] + S.halo[q1][side];
-    H0 = S.halo[qm][side] + hs;
-    H1 = hs + S.halo[q2][side];
+    const double hs = W.add(S.halo[q][side], S.halo[q1][side], 2);
+    H0 = W.add(S.halo[qm][side], hs, 3);
+    H1 = W.add(hs, S.halo[q2][side], 0);
   }
   // neighbours' column sums: x-1 from the lane below, x+2 from the lane above
   double L0 = __shfl_up_sync(0xffffffffu, V01, 1), L1 = __shfl_up_sync(0xffffffffu, V11, 1);
   double R0 = __shfl_down_sync(0xffffffffu, V00, 1), R1 = __shfl_down_sync(0xffffffffu, V10, 1);
   if (lane == 0) { L0 = H0; L1 = H1; }
   if (lane == 31) { R0 = H0; R1 = H1; }
-  const double wt0 = w * (V00 + V01), wt1 = w * (V10 + V11);
-  out[0][0] = fma(w, L0, wt0);
-  out[0][1] = fma(w, R0, wt0);
-  out[1][0] = fma(w, L1, wt1);
-  out[1][1] = fma(w, R1, wt1);
+  const double wt0 = fma(W.w[0], W.add(V00, V01, 2), W.z[0]);
+  const double wt1 = fma(W.w[1], W.add(V10, V11, 3), W.z[1]);
+  out[0][0] = fma(W.w[2], L0, wt0);
+  out[0][1] = fma(W.w[3], R0, wt0);
+  out[1][0] = fma(W.w[4], L1, wt1);
+  out[1][1] = fma(W.w[5], R1, wt1);
 }
 
 template <int NT, bool BOX, bool PERIODIC, bool EQUAL>
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant_
       if (EQUAL) {
         const int r = 2 * warp;  // rows r, r+1 of the block
         double out[2][2];
-        quad_equal(S, W.w[0], slot * kRB + r, lane, out);
+        quad_equal<NT>(S, W, slot * kRB + r, lane, out);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           const int y = blk * kRB + r + i;

@@ -18,6 +18,7 @@
 // and at the end dL/dkappa_i = (dt/2) * sum_{faces f of i} G_f + dt * Gg_i,
 // Gg_i collecting -u_i * lambda_i once per ghost face of cell i.
 #include "internal.h"
+#include "taps.cuh"
 
 namespace gbst {
 namespace {
@@ -125,6 +126,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const double* __restrict__ lam,
                                                  int ny, int nx, const double* __restrict__ zp) {
   CELL_COORDS
   lam_out[i] = apply_a<NDIM>(lam, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, sy, sz, __ldg(zp));
+  // differences as fma(a, 1, -b): the rounding of a - b at the FMA's full rate
+  const double one = __ldg(zp + kZeroSlots);
   const double ui = __ldg(u + i), li = __ldg(lam + i);
   const int cs[3] = {x, y, z};
   const int ns[3] = {nx, ny, nz};
@@ -135,8 +138,8 @@ __global__ void __launch_bounds__(256) k_adjoint(const double* __restrict__ lam,
   for (int d = 0; d < NDIM; ++d) {
     Nbr hi = nbr(cs[d], ns[d], +1, periodic, i, st[d]);
     if (hi.in) {
-      const double du = __ldg(u + hi.idx) - ui;
-      const double dl = li - __ldg(lam + hi.idx);
+      const double du = fma(__ldg(u + hi.idx), one, -ui);
+      const double dl = fma(li, one, -__ldg(lam + hi.idx));
       g[d][i] = fma(du, dl, g[d][i]);
     } else {
       ++ghosts;
