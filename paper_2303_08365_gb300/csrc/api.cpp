@@ -233,13 +233,15 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   rc = ensure_weights(p);
   if (rc) return rc;
   const bool stream_ok = p->ndim == 3
-                             ? stream3d_eligible(p->ndim, p->radius, p->boundary, p->g, d_grid, p->d_tmp)
+                             ? stream3d_eligible(p->ndim, p->radius, p->shape, p->boundary, p->g, d_grid,
+                                                 p->d_tmp)
                              : stream2d_eligible(p->ndim, p->radius, p->boundary, p->g, d_grid, p->d_tmp);
   if (variant == kVariantStream && !stream_ok) {
     if (forced)
       return fail(STENCIL_ERR_UNSUPPORTED,
                   "the streaming kernel needs a 2D or 3D radius-1 plan, even nx, 16-byte aligned "
-                  "buffers and, for periodic grids, nx %% 64 == 0 and ny %% 16 == 0");
+                  "buffers and, for periodic grids, nx %% 64 == 0 and ny a multiple of the tile "
+                  "height (16; 32 for the 3D star)");
     variant = kVariantDirect;
   }
   if (variant == kVariantPersistent) {

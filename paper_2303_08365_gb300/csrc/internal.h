@@ -66,8 +66,8 @@ cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const
 
 // 3D radius-1 streaming sweep (TMA-fed shared-memory plane ring).  Eligible
 // when nx is even, both buffers are 16-byte aligned and, for periodic grids,
-// nx % 64 == 0 and ny % 16 == 0.
-bool stream3d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
+// nx % 64 == 0 and ny a multiple of the tile height (32 star, 16 box).
+bool stream3d_eligible(int ndim, int radius, Shape shape, int boundary, const Geom& g, const void* a,
                        const void* b);
 cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const HostTaps& taps,
                             const double* wdev, const double* src, double* dst, int* status,

@@ -51,16 +51,25 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 namespace {
 
 constexpr int kTX = 64;
-constexpr int kTY = 16;
-constexpr int kRows = kTY + 2;
 constexpr int kSlots = 4;
 constexpr int kThreads = 256;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
-constexpr uint32_t kPlaneBytes = kRows * kTX * sizeof(double);
 
+// Tile height: the 7-point star takes 32 rows (4 per warp, 8 FMA chains per
+// thread, one barrier per 2048 cells); the 27-point box keeps 16 rows (its 27
+// register-resident weights leave no room for more chains).
+template <bool BOX>
+struct Tile {
+  static constexpr int TY = BOX ? 16 : 32;
+  static constexpr int Rows = TY + 2;
+  static constexpr int RowsPerWarp = TY / 8;
+  static constexpr uint32_t PlaneBytes = Rows * kTX * sizeof(double);
+};
+
+template <bool BOX>
 struct __align__(128) StreamSmem {
-  double plane[kSlots][kRows][kTX];  // TMA destination
-  double halo[kSlots][2][kRows];     // x-halo columns: [0] = x0-1, [1] = x0+64
+  double plane[kSlots][Tile<BOX>::Rows][kTX];  // TMA destination
+  double halo[kSlots][2][Tile<BOX>::Rows];     // x-halo columns: [0] = x0-1, [1] = x0+64
   uint64_t full[kSlots];
   int abort;
 };
@@ -68,7 +77,7 @@ struct __align__(128) StreamSmem {
 template <int NT>
 struct StreamParams {
   CUtensorMap map_row;   // box {64, 1, 1} over src
-  CUtensorMap map_main;  // box {64, 16, 1} over src
+  CUtensorMap map_main;  // box {64, TY, 1} over src
   const double* src;
   double* dst;
   int nz, ny, nx;
@@ -84,11 +93,12 @@ __device__ __forceinline__ int wrap_or_keep(int c, int n, bool periodic) {
 }
 
 // Loads (into a register) the x-halo value this thread is responsible for in
-// plane z, or 0 when the thread holds none.  Threads 0..35 cover the left
-// (x0-1) and right (x0+64) columns for rows y0-1 .. y0+16.
-template <bool PERIODIC>
+// plane z, or 0 when the thread holds none.  Threads 0 .. 2*Rows-1 cover the
+// left (x0-1) and right (x0+64) columns for rows y0-1 .. y0+TY.
+template <bool BOX, bool PERIODIC>
 __device__ __forceinline__ double load_halo(const double* __restrict__ src, int z, int y0, int x0,
                                             int nz, int ny, int nx) {
+  constexpr int kRows = Tile<BOX>::Rows;
   const int t = threadIdx.x;
   if (t >= 2 * kRows) return 0.0;
   const int side = t / kRows, r = t % kRows;
@@ -106,18 +116,21 @@ __device__ __forceinline__ double load_halo(const double* __restrict__ src, int 
   return __ldg(src + ((int64_t)zz * ny + y) * nx + x);
 }
 
-__device__ __forceinline__ void store_halo(StreamSmem& S, int slot, double v) {
+template <bool BOX>
+__device__ __forceinline__ void store_halo(StreamSmem<BOX>& S, int slot, double v) {
+  constexpr int kRows = Tile<BOX>::Rows;
   const int t = threadIdx.x;
   if (t < 2 * kRows) S.halo[slot][t / kRows][t % kRows] = v;
 }
 
-template <int NT, bool PERIODIC>
-__device__ __forceinline__ void issue_plane(StreamSmem& S, const StreamParams<NT>& P, int slot,
+template <int NT, bool BOX, bool PERIODIC>
+__device__ __forceinline__ void issue_plane(StreamSmem<BOX>& S, const StreamParams<NT>& P, int slot,
                                             int z, int y0, int x0) {
+  constexpr int kRows = Tile<BOX>::Rows;
   const int zc = wrap_or_keep(z, P.nz, PERIODIC);
   const int ya = wrap_or_keep(y0 - 1, P.ny, PERIODIC);
-  const int yb = wrap_or_keep(y0 + kTY, P.ny, PERIODIC);
-  mbar_arrive_expect_tx(&S.full[slot], kPlaneBytes);
+  const int yb = wrap_or_keep(y0 + Tile<BOX>::TY, P.ny, PERIODIC);
+  mbar_arrive_expect_tx(&S.full[slot], Tile<BOX>::PlaneBytes);
   tma_load_3d(&S.plane[slot][0][0], &P.map_row, x0, ya, zc, &S.full[slot]);
   tma_load_3d(&S.plane[slot][1][0], &P.map_main, x0, y0, zc, &S.full[slot]);
   tma_load_3d(&S.plane[slot][kRows - 1][0], &P.map_row, x0, yb, zc, &S.full[slot]);
@@ -134,7 +147,7 @@ __device__ __forceinline__ constexpr int tap_index(int dz, int dy, int dx) {
 // Two adjacent cells (x, x+1) of tile row ry in the plane whose neighbours are
 // in slots (sm, s0, sp).
 template <int NT, bool BOX>
-__device__ __forceinline__ void compute_pair(const StreamSmem& S, const RegWeights<NT>& W, int sm,
+__device__ __forceinline__ void compute_pair(const StreamSmem<BOX>& S, const RegWeights<NT>& W, int sm,
                                              int s0, int sp, int ry, int lane, int c0, double& a0,
                                              double& a1) {
   const int slots[3] = {sm, s0, sp};
@@ -168,7 +181,12 @@ __device__ __forceinline__ void compute_pair(const StreamSmem& S, const RegWeigh
 
 template <int NT, bool BOX, bool PERIODIC>
 __global__ void __launch_bounds__(kThreads, 2) k_stream3d(const __grid_constant__ StreamParams<NT> P) {
-  __shared__ StreamSmem S;
+  constexpr int kTY = Tile<BOX>::TY;
+  // dynamic shared memory (the 32-row star tile needs 70 KB); the kernel has
+  // no static shared memory, so the dynamic window starts at the (1 KB
+  // aligned) base of the CTA's shared memory, as the TMA destinations need
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  StreamSmem<BOX>& S = *reinterpret_cast<StreamSmem<BOX>*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   RegWeights<NT> W;
   W.load(P.wdev);
@@ -197,13 +215,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream3d(const __grid_constant_
     seq += nplanes;
     if (threadIdx.x == 0) {
       for (int j = 0; j < kSlots && j < nplanes; ++j)
-        issue_plane<NT, PERIODIC>(S, P, (base + j) % kSlots, za - 1 + j, y0, x0);
+        issue_plane<NT, BOX, PERIODIC>(S, P, (base + j) % kSlots, za - 1 + j, y0, x0);
     }
     for (int j = 0; j < 3; ++j)
-      store_halo(S, (base + j) % kSlots,
-                 load_halo<PERIODIC>(P.src, za - 1 + j, y0, x0, P.nz, P.ny, P.nx));
+      store_halo<BOX>(S, (base + j) % kSlots,
+                      load_halo<BOX, PERIODIC>(P.src, za - 1 + j, y0, x0, P.nz, P.ny, P.nx));
     double halo_next = 0.0;
-    if (nplanes > 3) halo_next = load_halo<PERIODIC>(P.src, za + 2, y0, x0, P.nz, P.ny, P.nx);
+    if (nplanes > 3) halo_next = load_halo<BOX, PERIODIC>(P.src, za + 2, y0, x0, P.nz, P.ny, P.nx);
     __syncthreads();
     int issued = min(kSlots, nplanes) - 1;  // highest plane index issued so far
     for (int k = 1; k <= nplanes - 2; ++k) {
@@ -219,16 +237,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream3d(const __grid_constant_
       const int sm = (base + k - 1) % kSlots, s0 = (base + k) % kSlots, sp = (base + k + 1) % kSlots;
       const int z = za + k - 1;
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < Tile<BOX>::RowsPerWarp; ++r) {
         const int ry = warp + 8 * r;
         double a0 = 0.0, a1 = 0.0;
-        compute_pair<NT, BOX>(S, W, sm, s0, sp, ry, lane, 2 * r, a0, a1);
+        compute_pair<NT, BOX>(S, W, sm, s0, sp, ry, lane, (2 * r) & 3, a0, a1);
         const int y = y0 + ry, x = x0 + 2 * lane;
         if (y < P.ny && x < P.nx) st_global_v2(P.dst + ((int64_t)z * P.ny + y) * P.nx + x, a0, a1);
       }
-      if (k + 2 <= nplanes - 1) store_halo(S, (base + k + 2) % kSlots, halo_next);
+      if (k + 2 <= nplanes - 1) store_halo<BOX>(S, (base + k + 2) % kSlots, halo_next);
       if (k + 3 <= nplanes - 1)
-        halo_next = load_halo<PERIODIC>(P.src, za + k + 2, y0, x0, P.nz, P.ny, P.nx);
+        halo_next = load_halo<BOX, PERIODIC>(P.src, za + k + 2, y0, x0, P.nz, P.ny, P.nx);
       __syncthreads();
       if (S.abort) {
         // a wait gave up: let the copies still in flight land (bounded), then leave
@@ -240,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream3d(const __grid_constant_
       if (k + 3 <= nplanes - 1) {
         if (threadIdx.x == 0) {
           fence_proxy_async_smem();
-          issue_plane<NT, PERIODIC>(S, P, (base + k + 3) % kSlots, za + k + 2, y0, x0);
+          issue_plane<NT, BOX, PERIODIC>(S, P, (base + k + 3) % kSlots, za + k + 2, y0, x0);
         }
         issued = k + 3;
       }
@@ -261,12 +279,19 @@ bool encode_3d(CUtensorMap* map, const double* base, int nz, int ny, int nx, int
   return r == CUDA_SUCCESS;
 }
 
+template <bool BOX>
+constexpr size_t smem_bytes() { return sizeof(StreamSmem<BOX>); }
+
 template <int NT, bool BOX, bool PERIODIC>
 int occupancy() {
   static int n = -1;
   if (n < 0) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream3d<NT, BOX, PERIODIC>, kThreads, 0) !=
-        cudaSuccess)
+    cudaFuncSetAttribute(k_stream3d<NT, BOX, PERIODIC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaFuncSetAttribute(k_stream3d<NT, BOX, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<BOX>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream3d<NT, BOX, PERIODIC>, kThreads,
+                                                      smem_bytes<BOX>()) != cudaSuccess)
       n = 0;
   }
   return n;
@@ -275,6 +300,7 @@ int occupancy() {
 template <int NT, bool BOX, bool PERIODIC>
 cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, double* dst, int* status,
                      int sms, cudaStream_t stream) {
+  constexpr int kTY = Tile<BOX>::TY;
   StreamParams<NT> P;
   if (!encode_3d(&P.map_row, src, g.nz, g.ny, g.nx, 1) ||
       !encode_3d(&P.map_main, src, g.nz, g.ny, g.nx, kTY))
@@ -293,19 +319,20 @@ cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, doubl
   if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)sms * occ;
   if (grid > P.work) grid = P.work;
-  k_stream3d<NT, BOX, PERIODIC><<<(unsigned)grid, kThreads, 0, stream>>>(P);
+  k_stream3d<NT, BOX, PERIODIC><<<(unsigned)grid, kThreads, smem_bytes<BOX>(), stream>>>(P);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool stream3d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
+bool stream3d_eligible(int ndim, int radius, Shape shape, int boundary, const Geom& g, const void* a,
                        const void* b) {
   if (ndim != 3 || radius != 1) return false;
   if (g.nx % 2 != 0) return false;                        // TMA: row pitch multiple of 16 bytes
   if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return false;  // TMA base and 16-byte stores
-  if (boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % kTY != 0)) return false;
+  const int ty = shape == Shape::kBox ? Tile<true>::TY : Tile<false>::TY;
+  if (boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % ty != 0)) return false;
   return tensor_map_encoder() != nullptr;
 }
 

@@ -221,7 +221,7 @@ def test_fp64_peak_is_plausible(st):
 
 STREAM_CASES = [
     # shape, boundary, kind
-    ((40, 48, 128), PERIODIC, "heat"),
+    ((40, 64, 128), PERIODIC, "heat"),
     ((40, 48, 128), PERIODIC, "box_rand"),
     ((13, 37, 70), DIRICHLET, "heat"),
     ((13, 37, 70), DIRICHLET, "box_rand"),
