@@ -93,6 +93,7 @@ struct stencil_plan_s {
   double* d_adj = nullptr;     // adjoint scratch
   size_t adj_cells = 0;
   int* d_status = nullptr;     // device status word (bounded waits that gave up)
+  unsigned int* d_ctl = nullptr;  // barrier words of the persistent temporal kernel
   double* d_w = nullptr;       // weights in tap order, then kZeroSlots zeros and kOneSlots ones
   stencil_batch_s* persist = nullptr;  // one-item batch for the persistent 2D path
   const double* persist_grid = nullptr;
@@ -173,11 +174,17 @@ int sm_count() {
   return n;
 }
 
-// The kernel a constant-weight plan uses when nothing was tuned or forced.
-int default_variant(const stencil_plan_s* p) {
+// The kernel (and Tb) a constant-weight plan uses when nothing was tuned or
+// forced.  Small 2D grids are latency-bound: they run as one persistent
+// launch with Tb steps in shared memory between device-wide barriers.
+int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
+  if (Tb) *Tb = 1;
   if (p->ndim == 3 && p->radius == 1) return kVariantStream;
   if (p->ndim == 2 && p->radius == 1) {
-    if (p->shape == Shape::kStar && p->cells() <= ((int64_t)1 << 20)) return kVariantPersistent;
+    if (p->cells() <= ((int64_t)1 << 20)) {
+      if (Tb) *Tb = p->cells() <= ((int64_t)1 << 17) ? 8 : 4;
+      return kVariantPersistent;
+    }
     return kVariantStream;
   }
   return kVariantDirect;
@@ -199,8 +206,7 @@ void choose(const stencil_plan_s* p, int& Tb, int& variant) {
     variant = p->tuned_variant;
     return;
   }
-  Tb = 1;
-  variant = default_variant(p);
+  variant = default_variant(p, &Tb);
 }
 
 // Uploads the plan's weights (and the zero slots) to the device once.
@@ -243,6 +249,31 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
                   "buffers and, for periodic grids, nx %% 64 == 0 and ny a multiple of the tile "
                   "height (16; 32 for the 3D star)");
     variant = kVariantDirect;
+  }
+  if (variant == kVariantPersistent && Tb > 1) {
+    // Tb steps in shared memory per device-wide barrier (2D radius 1, star or box)
+    if (p->ndim != 2 || p->radius != 1 || (p->taps.n != 5 && p->taps.n != 9) || Tb > 8) {
+      if (forced)
+        return fail(STENCIL_ERR_UNSUPPORTED, "the persistent temporal kernel covers 2D radius-1 plans");
+      variant = kVariantDirect;
+      Tb = 1;
+    } else {
+      if (!p->d_ctl) CUDA_TRY(cudaMalloc(&p->d_ctl, 4 * sizeof(unsigned int)), "allocating barrier words");
+      CUDA_TRY(cudaMemsetAsync(p->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing barrier words");
+      PersistTbLaunch L;
+      L.a = d_grid;
+      L.b = p->d_tmp;
+      L.ny = p->g.ny;
+      L.nx = p->g.nx;
+      L.T = T;
+      L.wdev = p->d_w;
+      L.barrier = p->d_ctl;
+      L.status = p->d_status;
+      L.spin_limit = 2000000000LL;
+      cudaError_t e = launch_persist_tb(p->shape, p->boundary, Tb, L, sm_count(), s);
+      if (e != cudaSuccess) return cuda_fail(e, "launching the persistent temporal kernel");
+      return STENCIL_OK;
+    }
   }
   if (variant == kVariantPersistent) {
     if (!persistent_eligible(p) || T > (1 << 30)) {
@@ -498,6 +529,7 @@ void stencil_destroy(stencil_plan p) {
   cudaFree(p->d_coef);
   cudaFree(p->d_adj);
   cudaFree(p->d_status);
+  cudaFree(p->d_ctl);
   cudaFree(p->d_w);
   if (p->persist) {
     p->persist->d_partner = nullptr;  // the plan's own ping-pong buffer
@@ -705,6 +737,7 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   struct Cand { int Tb, variant; };
   std::vector<Cand> cands = {{1, kVariantDirect}, {1, kVariantStream}, {1, kVariantPersistent},
+                             {4, kVariantPersistent}, {8, kVariantPersistent},
                              {2, kVariantTemporal}, {4, kVariantTemporal}, {8, kVariantTemporal}};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0), "creating an event");

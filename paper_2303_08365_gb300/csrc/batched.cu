@@ -16,6 +16,7 @@
 // product is a plain multiply), so a batched grid is bitwise equal to the
 // same grid advanced by stencil_run.
 #include "internal.h"
+#include "taps.cuh"
 
 namespace gbst {
 namespace {
@@ -147,6 +148,162 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchLaunch L) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Persistent temporal blocking for one small 2D grid: every CTA owns tiles of
+// kPTH x kPTW cells, loads each with a halo of Tb cells, advances it Tb steps
+// in shared memory (the region shrinks by one cell per side per step: the
+// overlapped-tile recompute of the paper's temporal tiling, Sec. 4.1), writes
+// the tile back, and only then meets the other CTAs at the device-wide
+// barrier -- one barrier per Tb steps instead of one per step.  Every cell
+// applies the lexicographic tap chain of the single-step kernels (bitwise
+// equal results).  Loads after a barrier bypass L1 (other SMs wrote them).
+constexpr int kPTH = 16, kPTW = 32;
+constexpr int kPThreads = 512;  // one CTA per SM on small grids: 16 warps to hide FP64 latency
+
+template <int NT, bool BOX, bool PERIODIC, int TB>
+__device__ __forceinline__ double ptb_cell(const RegWeights<NT>& W, const double* in, int ry, int rx,
+                                           int y, int x, int ny, int nx, int chain) {
+  constexpr int RW = kPTW + 2 * TB;
+  double acc = 0.0;
+  if (PERIODIC || ((unsigned)y < (unsigned)ny && (unsigned)x < (unsigned)nx)) {
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!BOX && dy != 0 && dx != 0) continue;
+        const int k = BOX ? (dy + 1) * 3 + (dx + 1) : (dy < 0 ? 0 : dy > 0 ? 4 : 2 + dx);
+        W.tap(acc, k, in[(ry + dy) * RW + rx + dx], chain);
+      }
+  }
+  return acc;
+}
+
+template <int NT, bool BOX, bool PERIODIC, int TB>
+__global__ void __launch_bounds__(kPThreads) k_persist_tb(PersistTbLaunch L) {
+  constexpr int RH = kPTH + 2 * TB, RW = kPTW + 2 * TB;
+  __shared__ double buf[2][RH * RW];
+  RegWeights<NT> W;
+  W.load(L.wdev);
+  const unsigned int G = gridDim.x;
+  const int ny = L.ny, nx = L.nx;
+  const int tiles_x = (nx + kPTW - 1) / kPTW, tiles_y = (ny + kPTH - 1) / kPTH;
+  const int ntiles = tiles_x * tiles_y;
+  double* src = L.a;
+  double* dst = L.b;
+  for (long long t0 = 0; t0 < L.T; t0 += TB) {
+    const int tb = (int)(L.T - t0 < TB ? L.T - t0 : TB);
+    for (int j = blockIdx.x; j < ntiles; j += G) {
+      const int y0 = (j / tiles_x) * kPTH, x0 = (j % tiles_x) * kPTW;
+      // load the tile with a halo of tb cells (region offset TB - tb inside the buffer)
+      const int off = TB - tb;
+      const int lh = kPTH + 2 * tb, lw = kPTW + 2 * tb;
+      for (int c = threadIdx.x; c < lh * lw; c += kPThreads) {
+        const int ry = c / lw, rx = c % lw;
+        int y = y0 - tb + ry, x = x0 - tb + rx;
+        double v = 0.0;
+        if (PERIODIC) {
+          y %= ny; y += y < 0 ? ny : 0;
+          x %= nx; x += x < 0 ? nx : 0;
+          v = __ldcg(src + (int64_t)y * nx + x);
+        } else if ((unsigned)y < (unsigned)ny && (unsigned)x < (unsigned)nx) {
+          v = __ldcg(src + (int64_t)y * nx + x);
+        }
+        buf[0][(off + ry) * RW + off + rx] = v;
+      }
+      __syncthreads();
+      int cur = 0;
+      for (int s = 1; s <= tb; ++s) {
+        const int m = tb - s;  // remaining halo after this step
+        const int h = kPTH + 2 * m, w = kPTW + 2 * m;
+        const double* in = buf[cur];
+        double* out = buf[cur ^ 1];
+        // two cells per thread per pass: two independent FMA chains in flight
+        for (int c = threadIdx.x; c < h * w; c += 2 * kPThreads) {
+          const int c2 = c + kPThreads;
+          const int ry = TB - m + c / w, rx = TB - m + c % w;  // buffer coordinates
+          const int ry2 = TB - m + c2 / w, rx2 = TB - m + c2 % w;
+          const double v1 = ptb_cell<NT, BOX, PERIODIC, TB>(W, in, ry, rx, y0 - TB + ry, x0 - TB + rx, ny,
+                                                           nx, 0);
+          double v2 = 0.0;
+          if (c2 < h * w)
+            v2 = ptb_cell<NT, BOX, PERIODIC, TB>(W, in, ry2, rx2, y0 - TB + ry2, x0 - TB + rx2, ny, nx, 1);
+          out[ry * RW + rx] = v1;
+          if (c2 < h * w) out[ry2 * RW + rx2] = v2;
+        }
+        __syncthreads();
+        cur ^= 1;
+      }
+      // the tile itself back to global memory
+      for (int c = threadIdx.x; c < kPTH * kPTW; c += kPThreads) {
+        const int ry = c / kPTW, rx = c % kPTW;
+        const int y = y0 + ry, x = x0 + rx;
+        if (y < ny && x < nx) dst[(int64_t)y * nx + x] = buf[cur][(TB + ry) * RW + TB + rx];
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(L.barrier, G, L.spin_limit, L.status)) return;
+    double* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  // the result is in `src`; if that is the partner buffer, copy it back
+  if (src != L.a) {
+    for (int j = blockIdx.x; j < ntiles; j += G) {
+      const int y0 = (j / tiles_x) * kPTH, x0 = (j % tiles_x) * kPTW;
+      for (int c = threadIdx.x; c < kPTH * kPTW; c += kPThreads) {
+        const int y = y0 + c / kPTW, x = x0 + c % kPTW;
+        if (y < ny && x < nx) L.a[(int64_t)y * nx + x] = __ldcg(src + (int64_t)y * nx + x);
+      }
+    }
+  }
+}
+
+template <int NT, bool BOX, bool PERIODIC, int TB>
+cudaError_t launch_ptb(const PersistTbLaunch& L, int sms, cudaStream_t stream) {
+  auto kern = k_persist_tb<NT, BOX, PERIODIC, TB>;
+  static int occ = -1;
+  if (occ < 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPThreads, 0) != cudaSuccess)
+    occ = 0;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const int tiles = ((L.nx + kPTW - 1) / kPTW) * ((L.ny + kPTH - 1) / kPTH);
+  int grid = sms * (occ < 2 ? occ : 2);
+  if (tiles < grid) grid = tiles;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kPThreads, 1, 1);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, L);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+template <int NT, bool BOX, bool PERIODIC>
+cudaError_t ptb_by_tb(int Tb, const PersistTbLaunch& L, int sms, cudaStream_t stream) {
+  switch (Tb) {
+    case 2: return launch_ptb<NT, BOX, PERIODIC, 2>(L, sms, stream);
+    case 4: return launch_ptb<NT, BOX, PERIODIC, 4>(L, sms, stream);
+    case 8: return launch_ptb<NT, BOX, PERIODIC, 8>(L, sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_persist_tb(Shape shape, int boundary, int Tb, const PersistTbLaunch& L, int sms,
+                              cudaStream_t stream) {
+  const bool per = boundary == kPeriodic;
+  if (shape == Shape::kBox)
+    return per ? ptb_by_tb<9, true, true>(Tb, L, sms, stream) : ptb_by_tb<9, true, false>(Tb, L, sms, stream);
+  return per ? ptb_by_tb<5, false, true>(Tb, L, sms, stream) : ptb_by_tb<5, false, false>(Tb, L, sms, stream);
+}
+
+namespace {
 }  // namespace
 
 int batched_block_size() { return kThreads; }

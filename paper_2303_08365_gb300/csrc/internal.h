@@ -152,6 +152,21 @@ int batched_block_size();
 int batched_tile_h();
 int batched_tile_w();
 
+// Persistent temporal blocking for one small 2D grid (radius 1, star or box):
+// Tb in {2, 4, 8} steps per device-wide barrier.
+struct PersistTbLaunch {
+  double* a;             // the caller's grid
+  double* b;             // partner buffer
+  int ny, nx;
+  long long T;
+  const double* wdev;    // weights, then the zero and one slots
+  unsigned int* barrier; // two words, zero before the launch
+  int* status;
+  long long spin_limit;  // ns
+};
+cudaError_t launch_persist_tb(Shape shape, int boundary, int Tb, const PersistTbLaunch& L, int sms,
+                              cudaStream_t stream);
+
 // FP64 peak microbenchmark: `iters` rounds of 8 independent DFMA chains in
 // blocks x 256 threads; out receives one double per thread.
 cudaError_t launch_fp64_peak(int blocks, int iters, double* out, cudaStream_t stream);

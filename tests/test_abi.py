@@ -60,7 +60,7 @@ def test_create_rejects_bad_arguments_on_host(stencil):
 
 def test_plan_lifecycle_and_tuning_checks_on_host(stencil):
     h = stencil.stencil_create((8, 9), 1, np.ones(9) / 9, stencil.PERIODIC)
-    assert stencil.stencil_get_tuning(h) == (1, stencil.VARIANT_STREAM)
+    assert stencil.stencil_get_tuning(h) == (8, stencil.VARIANT_PERSISTENT)  # small 2D grid
     with pytest.raises(stencil.StencilError):
         stencil.stencil_set_tuning(h, 3, 0)
     with pytest.raises(stencil.StencilError):
@@ -68,11 +68,14 @@ def test_plan_lifecycle_and_tuning_checks_on_host(stencil):
     stencil.stencil_set_tuning(h, 2, stencil.VARIANT_TEMPORAL)
     assert stencil.stencil_get_tuning(h) == (2, stencil.VARIANT_TEMPORAL)
     stencil.stencil_set_tuning(h, 0, 0)
-    assert stencil.stencil_get_tuning(h) == (1, stencil.VARIANT_STREAM)
-    small = stencil.stencil_create((64, 64), 1, np.array([0, .1, 0, .1, .6, .1, 0, .1, 0]),
-                                   stencil.DIRICHLET_ZERO)
-    assert stencil.stencil_get_tuning(small) == (1, stencil.VARIANT_PERSISTENT)
-    stencil.stencil_destroy(small)
+    assert stencil.stencil_get_tuning(h) == (8, stencil.VARIANT_PERSISTENT)
+    mid = stencil.stencil_create((1024, 1024), 1, np.array([0, .1, 0, .1, .6, .1, 0, .1, 0]),
+                                 stencil.DIRICHLET_ZERO)
+    assert stencil.stencil_get_tuning(mid) == (4, stencil.VARIANT_PERSISTENT)
+    stencil.stencil_destroy(mid)
+    big = stencil.stencil_create((2048, 1024), 1, np.ones(9) / 9, stencil.PERIODIC)
+    assert stencil.stencil_get_tuning(big) == (1, stencil.VARIANT_STREAM)
+    stencil.stencil_destroy(big)
     r2 = stencil.stencil_create((9, 10, 11), 2, np.ones(125) / 125, stencil.PERIODIC)
     assert stencil.stencil_get_tuning(r2) == (1, stencil.VARIANT_DIRECT)
     stencil.stencil_destroy(r2)

@@ -360,3 +360,19 @@ def test_autotune_picks_a_candidate_and_keeps_results(st):
     p.run(g, 10)
     assert normwise_rel(g.cpu().numpy(), oracle.run(u0, w, 1, PERIODIC, 10, nthreads=0)) <= TOL
     p.close()
+
+
+@pytest.mark.parametrize("shape,boundary,kind,Tb,T", [((256, 256), DIRICHLET, "heat", 8, 100),
+                                                      ((37, 53), DIRICHLET, "star_rand", 4, 17),
+                                                      ((48, 64), PERIODIC, "box_rand", 8, 21),
+                                                      ((5, 3), PERIODIC, "heat", 8, 9),
+                                                      ((300, 257), DIRICHLET, "box_eq", 2, 7)])
+def test_persistent_temporal_matches_single_steps_bitwise(st, shape, boundary, kind, Tb, T):
+    """Tb steps in shared memory between device-wide barriers: bitwise equal to
+    single steps (same per-cell chain), remainder blocks included."""
+    w = weights_for(kind, 2, 1, 700 + Tb) if kind != "box_eq" else synth.box_weights(2, 1.0 / 9.0)
+    u0 = synth.uniform(13, shape)
+    a = gpu_run(st, u0, w, 1, boundary, T, Tb=Tb, variant=st.VARIANT_PERSISTENT)
+    b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
