@@ -187,6 +187,7 @@ int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
     }
     return kVariantStream;
   }
+  if (p->ndim == 2 && p->radius == 2) return kVariantStream;
   return kVariantDirect;
 }
 
@@ -336,8 +337,8 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
       if (v == kVariantStream && p->ndim == 3)
         e = launch_stream3d(p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, p->d_status, sms, s);
       else if (v == kVariantStream)
-        e = launch_stream2d(p->shape, p->boundary, equal_box, p->g, p->taps, p->d_w, a, b, p->d_status,
-                            sms, s);
+        e = launch_stream2d(p->shape, p->radius, p->boundary, equal_box && p->radius == 1, p->g, p->taps,
+                            p->d_w, a, b, p->d_status, sms, s);
       else
         e = launch_direct(p->ndim, p->radius, p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, s);
     }

@@ -73,13 +73,13 @@ cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const Host
                             const double* wdev, const double* src, double* dst, int* status,
                             int sms, cudaStream_t stream);
 
-// 2D radius-1 streaming sweep (TMA-fed ring of 16-row blocks).  Same
+// 2D radius-1 or radius-2 streaming sweep (TMA-fed ring of 16-row blocks).  Same
 // eligibility rules with ny % 16 == 0 for periodic grids.  `equal` selects
 // the shared-partial-sum form for a box whose weights are all equal.
 bool stream2d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
                        const void* b);
 bool taps_all_equal(const HostTaps& t);
-cudaError_t launch_stream2d(Shape shape, int boundary, bool equal, const Geom& g,
+cudaError_t launch_stream2d(Shape shape, int radius, int boundary, bool equal, const Geom& g,
                             const HostTaps& taps, const double* wdev, const double* src, double* dst,
                             int* status, int sms, cudaStream_t stream);
 

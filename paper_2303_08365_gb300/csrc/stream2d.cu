@@ -43,9 +43,10 @@ constexpr int kThreads = 256;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 constexpr uint32_t kBlockBytes = kRB * kTX * sizeof(double);
 
+template <int R>
 struct __align__(128) Smem2 {
   double row[kRing][kTX];    // TMA destination (block s = rows 16s .. 16s+15)
-  double halo[kRing][2];     // columns x0-1 and x0+64 of each ring row
+  double halo[kRing][2 * R]; // columns x0-R .. x0-1 and x0+64 .. x0+63+R of each ring row
   uint64_t full[kSlots];
   int abort;
 };
@@ -64,14 +65,15 @@ struct Params2 {
 
 __device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
 
-// Thread t < 32 loads the halo value (row t % 16 of block `blk`, side t / 16).
-template <bool PERIODIC>
+// Thread t < 2R*16 loads one halo value: row t % 16 of block `blk`, halo
+// column h = t / 16 (0 .. R-1: x0-R+h; R .. 2R-1: x0+64+h-R).
+template <int R, bool PERIODIC>
 __device__ __forceinline__ double load_halo2(const double* __restrict__ src, int blk, int x0, int ny,
                                              int nx) {
   const int t = threadIdx.x;
-  if (t >= 2 * kRB) return 0.0;
-  const int side = t / kRB, r = t % kRB;
-  int x = side ? x0 + kTX : x0 - 1;
+  if (t >= 2 * R * kRB) return 0.0;
+  const int h = t / kRB, r = t % kRB;
+  int x = h < R ? x0 - R + h : x0 + kTX + (h - R);
   int y = blk * kRB + r;
   if (PERIODIC) {
     x = wrapc(x, nx);
@@ -82,13 +84,14 @@ __device__ __forceinline__ double load_halo2(const double* __restrict__ src, int
   return __ldg(src + (int64_t)y * nx + x);
 }
 
-__device__ __forceinline__ void store_halo2(Smem2& S, int slot, double v) {
+template <int R>
+__device__ __forceinline__ void store_halo2(Smem2<R>& S, int slot, double v) {
   const int t = threadIdx.x;
-  if (t < 2 * kRB) S.halo[slot * kRB + t % kRB][t / kRB] = v;
+  if (t < 2 * R * kRB) S.halo[slot * kRB + t % kRB][t / kRB] = v;
 }
 
-template <int NT, bool PERIODIC>
-__device__ __forceinline__ void issue_block(Smem2& S, const Params2<NT>& P, int slot, int blk,
+template <int NT, int R, bool PERIODIC>
+__device__ __forceinline__ void issue_block(Smem2<R>& S, const Params2<NT>& P, int slot, int blk,
                                             int x0) {
   int y = blk * kRB;
   if (PERIODIC) y = wrapc(y, P.ny);  // ny % 16 == 0: a block never straddles the edge
@@ -96,34 +99,47 @@ __device__ __forceinline__ void issue_block(Smem2& S, const Params2<NT>& P, int 
   tma_load_2d(&S.row[slot * kRB][0], &P.map, x0, y, &S.full[slot]);
 }
 
-template <bool BOX>
+// Position of offset (dy, dx) in the lexicographic tap list of the shape
+// class of radius R (box: all (2R+1)^2; star: the 4R+1 axis offsets).
+template <bool BOX, int R>
 __device__ __forceinline__ constexpr int tap_index2(int dy, int dx) {
-  if (BOX) return (dy + 1) * 3 + (dx + 1);
-  return dy < 0 ? 0 : dy > 0 ? 4 : 2 + dx;
+  if (BOX) return (dy + R) * (2 * R + 1) + (dx + R);
+  return dy < 0 ? dy + R : dy > 0 ? 3 * R + dy : 2 * R + dx;
 }
 
-// General weights: cells (x, x+1) of ring row q.
-template <int NT, bool BOX>
-__device__ __forceinline__ void pair_general(const Smem2& S, const RegWeights<NT>& W, int q, int lane,
+// General weights: cells (x, x+1) of ring row q.  A row's values x-R ..
+// x+1+R come from the lane's own pair and the adjacent lanes' pairs by
+// shuffle (each lane holds two columns, so R <= 2 reaches one lane away);
+// the warp's edge lanes take the halo columns instead.
+template <int NT, bool BOX, int R>
+__device__ __forceinline__ void pair_general(const Smem2<R>& S, const RegWeights<NT>& W, int q, int lane,
                                              int c0, double& a0, double& a1) {
 #pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
+  for (int dy = -R; dy <= R; ++dy) {
     const int rr = (q + dy + kRing) % kRing;
     const double2 p = *reinterpret_cast<const double2*>(&S.row[rr][2 * lane]);
     if (BOX || dy == 0) {
-      double wv = __shfl_up_sync(0xffffffffu, p.y, 1);
-      double ev = __shfl_down_sync(0xffffffffu, p.x, 1);
-      if (lane == 0) wv = S.halo[rr][0];
-      if (lane == 31) ev = S.halo[rr][1];
-      W.tap(a0, tap_index2<BOX>(dy, -1), wv, c0);
-      W.tap(a0, tap_index2<BOX>(dy, 0), p.x, c0);
-      W.tap(a0, tap_index2<BOX>(dy, 1), p.y, c0);
-      W.tap(a1, tap_index2<BOX>(dy, -1), p.x, c0 + 1);
-      W.tap(a1, tap_index2<BOX>(dy, 0), p.y, c0 + 1);
-      W.tap(a1, tap_index2<BOX>(dy, 1), ev, c0 + 1);
+      double v[2 * R + 2];  // columns x-R .. x+1+R
+      const double lx = __shfl_up_sync(0xffffffffu, p.x, 1), ly = __shfl_up_sync(0xffffffffu, p.y, 1);
+      const double rx = __shfl_down_sync(0xffffffffu, p.x, 1), ry = __shfl_down_sync(0xffffffffu, p.y, 1);
+      if (R == 2) {
+        v[0] = lane == 0 ? S.halo[rr][0] : lx;
+        v[1] = lane == 0 ? S.halo[rr][1] : ly;
+        v[4] = lane == 31 ? S.halo[rr][2] : rx;
+        v[5] = lane == 31 ? S.halo[rr][3] : ry;
+      } else {
+        v[0] = lane == 0 ? S.halo[rr][0] : ly;
+        v[2 * R + 1] = lane == 31 ? S.halo[rr][1] : rx;
+      }
+      v[R] = p.x;
+      v[R + 1] = p.y;
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx) W.tap(a0, tap_index2<BOX, R>(dy, dx), v[R + dx], c0);
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx) W.tap(a1, tap_index2<BOX, R>(dy, dx), v[R + 1 + dx], c0 + 1);
     } else {
-      W.tap(a0, tap_index2<BOX>(dy, 0), p.x, c0);
-      W.tap(a1, tap_index2<BOX>(dy, 0), p.y, c0 + 1);
+      W.tap(a0, tap_index2<BOX, R>(dy, 0), p.x, c0);
+      W.tap(a1, tap_index2<BOX, R>(dy, 0), p.y, c0 + 1);
     }
   }
 }
@@ -132,7 +148,7 @@ __device__ __forceinline__ void pair_general(const Smem2& S, const RegWeights<NT
 // Every addition is an FMA against a register holding 1.0 (same rounding,
 // full FP64 rate); the common weight comes from the register copies W.w[k].
 template <int NT>
-__device__ __forceinline__ void quad_equal(const Smem2& S, const RegWeights<NT>& W, int q, int lane,
+__device__ __forceinline__ void quad_equal(const Smem2<1>& S, const RegWeights<NT>& W, int q, int lane,
                                            double out[2][2]) {
   const int qm = (q - 1 + kRing) % kRing, q1 = (q + 1) % kRing, q2 = (q + 2) % kRing;
   const double2 a = *reinterpret_cast<const double2*>(&S.row[qm][2 * lane]);
@@ -164,9 +180,9 @@ __device__ __forceinline__ void quad_equal(const Smem2& S, const RegWeights<NT>&
   out[1][1] = fma(W.w[5], R1, wt1);
 }
 
-template <int NT, bool BOX, bool PERIODIC, bool EQUAL>
+template <int NT, bool BOX, int R, bool PERIODIC, bool EQUAL>
 __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant__ Params2<NT> P) {
-  __shared__ Smem2 S;
+  __shared__ Smem2<R> S;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   RegWeights<NT> W;
   W.load(P.wdev);
@@ -193,11 +209,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant_
     seq += nblk;
     if (threadIdx.x == 0)
       for (int j = 0; j < kSlots && j < nblk; ++j)
-        issue_block<NT, PERIODIC>(S, P, (base + j) % kSlots, ba - 1 + j, x0);
+        issue_block<NT, R, PERIODIC>(S, P, (base + j) % kSlots, ba - 1 + j, x0);
     for (int j = 0; j < 3; ++j)
-      store_halo2(S, (base + j) % kSlots, load_halo2<PERIODIC>(P.src, ba - 1 + j, x0, P.ny, P.nx));
+      store_halo2<R>(S, (base + j) % kSlots, load_halo2<R, PERIODIC>(P.src, ba - 1 + j, x0, P.ny, P.nx));
     double halo_next = 0.0;
-    if (nblk > 3) halo_next = load_halo2<PERIODIC>(P.src, ba + 2, x0, P.ny, P.nx);
+    if (nblk > 3) halo_next = load_halo2<R, PERIODIC>(P.src, ba + 2, x0, P.ny, P.nx);
     __syncthreads();
     int issued = min(kSlots, nblk) - 1;
     for (int k = 1; k <= nblk - 2; ++k) {
@@ -215,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant_
       if (EQUAL) {
         const int r = 2 * warp;  // rows r, r+1 of the block
         double out[2][2];
-        quad_equal<NT>(S, W, slot * kRB + r, lane, out);
+        if constexpr (R == 1) quad_equal<NT>(S, W, slot * kRB + r, lane, out);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
           const int y = blk * kRB + r + i;
@@ -226,13 +242,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant_
         for (int i = 0; i < 2; ++i) {
           const int r = warp + 8 * i;
           double a0 = 0.0, a1 = 0.0;
-          pair_general<NT, BOX>(S, W, slot * kRB + r, lane, 2 * i, a0, a1);
+          pair_general<NT, BOX, R>(S, W, slot * kRB + r, lane, 2 * i, a0, a1);
           const int y = blk * kRB + r;
           if (y < P.ny && x < P.nx) st_global_v2(P.dst + (int64_t)y * P.nx + x, a0, a1);
         }
       }
-      if (k + 2 <= nblk - 1) store_halo2(S, (base + k + 2) % kSlots, halo_next);
-      if (k + 3 <= nblk - 1) halo_next = load_halo2<PERIODIC>(P.src, ba + k + 2, x0, P.ny, P.nx);
+      if (k + 2 <= nblk - 1) store_halo2<R>(S, (base + k + 2) % kSlots, halo_next);
+      if (k + 3 <= nblk - 1) halo_next = load_halo2<R, PERIODIC>(P.src, ba + k + 2, x0, P.ny, P.nx);
       __syncthreads();
       if (S.abort) {
         if (threadIdx.x == 0)
@@ -243,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant_
       if (k + 3 <= nblk - 1) {
         if (threadIdx.x == 0) {
           fence_proxy_async_smem();
-          issue_block<NT, PERIODIC>(S, P, (base + k + 3) % kSlots, ba + k + 2, x0);
+          issue_block<NT, R, PERIODIC>(S, P, (base + k + 3) % kSlots, ba + k + 2, x0);
         }
         issued = k + 3;
       }
@@ -263,7 +279,7 @@ bool encode_2d(CUtensorMap* map, const double* base, int ny, int nx) {
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NT, bool BOX, bool PERIODIC, bool EQUAL>
+template <int NT, bool BOX, int R, bool PERIODIC, bool EQUAL>
 cudaError_t launch2(const Geom& g, const double* wdev, const double* src, double* dst, int* status,
                     int sms, cudaStream_t stream) {
   Params2<NT> P;
@@ -279,13 +295,13 @@ cudaError_t launch2(const Geom& g, const double* wdev, const double* src, double
   P.wdev = wdev;
   static int occ = -1;
   if (occ < 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream2d<NT, BOX, PERIODIC, EQUAL>, kThreads,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream2d<NT, BOX, R, PERIODIC, EQUAL>, kThreads,
                                                     0) != cudaSuccess)
     occ = 0;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)sms * occ;
   if (grid > P.work) grid = P.work;
-  k_stream2d<NT, BOX, PERIODIC, EQUAL><<<(unsigned)grid, kThreads, 0, stream>>>(P);
+  k_stream2d<NT, BOX, R, PERIODIC, EQUAL><<<(unsigned)grid, kThreads, 0, stream>>>(P);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
@@ -294,7 +310,7 @@ cudaError_t launch2(const Geom& g, const double* wdev, const double* src, double
 
 bool stream2d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
                        const void* b) {
-  if (ndim != 2 || radius != 1) return false;
+  if (ndim != 2 || (radius != 1 && radius != 2)) return false;
   if (g.nx % 2 != 0) return false;
   if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return false;
   if (boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % kRB != 0)) return false;
@@ -307,21 +323,31 @@ bool taps_all_equal(const HostTaps& t) {
   return t.n > 0;
 }
 
-cudaError_t launch_stream2d(Shape shape, int boundary, bool equal, const Geom& g,
+cudaError_t launch_stream2d(Shape shape, int radius, int boundary, bool equal, const Geom& g,
                             const HostTaps& taps, const double* wdev, const double* src, double* dst,
                             int* status, int sms, cudaStream_t stream) {
   const bool per = boundary == kPeriodic;
+  if (radius == 2) {
+    if (shape == Shape::kBox) {
+      if (taps.n != 25) return cudaErrorInvalidValue;
+      return per ? launch2<25, true, 2, true, false>(g, wdev, src, dst, status, sms, stream)
+                 : launch2<25, true, 2, false, false>(g, wdev, src, dst, status, sms, stream);
+    }
+    if (taps.n != 9) return cudaErrorInvalidValue;
+    return per ? launch2<9, false, 2, true, false>(g, wdev, src, dst, status, sms, stream)
+               : launch2<9, false, 2, false, false>(g, wdev, src, dst, status, sms, stream);
+  }
   if (shape == Shape::kBox) {
     if (taps.n != 9) return cudaErrorInvalidValue;
     if (equal)
-      return per ? launch2<9, true, true, true>(g, wdev, src, dst, status, sms, stream)
-                 : launch2<9, true, false, true>(g, wdev, src, dst, status, sms, stream);
-    return per ? launch2<9, true, true, false>(g, wdev, src, dst, status, sms, stream)
-               : launch2<9, true, false, false>(g, wdev, src, dst, status, sms, stream);
+      return per ? launch2<9, true, 1, true, true>(g, wdev, src, dst, status, sms, stream)
+                 : launch2<9, true, 1, false, true>(g, wdev, src, dst, status, sms, stream);
+    return per ? launch2<9, true, 1, true, false>(g, wdev, src, dst, status, sms, stream)
+               : launch2<9, true, 1, false, false>(g, wdev, src, dst, status, sms, stream);
   }
   if (taps.n != 5) return cudaErrorInvalidValue;
-  return per ? launch2<5, false, true, false>(g, wdev, src, dst, status, sms, stream)
-             : launch2<5, false, false, false>(g, wdev, src, dst, status, sms, stream);
+  return per ? launch2<5, false, 1, true, false>(g, wdev, src, dst, status, sms, stream)
+             : launch2<5, false, 1, false, false>(g, wdev, src, dst, status, sms, stream);
 }
 
 }  // namespace gbst

@@ -376,3 +376,18 @@ def test_persistent_temporal_matches_single_steps_bitwise(st, shape, boundary, k
     b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
     assert np.array_equal(a, b)
     assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
+
+
+@pytest.mark.parametrize("shape,boundary,kind", [((32, 128), PERIODIC, "star_rand"), ((32, 128), PERIODIC, "box_rand"),
+                                                 ((37, 70), DIRICHLET, "star_rand"), ((37, 70), DIRICHLET, "box_rand"),
+                                                 ((130, 64), DIRICHLET, "box_rand"), ((3, 4), DIRICHLET, "star_rand")])
+def test_stream2d_radius2_matches_direct_bitwise_and_oracle(st, shape, boundary, kind):
+    """Table 1's Star-2D9P and Box-2D25P shapes (radius 2) in the streaming
+    kernel: bitwise equal to the direct kernel, within 1e-12 of the oracle."""
+    w = weights_for(kind, 2, 2, 800)
+    u0 = synth.normal(14, shape)
+    T = 6
+    a = gpu_run(st, u0, w, 2, boundary, T, Tb=1, variant=st.VARIANT_STREAM)
+    b = gpu_run(st, u0, w, 2, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    assert normwise_rel(a, oracle.run(u0, w, 2, boundary, T, nthreads=0)) <= TOL
