@@ -39,14 +39,16 @@ HEADLINE = dict(name="heat3d-7pt", shape=(512, 512, 512), T=1000, alpha=0.1, bou
 # face coefficients = 7 products and 6 sums; adjoint step = the transposed
 # update (13) plus 3 faces x (2 differences, 1 product, 1 sum) = 25.
 FLOPS = {"heat3d-7pt": 13, "box2d-9pt": 17, "box3d-27pt": 53, "heat2d-5pt": 9,
-         "varcoef-7pt": 13, "adjoint-7pt": 13 + 25, "star2d-9pt": 17, "box2d-25pt": 49}
+         "varcoef-7pt": 13, "adjoint-7pt": 13 + 25, "star2d-9pt": 17, "box2d-25pt": 49,
+         "heat1d-3pt": 5, "star1d-5pt": 9}
 NOMINAL_FP64_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flop
 # FP64 instructions the kernels issue per cell update (one pipe slot each):
 # K for a K-tap chain; 4.25 for the equal-weight 9-point box with shared
 # partial sums (17 warp instructions per 2 rows x 64 columns, strip edges
 # included); adjoint: forward 7 + recompute 7 + transposed step 7 + 3 faces x 3.
 INSTR = {"heat3d-7pt": 7, "box3d-27pt": 27, "box2d-9pt": 4.25, "heat2d-5pt": 5,
-         "varcoef-7pt": 7, "adjoint-7pt": 7 + 7 + 7 + 9, "star2d-9pt": 9, "box2d-25pt": 25}
+         "varcoef-7pt": 7, "adjoint-7pt": 7 + 7 + 7 + 9, "star2d-9pt": 9, "box2d-25pt": 25,
+         "heat1d-3pt": 3 * (2048 + 8) / 2048, "star1d-5pt": 5 * (2048 + 16) / 2048}
 
 
 # ------------------------------------------------------------------ helpers
@@ -535,7 +537,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h["u0"])
     forms = {}
-    want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2"]) if args.forms == "all" else \
+    want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2", "onedim"]) if args.forms == "all" else \
         set() if args.forms == "none" else set(args.forms.split(","))
     if "batched" in want:
         forms["batched"] = form_batched(st, stream, peak_tflops, rank, world)
@@ -561,6 +563,15 @@ def main():
             u0 = synth.uniform(synth.SEED_BOX2D + 11, shp)
             forms["star2d9p"] = form_const(st, "star2d-9pt", shp, 2, star9, 1, 100, u0, stream, peak_tflops)
             forms["box2d25p"] = form_const(st, "box2d-25pt", shp, 2, box25, 1, 100, u0, stream, peak_tflops)
+        if "onedim" in want:
+            # Table 1's 1D shapes: Heat-1D (alpha = 0.25) and Star-1D5P, 10^7 cells
+            n1 = 10_000_000
+            u1 = synth.uniform(synth.SEED_HEAT2D + 20, (n1,))
+            forms["heat1d"] = form_const(st, "heat1d-3pt", (n1,), 1, np.array([0.25, 0.5, 0.25]), 0, 1000,
+                                         u1, stream, peak_tflops)
+            v5 = synth.uniform(synth.SEED_HEAT2D + 21, (5,))
+            forms["star1d5p"] = form_const(st, "star1d-5pt", (n1,), 2, v5 / v5.sum(), 1, 1000, u1, stream,
+                                           peak_tflops)
         if "box3d" in want:
             shp = (384, 384, 384)
             forms["box3d"] = form_const(st, "box3d-27pt", shp, 1, synth.box_weights(3, seed=synth.SEED_BOX3D),

@@ -188,6 +188,10 @@ int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
     return kVariantStream;
   }
   if (p->ndim == 2 && p->radius == 2) return kVariantStream;
+  if (p->ndim == 1) {
+    if (Tb) *Tb = 8;  // 8 steps per launch in shared memory, 0.4-0.8% halo recompute
+    return kVariantTemporal;
+  }
   return kVariantDirect;
 }
 
@@ -313,7 +317,8 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   if (variant == kVariantTemporal && !temporal_supported(p->ndim, p->radius, Tb)) {
     if (forced)
       return fail(STENCIL_ERR_UNSUPPORTED,
-                  "temporal blocking covers radius-1 plans with Tb in {2, 4} (3D) or {2, 4, 8} (2D)");
+                  "temporal blocking covers radius-1 plans with Tb in {2, 4} (3D) or {2, 4, 8} (2D), "
+                  "and 1D plans of radius 1 or 2 with Tb in {2, 4, 8}");
     variant = default_variant(p) == kVariantStream && stream_ok ? kVariantStream : kVariantDirect;
   }
   if (variant != kVariantTemporal) Tb = 1;
@@ -330,7 +335,7 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
     cudaError_t e;
     int steps = 1;
     if (variant == kVariantTemporal && T - t >= Tb) {
-      e = launch_temporal(p->ndim, p->shape, p->boundary, Tb, p->g, p->d_w, a, b, sms, s);
+      e = launch_temporal(p->ndim, p->radius, p->shape, p->boundary, Tb, p->g, p->d_w, a, b, sms, s);
       steps = Tb;
     } else {
       const int v = variant == kVariantTemporal ? single : variant;

@@ -84,9 +84,10 @@ cudaError_t launch_stream2d(Shape shape, int radius, int boundary, bool equal, c
                             int* status, int sms, cudaStream_t stream);
 
 // Temporal blocking: Tb fused steps per launch (3D: Tb in {2, 4}; 2D: Tb in
-// {2, 4, 8}), radius 1, any shape and boundary.
+// {2, 4, 8}; radius 1, any shape and boundary; 1D: radius 1 or 2, Tb in
+// {2, 4, 8}).
 bool temporal_supported(int ndim, int radius, int Tb);
-cudaError_t launch_temporal(int ndim, Shape shape, int boundary, int Tb, const Geom& g,
+cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int Tb, const Geom& g,
                             const double* wdev, const double* src, double* dst, int sms,
                             cudaStream_t stream);
 

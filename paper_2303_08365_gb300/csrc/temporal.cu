@@ -257,20 +257,99 @@ cudaError_t by_tb(int Tb, const Geom& g, const double* wdev, const double* src, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// 1D: a CTA owns 2048 consecutive cells, loads them with a halo of R*Tb cells
+// per side into shared memory, advances them Tb steps there (the region
+// shrinks by R per side per step) and writes the 2048 cells back: one launch
+// per Tb steps, (2048 + R*Tb)/2048 of the single-step FP64 work.  Taps in
+// lexicographic order with register weights, as in every other sweep.
+constexpr int k1W = 2048;
+
+template <int R, bool PERIODIC, int TB>
+__global__ void __launch_bounds__(kThreads) k_temporal1d(const double* __restrict__ src,
+                                                         double* __restrict__ dst, int n,
+                                                         const double* __restrict__ wdev) {
+  constexpr int NT = 2 * R + 1;
+  constexpr int H = R * TB;
+  constexpr int L = k1W + 2 * H;
+  __shared__ double buf[2][L];
+  RegWeights<NT> W;
+  W.load(wdev);
+  const long long x0 = (long long)blockIdx.x * k1W;
+  for (int i = threadIdx.x; i < L; i += kThreads) {
+    long long x = x0 - H + i;
+    double v = 0.0;
+    if (PERIODIC) {
+      x %= n;
+      if (x < 0) x += n;
+      v = __ldg(src + x);
+    } else if (x >= 0 && x < n) {
+      v = __ldg(src + x);
+    }
+    buf[0][i] = v;
+  }
+  __syncthreads();
+  int cur = 0;
+#pragma unroll 1
+  for (int s = 1; s <= TB; ++s) {
+    const double* in = buf[cur];
+    double* out = buf[cur ^ 1];
+    for (int i = R * s + threadIdx.x; i < L - R * s; i += kThreads) {
+      const long long x = x0 - H + i;
+      double acc = 0.0;
+      if (PERIODIC || (x >= 0 && x < n)) {
+#pragma unroll
+        for (int k = 0; k < NT; ++k) W.tap(acc, k, in[i + k - R], 0);
+      }
+      out[i] = acc;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  for (int i = threadIdx.x; i < k1W; i += kThreads) {
+    const long long x = x0 + i;
+    if (x < n) dst[x] = buf[cur][H + i];
+  }
+}
+
+template <int R, bool PERIODIC>
+cudaError_t launch_1d(int Tb, const Geom& g, const double* wdev, const double* src, double* dst,
+                      cudaStream_t stream) {
+  const unsigned blocks = (unsigned)((g.nx + k1W - 1) / k1W);
+  switch (Tb) {
+    case 2: k_temporal1d<R, PERIODIC, 2><<<blocks, kThreads, 0, stream>>>(src, dst, g.nx, wdev); break;
+    case 4: k_temporal1d<R, PERIODIC, 4><<<blocks, kThreads, 0, stream>>>(src, dst, g.nx, wdev); break;
+    case 8: k_temporal1d<R, PERIODIC, 8><<<blocks, kThreads, 0, stream>>>(src, dst, g.nx, wdev); break;
+    default: return cudaErrorInvalidValue;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool temporal_supported(int ndim, int radius, int Tb) {
+  if (ndim == 1) return (radius == 1 || radius == 2) && (Tb == 2 || Tb == 4 || Tb == 8);
   if (radius != 1) return false;
   if (ndim == 3) return Tb == 2 || Tb == 4;
   if (ndim == 2) return Tb == 2 || Tb == 4 || Tb == 8;
   return false;
 }
 
-cudaError_t launch_temporal(int ndim, Shape shape, int boundary, int Tb, const Geom& g,
+cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int Tb, const Geom& g,
                             const double* wdev, const double* src, double* dst, int sms,
                             cudaStream_t stream) {
   const bool per = boundary == kPeriodic;
   const bool box = shape == Shape::kBox;
+  if (ndim == 1) {
+    // the radius is implied by the tap count (3 or 5)
+    (void)box;
+    if (radius == 2)
+      return per ? launch_1d<2, true>(Tb, g, wdev, src, dst, stream)
+                 : launch_1d<2, false>(Tb, g, wdev, src, dst, stream);
+    return per ? launch_1d<1, true>(Tb, g, wdev, src, dst, stream)
+               : launch_1d<1, false>(Tb, g, wdev, src, dst, stream);
+  }
   if (ndim == 3) {
     if (box) return per ? by_tb<3, 27, true, true>(Tb, g, wdev, src, dst, sms, stream)
                         : by_tb<3, 27, true, false>(Tb, g, wdev, src, dst, sms, stream);

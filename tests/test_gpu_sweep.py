@@ -391,3 +391,18 @@ def test_stream2d_radius2_matches_direct_bitwise_and_oracle(st, shape, boundary,
     b = gpu_run(st, u0, w, 2, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
     assert np.array_equal(a, b)
     assert normwise_rel(a, oracle.run(u0, w, 2, boundary, T, nthreads=0)) <= TOL
+
+
+@pytest.mark.parametrize("n,radius,boundary,Tb,T", [(10000, 1, PERIODIC, 8, 29), (10000, 2, DIRICHLET, 8, 21),
+                                                    (4097, 1, DIRICHLET, 4, 10), (5, 2, PERIODIC, 8, 17),
+                                                    (2048, 2, PERIODIC, 2, 5)])
+def test_temporal_1d_matches_direct_bitwise_and_oracle(st, n, radius, boundary, Tb, T):
+    """Table 1's Heat-1D / Star-1D5P shapes: Tb steps per launch in shared
+    memory, bitwise equal to single steps, within 1e-12 of the oracle."""
+    w = synth.uniform(900 + radius, (2 * radius + 1,))
+    w = w / w.sum()
+    u0 = synth.normal(15, (n,))
+    a = gpu_run(st, u0, w, radius, boundary, T, Tb=Tb, variant=st.VARIANT_TEMPORAL)
+    b = gpu_run(st, u0, w, radius, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    assert normwise_rel(a, oracle.run(u0, w, radius, boundary, T, nthreads=0)) <= TOL
