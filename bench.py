@@ -418,6 +418,59 @@ def run_reference(args):
     return 0
 
 
+THERMAL = dict(mu=0.23, n=9600, T_full=3_800_000,
+               table3={"naive_s": 124448.5, "tetris_cpu_s": 27709.1, "tetris_gpu_s": 5597.4,
+                       "tetris_s": 4270.9, "tetris_gpu_gst": 63.3, "tetris_gst": 82.9,
+                       "hardware": "AMD EPYC 7V13 (24 cores) + NVIDIA A100-80GB, FP64"})
+
+
+def thermal_case(st, n, T, stream, fp32=True):
+    """The paper's copper-plate case study (Sec. 5.5) on an n x n grid: heat
+    stencil with mu = 0.23 (Eq. 3 weights 0.08 / 0.23), Dirichlet 0 at the
+    edges, Gaussian initial field peaked at 100 degrees.  FP64 production
+    sweep timed; optionally the FP32 twin for the Table 4 deviation counts."""
+    import torch
+    w = synth.heat_weights(2, THERMAL["mu"])
+    u0 = synth.gaussian_plate((n, n))
+    g = torch.from_numpy(u0).cuda()
+    plan = st.Plan((n, n), 1, w, st.DIRICHLET_ZERO)
+    plan.run(g, min(T, 10), stream=stream)          # warm-up (and plan set-up)
+    g.copy_(torch.from_numpy(u0))
+    ms = cuda_time(lambda: plan.run(g, T, stream=stream), stream)
+    tb, v = plan.get_tuning()
+    out = {"workload": f"thermal plate {n}x{n}, mu=0.23, Dirichlet 0, Gaussian 100 C (sigma "
+                       f"{1376.0 * n / 9600:.0f} cells), T={T}",
+           "variant": st.stencil_variant_name(v), "Tb": tb,
+           "gstencil_per_s": round(n * n * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
+           "centre_C": round(float(g[n // 2, n // 2]), 4)}
+    rate = n * n * T / (ms * 1e-3)
+    if n == THERMAL["n"]:
+        full = THERMAL["n"] ** 2 * THERMAL["T_full"] / rate
+        out["extrapolated_full_run_s"] = round(full, 1)
+        out["paper_table3_context"] = THERMAL["table3"]
+    if fp32:
+        g32 = torch.from_numpy(u0.astype(np.float32)).cuda()
+        work = torch.empty_like(g32)
+        st.stencil_run_f32(plan.handle, g32, work, T)
+        torch.cuda.synchronize()
+        d = (g32.double() - g).abs()
+        rel = d / g.abs().clamp_min(1e-300)
+        total = d.numel()
+        out["fp32_vs_fp64_percent_of_cells"] = {
+            "abs>0.1C": round(100.0 * float((d > 0.1).sum()) / total, 3),
+            "abs>0.5C": round(100.0 * float((d > 0.5).sum()) / total, 3),
+            "abs>1.0C": round(100.0 * float((d > 1.0).sum()) / total, 3),
+            "rel>1%": round(100.0 * float((rel > 0.01).sum()) / total, 3),
+            "rel>3%": round(100.0 * float((rel > 0.03).sum()) / total, 3),
+            "rel>5%": round(100.0 * float((rel > 0.05).sum()) / total, 3),
+            "max_abs_C": float(d.max())}
+        del g32, work
+    plan.close()
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_case(args):
     """One workload at a chosen size for profiling (not the benchmark line):
     W warm-up runs and `steps` timed runs of T time steps each."""
@@ -438,6 +491,9 @@ def run_case(args):
         bnd = 0 if name == "heat2d" else 1
     elif name in ("varcoef", "adjoint"):
         shape = (n, n, n)
+    elif name == "thermal":
+        print(json.dumps(thermal_case(st, n, args.T, stream)))
+        return 0
     elif name == "batched":
         # a reduced batch of the 96-grid workload's kind: sides log-uniform in [64, n]
         items = synth.batch_items(synth.SEED_BATCH, count=24, side_lo=64, side_hi=n, t_lo=args.T,
@@ -489,7 +545,8 @@ def main():
                     "box2d,box3d,heat2d,batched,adjoint")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None,
-                    help="profiling mode: heat3d | box3d | heat2d | box2d | varcoef | adjoint | batched")
+                    help="profiling mode: heat3d | box3d | heat2d | box2d | varcoef | adjoint | batched | "
+                         "thermal (the case study with the FP32 deviation counts)")
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--T", type=int, default=4)
     ap.add_argument("--variant", type=int, default=0)
@@ -537,7 +594,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h["u0"])
     forms = {}
-    want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2", "onedim"]) if args.forms == "all" else \
+    want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2", "onedim", "thermal"]) \
+        if args.forms == "all" else \
         set() if args.forms == "none" else set(args.forms.split(","))
     if "batched" in want:
         forms["batched"] = form_batched(st, stream, peak_tflops, rank, world)
@@ -563,6 +621,8 @@ def main():
             u0 = synth.uniform(synth.SEED_BOX2D + 11, shp)
             forms["star2d9p"] = form_const(st, "star2d-9pt", shp, 2, star9, 1, 100, u0, stream, peak_tflops)
             forms["box2d25p"] = form_const(st, "box2d-25pt", shp, 2, box25, 1, 100, u0, stream, peak_tflops)
+        if "thermal" in want:
+            forms["thermal"] = thermal_case(st, THERMAL["n"], 1000, stream, fp32=False)
         if "onedim" in want:
             # Table 1's 1D shapes: Heat-1D (alpha = 0.25) and Star-1D5P, 10^7 cells
             n1 = 10_000_000

@@ -94,6 +94,14 @@ int stencil_run(stencil_plan p, double* d_grid, int64_t T, const double* d_kappa
 int stencil_run_host(stencil_plan p, double* h_grid, int64_t T, const double* h_kappa,
                      double dt, void* cuda_stream);
 
+/* FP32 twin of stencil_run, for accuracy studies only: the paper compares an
+ * FP32 run of its thermal-diffusion case with FP64 (Sec. 5.5, Table 4) to
+ * show why the method keeps FP64.  Same plan (constant weights, up to 27
+ * taps), same tap order, weights rounded to float.  d_grid and d_work are
+ * device float arrays of the plan's shape (caller-owned); the result is left
+ * in d_grid.  No FP64 entry point uses this path. */
+int stencil_run_f32(stencil_plan p, float* d_grid, float* d_work, int64_t T, void* cuda_stream);
+
 /* Loss and gradients of the variable-coefficient sweep (the adjoint, or
  * transposed stencil swept backward in time):
  *   u^0 = d_u0, u^{t+1} = A(kappa) u^t, L = 0.5 * sum_i (u^T_i - target_i)^2,

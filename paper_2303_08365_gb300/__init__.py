@@ -53,6 +53,7 @@ SIGNATURES = [
     ("stencil_destroy", None, [_VP]),
     ("stencil_run", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_double, _VP]),
     ("stencil_run_host", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, ctypes.c_double, _VP]),
+    ("stencil_run_f32", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP]),
     ("stencil_adjoint", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP, ctypes.c_int64, ctypes.c_int,
                                        _VP, _VP, _DP, _VP]),
     ("stencil_adjoint_vjp", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
@@ -180,6 +181,16 @@ def stencil_run(h, grid, T, kappa=None, dt=0.0, stream=None):
     gp = _dev_ptr(grid, "grid")
     kp = _dev_ptr(kappa, "kappa", grid.shape) if kappa is not None else None
     _check(lib().stencil_run(h, gp, int(T), kp, float(dt), _stream(stream)))
+
+
+def stencil_run_f32(h, grid, work, T, stream=None):
+    """FP32 twin of stencil_run (accuracy studies only): grid and work are
+    contiguous float32 CUDA tensors of the plan's shape."""
+    import torch
+    for t, name in ((grid, "grid"), (work, "work")):
+        if t.device.type != "cuda" or t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    _check(lib().stencil_run_f32(h, grid.data_ptr(), work.data_ptr(), int(T), _stream(stream)))
 
 
 def stencil_run_host(h, grid, T, kappa=None, dt=0.0, stream=None):

@@ -701,6 +701,26 @@ int stencil_adjoint_vjp(stencil_plan p, const double* d_u0, const double* d_kapp
                       nullptr, (cudaStream_t)cuda_stream);
 }
 
+int stencil_run_f32(stencil_plan p, float* d_grid, float* d_work, int64_t T, void* cuda_stream) {
+  g_err.clear();
+  if (!p || !d_grid || !d_work) return fail(STENCIL_ERR_ARG, "NULL argument");
+  if (p->varcoef) return fail(STENCIL_ERR_ARG, "the FP32 twin covers constant-weight plans");
+  if (p->taps.n > 27) return fail(STENCIL_ERR_UNSUPPORTED, "the FP32 twin covers up to 27 taps");
+  if (T < 0) return fail(STENCIL_ERR_ARG, "T must be >= 0");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  float* a = d_grid;
+  float* b = d_work;
+  for (int64_t t = 0; t < T; ++t) {
+    cudaError_t e = launch_direct_f32(p->ndim, p->radius, p->boundary, p->g, p->taps, a, b, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the FP32 sweep");
+    std::swap(a, b);
+  }
+  if (a != d_grid)
+    CUDA_TRY(cudaMemcpyAsync(d_grid, a, (size_t)p->cells() * sizeof(float), cudaMemcpyDeviceToDevice, s),
+             "copying the FP32 result back");
+  return STENCIL_OK;
+}
+
 int stencil_plan_status(stencil_plan p, void* cuda_stream) {
   g_err.clear();
   if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");

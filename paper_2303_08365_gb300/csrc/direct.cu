@@ -65,6 +65,78 @@ __global__ void __launch_bounds__(256) k_direct(const double* __restrict__ src,
   }
 }
 
+// FP32 twin of the direct sweep, for accuracy studies only (the paper's
+// Table 4 compares an FP32 run of its thermal case with FP64): the same tap
+// order with the weights rounded to float and float FMAs.
+template <int NT, int MODE>
+__global__ void __launch_bounds__(256) k_direct_f32(const float* __restrict__ src, float* __restrict__ dst,
+                                                    int nz, int ny, int nx, int zper,
+                                                    const __grid_constant__ TapList<NT> tp) {
+  float w[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) w[k] = (float)tp.w[k];
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= nx || y >= ny) return;
+  const int z0 = blockIdx.z * zper;
+  const int z1 = min(nz, z0 + zper);
+  for (int z = z0; z < z1; ++z) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      int zz, yy, xx;
+      bool in = axis_index<MODE>(z + tp.dz[k], nz, zz);
+      in &= axis_index<MODE>(y + tp.dy[k], ny, yy);
+      in &= axis_index<MODE>(x + tp.dx[k], nx, xx);
+      float v = 0.0f;
+      if (in) v = __ldg(src + ((int64_t)zz * ny + yy) * nx + xx);
+      acc = (k == 0) ? w[0] * v : fmaf(w[k], v, acc);
+    }
+    dst[((int64_t)z * ny + y) * nx + x] = acc;
+  }
+}
+
+void direct_shape(const Geom& g, dim3& grid, dim3& block, int& zper) {
+  zper = 1;
+  if (g.ny == 1 && g.nz == 1) {
+    block = dim3(256, 1, 1);
+    grid = dim3((g.nx + 255) / 256, 1, 1);
+  } else {
+    block = dim3(32, 8, 1);
+    unsigned gx = (g.nx + 31) / 32, gy = (g.ny + 7) / 8;
+    int64_t tiles = (int64_t)gx * gy;
+    int64_t want = 152 * 16;
+    int64_t zchunks = (want + tiles - 1) / tiles;
+    if (zchunks > g.nz) zchunks = g.nz;
+    if (zchunks < 1) zchunks = 1;
+    zper = (int)((g.nz + zchunks - 1) / zchunks);
+    zchunks = (g.nz + zper - 1) / zper;
+    grid = dim3(gx, gy, (unsigned)zchunks);
+  }
+}
+
+template <int NT>
+cudaError_t launch_nt_f32(int mode, const Geom& g, const HostTaps& ht, const float* src, float* dst,
+                          cudaStream_t stream) {
+  TapList<NT> tp;
+  for (int k = 0; k < NT; ++k) {
+    tp.w[k] = ht.w[k];
+    tp.dz[k] = ht.dz[k];
+    tp.dy[k] = ht.dy[k];
+    tp.dx[k] = ht.dx[k];
+  }
+  dim3 block, grid;
+  int zper;
+  direct_shape(g, grid, block, zper);
+  switch (mode) {
+    case 0: k_direct_f32<NT, 0><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp); break;
+    case 1: k_direct_f32<NT, 1><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp); break;
+    default: k_direct_f32<NT, 2><<<grid, block, 0, stream>>>(src, dst, g.nz, g.ny, g.nx, zper, tp); break;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
 template <int NT>
 cudaError_t launch_nt(int mode, const Geom& g, const HostTaps& ht, const double* wdev,
                       const double* src, double* dst, cudaStream_t stream) {
@@ -124,6 +196,25 @@ cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const
     default: return cudaErrorInvalidValue;
   }
   (void)shape;
+}
+
+cudaError_t launch_direct_f32(int ndim, int radius, int boundary, const Geom& g, const HostTaps& taps,
+                              const float* src, float* dst, cudaStream_t stream) {
+  int mode = 0;
+  if (boundary == kPeriodic) {
+    bool small = g.nx < radius || (ndim >= 2 && g.ny < radius) || (ndim >= 3 && g.nz < radius);
+    mode = small ? 2 : 1;
+  }
+  switch (taps.n) {
+    case 3: return launch_nt_f32<3>(mode, g, taps, src, dst, stream);
+    case 5: return launch_nt_f32<5>(mode, g, taps, src, dst, stream);
+    case 7: return launch_nt_f32<7>(mode, g, taps, src, dst, stream);
+    case 9: return launch_nt_f32<9>(mode, g, taps, src, dst, stream);
+    case 13: return launch_nt_f32<13>(mode, g, taps, src, dst, stream);
+    case 25: return launch_nt_f32<25>(mode, g, taps, src, dst, stream);
+    case 27: return launch_nt_f32<27>(mode, g, taps, src, dst, stream);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace gbst

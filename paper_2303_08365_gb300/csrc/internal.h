@@ -64,6 +64,10 @@ cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const
                           const HostTaps& taps, const double* wdev, const double* src, double* dst,
                           cudaStream_t stream);
 
+// FP32 twin of the direct sweep (accuracy studies only; up to 27 taps).
+cudaError_t launch_direct_f32(int ndim, int radius, int boundary, const Geom& g, const HostTaps& taps,
+                              const float* src, float* dst, cudaStream_t stream);
+
 // 3D radius-1 streaming sweep (TMA-fed shared-memory plane ring).  Eligible
 // when nx is even, both buffers are 16-byte aligned and, for periodic grids,
 // nx % 64 == 0 and ny a multiple of the tile height (32 star, 16 box).

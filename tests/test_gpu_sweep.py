@@ -406,3 +406,20 @@ def test_temporal_1d_matches_direct_bitwise_and_oracle(st, n, radius, boundary, 
     b = gpu_run(st, u0, w, radius, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
     assert np.array_equal(a, b)
     assert normwise_rel(a, oracle.run(u0, w, radius, boundary, T, nthreads=0)) <= TOL
+
+
+def test_fp32_twin_is_single_precision_and_close(st):
+    """The FP32 twin (accuracy studies only) follows the same stencil: within
+    float rounding of the oracle, and measurably less exact than FP64."""
+    import torch
+    shape = (96, 128)
+    w = synth.heat_weights(2, 0.23)
+    u0 = synth.gaussian_plate(shape, 100.0, 12.0)
+    ref = oracle.run(u0, w, 1, DIRICHLET, 50, nthreads=0)
+    p = st.Plan(shape, 1, w, DIRICHLET)
+    g32 = torch.from_numpy(u0.astype(np.float32)).cuda()
+    st.stencil_run_f32(p.handle, g32, torch.empty_like(g32), 50)
+    got = g32.cpu().numpy().astype(np.float64)
+    err = normwise_rel(got, ref)
+    assert 1e-9 < err <= 1e-5
+    p.close()
