@@ -226,6 +226,15 @@ const char* stencil_last_error(void);
  * all streams), for launch accounting in benchmarks. */
 int64_t stencil_launch_count(void);
 
+/* Failure-path self-test: launches the persistent kernel (one block, a 1 x 64
+ * grid) with a device-wide barrier that waits for one block more than the
+ * launch has, so its wait can only end by its wall-time limit (limit_ms, at
+ * most 2000).  Synchronous.  Returns STENCIL_ERR_TIMEOUT when the kernel gave
+ * up and reported it as designed (the context stays usable); any other code
+ * means the failure path did not behave.  Allocates and frees a few hundred
+ * bytes of device memory. */
+int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream);
+
 /* FP64 fused multiply-add throughput of the current device, measured with a
  * kernel of independent DFMA chains on every SM for about `millis` ms.
  * *dfma_per_s receives DFMA instructions per second (2 flops each). */

@@ -441,6 +441,7 @@ int batch_enqueue(stencil_batch_s* b, cudaStream_t s) {
   L.barrier = b->d_ctl;
   L.status = (int*)(b->d_ctl + 2);
   L.spin_limit = 2000000000LL;  // 2 s of wall time per barrier wait
+  L.barrier_blocks = 0;
   CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing the barrier words");
   cudaError_t e = launch_batched(L, b->blocks, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the batched kernel");
@@ -918,6 +919,67 @@ int stencil_run_batched(const stencil_batch_item* items, int n, int boundary, vo
   stencil_batch_destroy(b);
   g_err = keep;
   return rc;
+}
+
+// ------------------------------------------------------------ self-test
+
+int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream) {
+  g_err.clear();
+  if (!(limit_ms > 0.0) || limit_ms > 2000.0) return fail(STENCIL_ERR_ARG, "limit_ms must be in (0, 2000]");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // one 1 x 64 grid whose single tile is advanced by one block, while the
+  // barrier counts on one block more than the launch has: no wait can end
+  // except by its wall-time limit
+  double* grid = nullptr;
+  unsigned int* ctl = nullptr;
+  BatchItemDev* d_item = nullptr;
+  BatchTile* d_tile = nullptr;
+  int rc = STENCIL_OK;
+  auto cleanup = [&]() {
+    cudaFree(grid);
+    cudaFree(ctl);
+    cudaFree(d_item);
+    cudaFree(d_tile);
+  };
+  if (cudaMalloc(&grid, 2 * 64 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctl, 4 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&d_item, sizeof(BatchItemDev)) != cudaSuccess ||
+      cudaMalloc(&d_tile, sizeof(BatchTile)) != cudaSuccess) {
+    cleanup();
+    return fail(STENCIL_ERR_OOM, "allocating the self-test buffers");
+  }
+  BatchItemDev it{};
+  it.a = grid;
+  it.b = grid + 64;
+  it.ny = 1;
+  it.nx = 64;
+  it.T = 2;
+  it.w[2] = 1.0;
+  BatchTile tl{0, 0, 0};
+  cudaMemsetAsync(grid, 0, 2 * 64 * sizeof(double), s);
+  cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned int), s);
+  cudaMemcpyAsync(d_item, &it, sizeof(it), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_tile, &tl, sizeof(tl), cudaMemcpyHostToDevice, s);
+  BatchLaunch L;
+  L.items = d_item;
+  L.tiles = d_tile;
+  L.ntiles = 1;
+  L.max_T = 2;
+  L.boundary = 0;
+  L.barrier = ctl;
+  L.status = reinterpret_cast<int*>(ctl + 2);
+  L.spin_limit = (long long)(limit_ms * 1e6);
+  L.barrier_blocks = 2;  // the launch below has one block
+  cudaError_t e = launch_batched(L, 1, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, ctl + 2, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) rc = cuda_fail(e, "running the self-test");
+  cleanup();
+  if (rc) return rc;
+  if (st != STENCIL_ERR_TIMEOUT)
+    return fail(STENCIL_ERR_CUDA, "the bounded wait did not report a timeout (status %d)", st);
+  return st;
 }
 
 // ------------------------------------------------------------ measurement

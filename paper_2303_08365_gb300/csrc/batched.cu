@@ -119,6 +119,7 @@ __device__ __forceinline__ void tile_step(const BatchItemDev& it, const double* 
 
 __global__ void __launch_bounds__(kThreads) k_batched(BatchLaunch L) {
   const unsigned int G = gridDim.x;
+  const unsigned int arrivals = L.barrier_blocks > 0 ? (unsigned int)L.barrier_blocks : G;
   const bool periodic = L.boundary == kPeriodic;
   for (int t = 0; t < L.max_T; ++t) {
     for (int j = blockIdx.x; j < L.ntiles; j += G) {
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchLaunch L) {
       double* dst = (t & 1) ? it.a : it.b;
       tile_step(it, src, dst, tl.y0, tl.x0, periodic);
     }
-    if (!grid_barrier(L.barrier, G, L.spin_limit, L.status)) return;
+    if (!grid_barrier(L.barrier, arrivals, L.spin_limit, L.status)) return;
   }
   // grids with odd T hold their result in the partner buffer: copy it back
   for (int j = blockIdx.x; j < L.ntiles; j += G) {

@@ -150,7 +150,8 @@ struct BatchLaunch {
   int boundary;
   unsigned int* barrier;  // two words: arrival count, generation
   int* status;            // 0 ok, else a stencil_status
-  long long spin_limit;   // bounded waits: iterations before giving up
+  long long spin_limit;   // bounded waits: wall-time limit in ns
+  int barrier_blocks;     // arrivals a device-wide barrier waits for (0: the grid size)
 };
 cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, cudaStream_t stream);
 int batched_block_size();

@@ -123,8 +123,8 @@ __device__ __forceinline__ void store_halo(StreamSmem<BOX>& S, int slot, double 
   if (t < 2 * kRows) S.halo[slot][t / kRows][t % kRows] = v;
 }
 
-template <int NT, bool BOX, bool PERIODIC>
-__device__ __forceinline__ void issue_plane(StreamSmem<BOX>& S, const StreamParams<NT>& P, int slot,
+template <int NT, bool BOX, bool PERIODIC, class Smem>
+__device__ __forceinline__ void issue_plane(Smem& S, const StreamParams<NT>& P, int slot,
                                             int z, int y0, int x0) {
   constexpr int kRows = Tile<BOX>::Rows;
   const int zc = wrap_or_keep(z, P.nz, PERIODIC);
@@ -146,8 +146,8 @@ __device__ __forceinline__ constexpr int tap_index(int dz, int dy, int dx) {
 
 // Two adjacent cells (x, x+1) of tile row ry in the plane whose neighbours are
 // in slots (sm, s0, sp).
-template <int NT, bool BOX>
-__device__ __forceinline__ void compute_pair(const StreamSmem<BOX>& S, const RegWeights<NT>& W, int sm,
+template <int NT, bool BOX, class Smem>
+__device__ __forceinline__ void compute_pair(const Smem& S, const RegWeights<NT>& W, int sm,
                                              int s0, int sp, int ry, int lane, int c0, double& a0,
                                              double& a1) {
   const int slots[3] = {sm, s0, sp};
@@ -266,6 +266,146 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream3d(const __grid_constant_
   }
 }
 
+
+// Warp-specialised form of the same sweep (used for the 7-point star): warp 8
+// produces, warps 0..7 consume, and no CTA-wide barrier remains in the loop.
+//   - producer: for plane g (slot g % 4) it waits until the 8 consumer warps
+//     have released plane g-4 (`empty` mbarrier, 8 arrivals), then lane 0
+//     posts the TMA boxes with their byte count and every lane loads part of
+//     the x-halo into shared memory and arrives on `full` (1 + 32 arrivals);
+//   - consumers: wait on `full` for the planes a step reads, compute, and
+//     release plane k-1 with one arrival per warp on `empty`.
+template <bool BOX>
+struct __align__(128) WsSmem {
+  double plane[kSlots][Tile<BOX>::Rows][kTX];
+  double halo[kSlots][2][Tile<BOX>::Rows];
+  uint64_t full[kSlots];
+  uint64_t empty[kSlots];
+  int abort;
+};
+
+template <int NT, bool BOX, bool PERIODIC>
+__global__ void __launch_bounds__(kThreads + 32, BOX ? 2 : 3)
+    k_stream3d_ws(const __grid_constant__ StreamParams<NT> P) {
+  constexpr int kTY = Tile<BOX>::TY;
+  constexpr int kRows = Tile<BOX>::Rows;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  WsSmem<BOX>& S = *reinterpret_cast<WsSmem<BOX>*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSlots; ++s) {
+      mbar_init(&S.full[s], 33);
+      mbar_init(&S.empty[s], 8);
+    }
+    S.abort = 0;
+    fence_mbar_init();
+    prefetch_tmap(&P.map_row);
+    prefetch_tmap(&P.map_main);
+  }
+  __syncthreads();
+  const long long G = gridDim.x;
+  const long long f_begin = P.work * blockIdx.x / G;
+  const long long f_end = P.work * (blockIdx.x + 1) / G;
+  volatile int* abort_flag = &S.abort;
+
+  if (warp == 8) {
+    // ------------------------------------------------------------ producer
+    uint32_t g = 0;
+    for (long long f = f_begin; f < f_end;) {
+      const int tile = (int)(f / P.nz);
+      const int za = (int)(f % P.nz);
+      const long long rem = f_end - f;
+      const int zb = (long long)P.nz < za + rem ? P.nz : (int)(za + rem);
+      f += zb - za;
+      const int x0 = (tile % P.tiles_x) * kTX;
+      const int y0 = (tile / P.tiles_x) * kTY;
+      const int nplanes = zb - za + 2;
+      for (int j = 0; j < nplanes; ++j, ++g) {
+        const int slot = g % kSlots;
+        if (g >= kSlots &&
+            !mbar_wait_bounded(&S.empty[slot], ((g - kSlots) / kSlots) & 1, kWaitLimitNs)) {
+          *abort_flag = 1;
+          atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
+        }
+        if (*abort_flag) {
+          // let the copies already posted land (bounded), then leave
+          for (uint32_t q = g > kSlots ? g - kSlots : 0; q < g; ++q)
+            mbar_wait_bounded(&S.full[q % kSlots], (q / kSlots) & 1, kWaitLimitNs);
+          return;
+        }
+        const int z = za - 1 + j;
+        if (lane == 0) {
+          fence_proxy_async_smem();
+          issue_plane<NT, BOX, PERIODIC>(S, P, slot, z, y0, x0);
+        }
+        for (int h = lane; h < 2 * kRows; h += 32) {
+          const int side = h / kRows, r = h % kRows;
+          int x = side ? x0 + kTX : x0 - 1;
+          int y = y0 - 1 + r, zz = z;
+          double v = 0.0;
+          if (PERIODIC) {
+            x = wrap_or_keep(x, P.nx, true);
+            y = wrap_or_keep(y, P.ny, true);
+            zz = wrap_or_keep(zz, P.nz, true);
+            v = __ldg(P.src + ((int64_t)zz * P.ny + y) * P.nx + x);
+          } else if ((unsigned)x < (unsigned)P.nx && (unsigned)y < (unsigned)P.ny &&
+                     (unsigned)zz < (unsigned)P.nz) {
+            v = __ldg(P.src + ((int64_t)zz * P.ny + y) * P.nx + x);
+          }
+          S.halo[slot][side][r] = v;
+        }
+        mbar_arrive(&S.full[slot]);
+      }
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  RegWeights<NT> W;
+  W.load(P.wdev);
+  uint32_t seq = 0;
+  for (long long f = f_begin; f < f_end;) {
+    const int tile = (int)(f / P.nz);
+    const int za = (int)(f % P.nz);
+    const long long rem = f_end - f;
+    const int zb = (long long)P.nz < za + rem ? P.nz : (int)(za + rem);
+    f += zb - za;
+    const int x0 = (tile % P.tiles_x) * kTX;
+    const int y0 = (tile / P.tiles_x) * kTY;
+    const int nplanes = zb - za + 2;
+    const uint32_t base = seq;
+    seq += nplanes;
+    for (int k = 1; k <= nplanes - 2; ++k) {
+      const int jfirst = (k == 1) ? 0 : k + 1;
+      for (int j = jfirst; j <= k + 1; ++j) {
+        const uint32_t gq = base + j;
+        if (!mbar_wait_bounded(&S.full[gq % kSlots], (gq / kSlots) & 1, kWaitLimitNs)) {
+          *abort_flag = 1;
+          atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
+        }
+      }
+      if (*abort_flag) return;
+      const int sm = (base + k - 1) % kSlots, s0 = (base + k) % kSlots, sp = (base + k + 1) % kSlots;
+      const int z = za + k - 1;
+#pragma unroll
+      for (int r = 0; r < Tile<BOX>::RowsPerWarp; ++r) {
+        const int ry = warp + 8 * r;
+        double a0 = 0.0, a1 = 0.0;
+        compute_pair<NT, BOX>(S, W, sm, s0, sp, ry, lane, (2 * r) & 3, a0, a1);
+        const int y = y0 + ry, x = x0 + 2 * lane;
+        if (y < P.ny && x < P.nx) st_global_v2(P.dst + ((int64_t)z * P.ny + y) * P.nx + x, a0, a1);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.empty[sm]);  // plane k-1 is not read again
+    }
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&S.empty[(base + nplanes - 2) % kSlots]);
+      mbar_arrive(&S.empty[(base + nplanes - 1) % kSlots]);
+    }
+  }
+}
+
 bool encode_3d(CUtensorMap* map, const double* base, int nz, int ny, int nx, int box_y) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
@@ -281,6 +421,23 @@ bool encode_3d(CUtensorMap* map, const double* base, int nz, int ny, int nx, int
 
 template <bool BOX>
 constexpr size_t smem_bytes() { return sizeof(StreamSmem<BOX>); }
+template <bool BOX>
+constexpr size_t ws_smem_bytes() { return sizeof(WsSmem<BOX>); }
+
+template <int NT, bool BOX, bool PERIODIC>
+int ws_occupancy() {
+  static int n = -1;
+  if (n < 0) {
+    cudaFuncSetAttribute(k_stream3d_ws<NT, BOX, PERIODIC>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    if (cudaFuncSetAttribute(k_stream3d_ws<NT, BOX, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ws_smem_bytes<BOX>()) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream3d_ws<NT, BOX, PERIODIC>, kThreads + 32,
+                                                      ws_smem_bytes<BOX>()) != cudaSuccess)
+      n = 0;
+  }
+  return n;
+}
 
 template <int NT, bool BOX, bool PERIODIC>
 int occupancy() {
@@ -315,6 +472,16 @@ cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, doubl
   P.work = (long long)P.tiles_x * P.tiles_y * g.nz;
   P.status = status;
   P.wdev = wdev;
+  if constexpr (!BOX) {
+    // the 7-point star: warp-specialised producer / consumer pipeline
+    int occ = ws_occupancy<NT, BOX, PERIODIC>();
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    long long grid = (long long)sms * occ;
+    if (grid > P.work) grid = P.work;
+    k_stream3d_ws<NT, BOX, PERIODIC><<<(unsigned)grid, kThreads + 32, ws_smem_bytes<BOX>(), stream>>>(P);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+  }
   int occ = occupancy<NT, BOX, PERIODIC>();
   if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)sms * occ;

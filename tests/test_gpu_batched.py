@@ -83,3 +83,19 @@ def test_full_96_item_batch(st):
         ref = oracle.run(grids[i], synth.heat_weights(2, a), 1, DIRICHLET, T, nthreads=0)
         assert normwise_rel(dev[i].cpu().numpy(), ref) <= TOL
     b.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(st):
+    """Failure detection without a GPU fault: a device-wide barrier that can
+    never complete gives up after its 20 ms wall-time limit, the kernel
+    reports STENCIL_ERR_TIMEOUT, and the next sweep runs normally."""
+    import torch
+    assert st.stencil_selftest_barrier_timeout(20.0) == st.ERR_TIMEOUT
+    g0 = synth.uniform(31, (40, 70))
+    d = torch.from_numpy(g0.copy()).cuda()
+    b = st.Batch([d], [0.1], [5])
+    b.run()
+    assert b.status() == 0
+    ref = oracle.run(g0, synth.heat_weights(2, 0.1), 1, DIRICHLET, 5)
+    assert normwise_rel(d.cpu().numpy(), ref) <= TOL
+    b.close()
