@@ -3,23 +3,25 @@
 //
 // One step of u'(x) = sum_o w_o u~(x+o) (paper Sec. 2.1, Listing 1).  The
 // paper's GPU design keeps a tile in shared memory so that global accesses
-// are coalesced (Sec. 4.2, checkerboard blocking); here the tile is a 64 x 16
-// (x, y) slab that advances plane by plane along z:
-//   - a 4-slot ring of planes (rows y0-1 .. y0+16, columns x0 .. x0+63), each
-//     filled by three TMA boxes (halo row above, 16 rows, halo row below)
+// are coalesced (Sec. 4.2, checkerboard blocking); here the tile is a 64 x TY
+// (x, y) slab (TY = 32 for the 7-point star, 16 for the 27-point box) that
+// advances plane by plane along z:
+//   - a 4-slot ring of planes (rows y0-1 .. y0+TY, columns x0 .. x0+63), each
+//     filled by three TMA boxes (halo row above, TY rows, halo row below)
 //     whose y and z coordinates are wrapped for periodic grids; out-of-range
 //     boxes read zeros, which is exactly the Dirichlet-zero ghost rule;
-//   - two planes are in flight while the CTA computes a third (double
-//     buffering: mbarrier transaction counts signal arrival);
-//   - the x-halo columns (x0-1 and x0+64) are 2 x 18 plain loads per plane,
-//     issued one plane ahead into registers;
+//   - a producer warp posts the TMA boxes and loads the x-halo columns
+//     (x0-1 and x0+64) with plain loads, while 8 consumer warps compute; two
+//     planes are in flight while a third is computed (mbarrier transaction
+//     counts signal arrival, per-slot `empty` barriers release slots);
 //   - every lane owns two adjacent x cells (one 16-byte shared load, one
 //     16-byte global store); the x-1 / x+2 neighbours come from the adjacent
 //     lanes by warp shuffle, the warp's edge lanes take the halo column;
-//   - every warp owns rows w and w+8 of the tile: four independent FMA chains
-//     per thread keep the FP64 pipe, the bound of this kernel, busy.
+//   - every consumer warp owns rows w, w+8, ...: 4 (box) or 8 (star)
+//     independent FMA chains per thread keep the FP64 pipe, the bound of this
+//     kernel, busy.
 // The taps are applied in the same lexicographic order as the direct sweep,
-// starting with a plain multiply, so the two kernels agree bitwise.
+// starting with an FMA onto zero, so the two kernels agree bitwise.
 // Work split: the (tile, z) planes of the grid are cut into equal contiguous
 // ranges, one per persistent CTA (a CTA may finish one tile's z-column and
 // start the next one's).
@@ -66,14 +68,6 @@ struct Tile {
   static constexpr uint32_t PlaneBytes = Rows * kTX * sizeof(double);
 };
 
-template <bool BOX>
-struct __align__(128) StreamSmem {
-  double plane[kSlots][Tile<BOX>::Rows][kTX];  // TMA destination
-  double halo[kSlots][2][Tile<BOX>::Rows];     // x-halo columns: [0] = x0-1, [1] = x0+64
-  uint64_t full[kSlots];
-  int abort;
-};
-
 template <int NT>
 struct StreamParams {
   CUtensorMap map_row;   // box {64, 1, 1} over src
@@ -90,37 +84,6 @@ struct StreamParams {
 __device__ __forceinline__ int wrap_or_keep(int c, int n, bool periodic) {
   if (!periodic) return c;
   return c < 0 ? c + n : (c >= n ? c - n : c);
-}
-
-// Loads (into a register) the x-halo value this thread is responsible for in
-// plane z, or 0 when the thread holds none.  Threads 0 .. 2*Rows-1 cover the
-// left (x0-1) and right (x0+64) columns for rows y0-1 .. y0+TY.
-template <bool BOX, bool PERIODIC>
-__device__ __forceinline__ double load_halo(const double* __restrict__ src, int z, int y0, int x0,
-                                            int nz, int ny, int nx) {
-  constexpr int kRows = Tile<BOX>::Rows;
-  const int t = threadIdx.x;
-  if (t >= 2 * kRows) return 0.0;
-  const int side = t / kRows, r = t % kRows;
-  int x = side ? x0 + kTX : x0 - 1;
-  int y = y0 - 1 + r;
-  int zz = z;
-  if (PERIODIC) {
-    x = wrap_or_keep(x, nx, true);
-    y = wrap_or_keep(y, ny, true);
-    zz = wrap_or_keep(zz, nz, true);
-  } else if ((unsigned)x >= (unsigned)nx || (unsigned)y >= (unsigned)ny ||
-             (unsigned)zz >= (unsigned)nz) {
-    return 0.0;
-  }
-  return __ldg(src + ((int64_t)zz * ny + y) * nx + x);
-}
-
-template <bool BOX>
-__device__ __forceinline__ void store_halo(StreamSmem<BOX>& S, int slot, double v) {
-  constexpr int kRows = Tile<BOX>::Rows;
-  const int t = threadIdx.x;
-  if (t < 2 * kRows) S.halo[slot][t / kRows][t % kRows] = v;
 }
 
 template <int NT, bool BOX, bool PERIODIC, class Smem>
@@ -178,94 +141,6 @@ __device__ __forceinline__ void compute_pair(const Smem& S, const RegWeights<NT>
     }
   }
 }
-
-template <int NT, bool BOX, bool PERIODIC>
-__global__ void __launch_bounds__(kThreads, 2) k_stream3d(const __grid_constant__ StreamParams<NT> P) {
-  constexpr int kTY = Tile<BOX>::TY;
-  // dynamic shared memory (the 32-row star tile needs 70 KB); the kernel has
-  // no static shared memory, so the dynamic window starts at the (1 KB
-  // aligned) base of the CTA's shared memory, as the TMA destinations need
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  StreamSmem<BOX>& S = *reinterpret_cast<StreamSmem<BOX>*>(smem_raw);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  RegWeights<NT> W;
-  W.load(P.wdev);
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kSlots; ++s) mbar_init(&S.full[s], 1);
-    S.abort = 0;
-    fence_mbar_init();
-    prefetch_tmap(&P.map_row);
-    prefetch_tmap(&P.map_main);
-  }
-  __syncthreads();
-  const long long G = gridDim.x;
-  const long long f_begin = P.work * blockIdx.x / G;
-  const long long f_end = P.work * (blockIdx.x + 1) / G;
-  uint32_t seq = 0;  // planes issued by this CTA: slot = seq % 4, phase parity = (seq / 4) & 1
-  for (long long f = f_begin; f < f_end;) {
-    const int tile = (int)(f / P.nz);
-    const int za = (int)(f % P.nz);
-    const long long rem = f_end - f;
-    const int zb = (long long)P.nz < za + rem ? P.nz : (int)(za + rem);
-    f += zb - za;
-    const int x0 = (tile % P.tiles_x) * kTX;
-    const int y0 = (tile / P.tiles_x) * kTY;
-    const int nplanes = zb - za + 2;  // planes za-1 .. zb
-    const uint32_t base = seq;
-    seq += nplanes;
-    if (threadIdx.x == 0) {
-      for (int j = 0; j < kSlots && j < nplanes; ++j)
-        issue_plane<NT, BOX, PERIODIC>(S, P, (base + j) % kSlots, za - 1 + j, y0, x0);
-    }
-    for (int j = 0; j < 3; ++j)
-      store_halo<BOX>(S, (base + j) % kSlots,
-                      load_halo<BOX, PERIODIC>(P.src, za - 1 + j, y0, x0, P.nz, P.ny, P.nx));
-    double halo_next = 0.0;
-    if (nplanes > 3) halo_next = load_halo<BOX, PERIODIC>(P.src, za + 2, y0, x0, P.nz, P.ny, P.nx);
-    __syncthreads();
-    int issued = min(kSlots, nplanes) - 1;  // highest plane index issued so far
-    for (int k = 1; k <= nplanes - 2; ++k) {
-      // wait for the planes this step reads (each plane is waited on once)
-      const int jfirst = (k == 1) ? 0 : k + 1;
-      for (int j = jfirst; j <= k + 1; ++j) {
-        const uint32_t g = base + j;
-        if (!mbar_wait_bounded(&S.full[g % kSlots], (g / kSlots) & 1, kWaitLimitNs)) {
-          S.abort = 1;
-          atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
-        }
-      }
-      const int sm = (base + k - 1) % kSlots, s0 = (base + k) % kSlots, sp = (base + k + 1) % kSlots;
-      const int z = za + k - 1;
-#pragma unroll
-      for (int r = 0; r < Tile<BOX>::RowsPerWarp; ++r) {
-        const int ry = warp + 8 * r;
-        double a0 = 0.0, a1 = 0.0;
-        compute_pair<NT, BOX>(S, W, sm, s0, sp, ry, lane, (2 * r) & 3, a0, a1);
-        const int y = y0 + ry, x = x0 + 2 * lane;
-        if (y < P.ny && x < P.nx) st_global_v2(P.dst + ((int64_t)z * P.ny + y) * P.nx + x, a0, a1);
-      }
-      if (k + 2 <= nplanes - 1) store_halo<BOX>(S, (base + k + 2) % kSlots, halo_next);
-      if (k + 3 <= nplanes - 1)
-        halo_next = load_halo<BOX, PERIODIC>(P.src, za + k + 2, y0, x0, P.nz, P.ny, P.nx);
-      __syncthreads();
-      if (S.abort) {
-        // a wait gave up: let the copies still in flight land (bounded), then leave
-        if (threadIdx.x == 0)
-          for (int j = k + 2; j <= issued; ++j)
-            mbar_wait_bounded(&S.full[(base + j) % kSlots], ((base + j) / kSlots) & 1, kWaitLimitNs);
-        return;  // uniform: every thread read the flag after the barrier
-      }
-      if (k + 3 <= nplanes - 1) {
-        if (threadIdx.x == 0) {
-          fence_proxy_async_smem();
-          issue_plane<NT, BOX, PERIODIC>(S, P, (base + k + 3) % kSlots, za + k + 2, y0, x0);
-        }
-        issued = k + 3;
-      }
-    }
-  }
-}
-
 
 // Warp-specialised form of the same sweep (used for the 7-point star): warp 8
 // produces, warps 0..7 consume, and no CTA-wide barrier remains in the loop.
@@ -420,8 +295,6 @@ bool encode_3d(CUtensorMap* map, const double* base, int nz, int ny, int nx, int
 }
 
 template <bool BOX>
-constexpr size_t smem_bytes() { return sizeof(StreamSmem<BOX>); }
-template <bool BOX>
 constexpr size_t ws_smem_bytes() { return sizeof(WsSmem<BOX>); }
 
 template <int NT, bool BOX, bool PERIODIC>
@@ -434,21 +307,6 @@ int ws_occupancy() {
                              (int)ws_smem_bytes<BOX>()) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream3d_ws<NT, BOX, PERIODIC>, kThreads + 32,
                                                       ws_smem_bytes<BOX>()) != cudaSuccess)
-      n = 0;
-  }
-  return n;
-}
-
-template <int NT, bool BOX, bool PERIODIC>
-int occupancy() {
-  static int n = -1;
-  if (n < 0) {
-    cudaFuncSetAttribute(k_stream3d<NT, BOX, PERIODIC>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    if (cudaFuncSetAttribute(k_stream3d<NT, BOX, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<BOX>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream3d<NT, BOX, PERIODIC>, kThreads,
-                                                      smem_bytes<BOX>()) != cudaSuccess)
       n = 0;
   }
   return n;
@@ -472,21 +330,11 @@ cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, doubl
   P.work = (long long)P.tiles_x * P.tiles_y * g.nz;
   P.status = status;
   P.wdev = wdev;
-  if constexpr (!BOX) {
-    // the 7-point star: warp-specialised producer / consumer pipeline
-    int occ = ws_occupancy<NT, BOX, PERIODIC>();
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    long long grid = (long long)sms * occ;
-    if (grid > P.work) grid = P.work;
-    k_stream3d_ws<NT, BOX, PERIODIC><<<(unsigned)grid, kThreads + 32, ws_smem_bytes<BOX>(), stream>>>(P);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    return cudaGetLastError();
-  }
-  int occ = occupancy<NT, BOX, PERIODIC>();
+  int occ = ws_occupancy<NT, BOX, PERIODIC>();
   if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)sms * occ;
   if (grid > P.work) grid = P.work;
-  k_stream3d<NT, BOX, PERIODIC><<<(unsigned)grid, kThreads, smem_bytes<BOX>(), stream>>>(P);
+  k_stream3d_ws<NT, BOX, PERIODIC><<<(unsigned)grid, kThreads + 32, ws_smem_bytes<BOX>(), stream>>>(P);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
