@@ -7,8 +7,10 @@
 // so the row above / below any row is simply the previous / next ring row;
 // one TMA box (16 rows x 64 columns, y wrapped for periodic grids, zeros out
 // of range for Dirichlet) fills a block, two blocks are in flight while the
-// CTA computes a third.  x-halo columns come from plain loads one block ahead;
-// each lane owns two adjacent columns (16-byte shared loads and global
+// CTA computes a third.  A producer warp posts the TMA boxes and loads the
+// x-halo columns with plain loads; eight consumer warps compute, releasing
+// ring slots through per-slot mbarriers (no CTA-wide barrier in the loop).
+// Each lane owns two adjacent columns (16-byte shared loads and global
 // stores) and exchanges its edge values with the adjacent lanes by shuffle.
 //
 // Two arithmetic forms:
@@ -47,7 +49,8 @@ template <int R>
 struct __align__(128) Smem2 {
   double row[kRing][kTX];    // TMA destination (block s = rows 16s .. 16s+15)
   double halo[kRing][2 * R]; // columns x0-R .. x0-1 and x0+64 .. x0+63+R of each ring row
-  uint64_t full[kSlots];
+  uint64_t full[kSlots];     // TMA bytes + producer arrivals
+  uint64_t empty[kSlots];    // one arrival per consumer warp
   int abort;
 };
 
@@ -64,31 +67,6 @@ struct Params2 {
 };
 
 __device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
-
-// Thread t < 2R*16 loads one halo value: row t % 16 of block `blk`, halo
-// column h = t / 16 (0 .. R-1: x0-R+h; R .. 2R-1: x0+64+h-R).
-template <int R, bool PERIODIC>
-__device__ __forceinline__ double load_halo2(const double* __restrict__ src, int blk, int x0, int ny,
-                                             int nx) {
-  const int t = threadIdx.x;
-  if (t >= 2 * R * kRB) return 0.0;
-  const int h = t / kRB, r = t % kRB;
-  int x = h < R ? x0 - R + h : x0 + kTX + (h - R);
-  int y = blk * kRB + r;
-  if (PERIODIC) {
-    x = wrapc(x, nx);
-    y = wrapc(y, ny);
-  } else if ((unsigned)x >= (unsigned)nx || (unsigned)y >= (unsigned)ny) {
-    return 0.0;
-  }
-  return __ldg(src + (int64_t)y * nx + x);
-}
-
-template <int R>
-__device__ __forceinline__ void store_halo2(Smem2<R>& S, int slot, double v) {
-  const int t = threadIdx.x;
-  if (t < 2 * R * kRB) S.halo[slot * kRB + t % kRB][t / kRB] = v;
-}
 
 template <int NT, int R, bool PERIODIC>
 __device__ __forceinline__ void issue_block(Smem2<R>& S, const Params2<NT>& P, int slot, int blk,
@@ -180,14 +158,20 @@ __device__ __forceinline__ void quad_equal(const Smem2<1>& S, const RegWeights<N
   out[1][1] = fma(W.w[5], R1, wt1);
 }
 
+// Warp-specialised: warp 8 produces (waits for the consumers to release
+// block g-4 on the slot's `empty` barrier, posts the TMA box with its byte
+// count, loads its part of the x-halo columns, arrives on `full`); warps 0..7
+// consume (wait on `full` for the blocks a step reads, compute, release block
+// k-1 with one arrival per warp).  No CTA-wide barrier in the loop.
 template <int NT, bool BOX, int R, bool PERIODIC, bool EQUAL>
-__global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant__ Params2<NT> P) {
+__global__ void __launch_bounds__(kThreads + 32, 2) k_stream2d(const __grid_constant__ Params2<NT> P) {
   __shared__ Smem2<R> S;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  RegWeights<NT> W;
-  W.load(P.wdev);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kSlots; ++s) mbar_init(&S.full[s], 1);
+    for (int s = 0; s < kSlots; ++s) {
+      mbar_init(&S.full[s], 33);
+      mbar_init(&S.empty[s], 8);
+    }
     S.abort = 0;
     fence_mbar_init();
     prefetch_tmap(&P.map);
@@ -196,6 +180,59 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant_
   const long long G = gridDim.x;
   const long long f_begin = P.work * blockIdx.x / G;
   const long long f_end = P.work * (blockIdx.x + 1) / G;
+  volatile int* abort_flag = &S.abort;
+
+  if (warp == 8) {
+    // ------------------------------------------------------------ producer
+    uint32_t g = 0;
+    for (long long f = f_begin; f < f_end;) {
+      const int strip = (int)(f / P.blocks);
+      const int ba = (int)(f % P.blocks);
+      const long long rem = f_end - f;
+      const int bb = (long long)P.blocks < ba + rem ? P.blocks : (int)(ba + rem);
+      f += bb - ba;
+      const int x0 = strip * kTX;
+      const int nblk = bb - ba + 2;
+      for (int j = 0; j < nblk; ++j, ++g) {
+        const int slot = g % kSlots;
+        if (g >= kSlots &&
+            !mbar_wait_bounded(&S.empty[slot], ((g - kSlots) / kSlots) & 1, kWaitLimitNs)) {
+          *abort_flag = 1;
+          atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
+        }
+        if (*abort_flag) {
+          for (uint32_t q = g > kSlots ? g - kSlots : 0; q < g; ++q)
+            mbar_wait_bounded(&S.full[q % kSlots], (q / kSlots) & 1, kWaitLimitNs);
+          return;
+        }
+        const int blk = ba - 1 + j;
+        if (lane == 0) {
+          fence_proxy_async_smem();
+          issue_block<NT, R, PERIODIC>(S, P, slot, blk, x0);
+        }
+        for (int t = lane; t < 2 * R * kRB; t += 32) {
+          const int h = t / kRB, r = t % kRB;
+          int x = h < R ? x0 - R + h : x0 + kTX + (h - R);
+          int y = blk * kRB + r;
+          double v = 0.0;
+          if (PERIODIC) {
+            x = wrapc(x, P.nx);
+            y = wrapc(y, P.ny);
+            v = __ldg(P.src + (int64_t)y * P.nx + x);
+          } else if ((unsigned)x < (unsigned)P.nx && (unsigned)y < (unsigned)P.ny) {
+            v = __ldg(P.src + (int64_t)y * P.nx + x);
+          }
+          S.halo[slot * kRB + r][h] = v;
+        }
+        mbar_arrive(&S.full[slot]);
+      }
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  RegWeights<NT> W;
+  W.load(P.wdev);
   uint32_t seq = 0;
   for (long long f = f_begin; f < f_end;) {
     const int strip = (int)(f / P.blocks);
@@ -207,24 +244,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant_
     const int nblk = bb - ba + 2;  // blocks ba-1 .. bb
     const uint32_t base = seq;
     seq += nblk;
-    if (threadIdx.x == 0)
-      for (int j = 0; j < kSlots && j < nblk; ++j)
-        issue_block<NT, R, PERIODIC>(S, P, (base + j) % kSlots, ba - 1 + j, x0);
-    for (int j = 0; j < 3; ++j)
-      store_halo2<R>(S, (base + j) % kSlots, load_halo2<R, PERIODIC>(P.src, ba - 1 + j, x0, P.ny, P.nx));
-    double halo_next = 0.0;
-    if (nblk > 3) halo_next = load_halo2<R, PERIODIC>(P.src, ba + 2, x0, P.ny, P.nx);
-    __syncthreads();
-    int issued = min(kSlots, nblk) - 1;
     for (int k = 1; k <= nblk - 2; ++k) {
       const int jfirst = (k == 1) ? 0 : k + 1;
       for (int j = jfirst; j <= k + 1; ++j) {
-        const uint32_t g = base + j;
-        if (!mbar_wait_bounded(&S.full[g % kSlots], (g / kSlots) & 1, kWaitLimitNs)) {
-          S.abort = 1;
+        const uint32_t gq = base + j;
+        if (!mbar_wait_bounded(&S.full[gq % kSlots], (gq / kSlots) & 1, kWaitLimitNs)) {
+          *abort_flag = 1;
           atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
         }
       }
+      if (*abort_flag) return;
       const int slot = (base + k) % kSlots;
       const int blk = ba + k - 1;
       const int x = x0 + 2 * lane;
@@ -247,22 +276,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_stream2d(const __grid_constant_
           if (y < P.ny && x < P.nx) st_global_v2(P.dst + (int64_t)y * P.nx + x, a0, a1);
         }
       }
-      if (k + 2 <= nblk - 1) store_halo2<R>(S, (base + k + 2) % kSlots, halo_next);
-      if (k + 3 <= nblk - 1) halo_next = load_halo2<R, PERIODIC>(P.src, ba + k + 2, x0, P.ny, P.nx);
-      __syncthreads();
-      if (S.abort) {
-        if (threadIdx.x == 0)
-          for (int j = k + 2; j <= issued; ++j)
-            mbar_wait_bounded(&S.full[(base + j) % kSlots], ((base + j) / kSlots) & 1, kWaitLimitNs);
-        return;
-      }
-      if (k + 3 <= nblk - 1) {
-        if (threadIdx.x == 0) {
-          fence_proxy_async_smem();
-          issue_block<NT, R, PERIODIC>(S, P, (base + k + 3) % kSlots, ba + k + 2, x0);
-        }
-        issued = k + 3;
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.empty[(base + k - 1) % kSlots]);  // block k-1 is not read again
+    }
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&S.empty[(base + nblk - 2) % kSlots]);
+      mbar_arrive(&S.empty[(base + nblk - 1) % kSlots]);
     }
   }
 }
@@ -295,13 +315,13 @@ cudaError_t launch2(const Geom& g, const double* wdev, const double* src, double
   P.wdev = wdev;
   static int occ = -1;
   if (occ < 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream2d<NT, BOX, R, PERIODIC, EQUAL>, kThreads,
-                                                    0) != cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream2d<NT, BOX, R, PERIODIC, EQUAL>,
+                                                    kThreads + 32, 0) != cudaSuccess)
     occ = 0;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)sms * occ;
   if (grid > P.work) grid = P.work;
-  k_stream2d<NT, BOX, R, PERIODIC, EQUAL><<<(unsigned)grid, kThreads, 0, stream>>>(P);
+  k_stream2d<NT, BOX, R, PERIODIC, EQUAL><<<(unsigned)grid, kThreads + 32, 0, stream>>>(P);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
