@@ -8,7 +8,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -153,6 +156,18 @@ void build_taps(stencil_plan_s* p, const double* w) {
   }
 }
 
+std::string device_name();
+
+std::string plan_key(const stencil_plan_s* p) {
+  char buf[256];
+  bool equal = p->shape == Shape::kBox;
+  for (int k = 1; equal && k < p->taps.n; ++k) equal = p->taps.w[k] == p->taps.w[0];
+  std::snprintf(buf, sizeof(buf), "%s/d%d/%dx%dx%d/r%d/%s%s/b%d", device_name().c_str(), p->ndim, p->g.nz,
+                p->g.ny, p->g.nx, p->radius, p->shape == Shape::kBox ? "box" : "star", equal ? "eq" : "",
+                p->boundary);
+  return buf;
+}
+
 int ensure(double** buf, size_t count, const char* what) {
   if (*buf) return STENCIL_OK;
   cudaError_t e = cudaMalloc((void**)buf, count * sizeof(double));
@@ -172,6 +187,73 @@ int sm_count() {
     if (n <= 0) n = 1;
   }
   return n;
+}
+
+// ------------------------------------------------------------ tuning record
+// Process-wide record of autotuned choices, keyed by the GPU name and the
+// plan's shape (ndim, dims, radius, stencil class, equal-weight box,
+// boundary).  STENCIL_TUNE_CACHE=<file> persists it across processes (one
+// line per key: key Tb variant rate); STENCIL_TUNE=off ignores it,
+// STENCIL_TUNE=full tunes a plan on its first run when no record exists.
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;
+bool g_tune_loaded = false;
+
+std::string device_name() {
+  static std::string name;
+  if (name.empty()) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+      name = prop.name;
+    else
+      name = "unknown";
+    for (char& c : name)
+      if (c == ' ') c = '_';
+  }
+  return name;
+}
+
+std::string tune_mode() {
+  const char* m = std::getenv("STENCIL_TUNE");
+  return m ? std::string(m) : std::string("cached");
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("STENCIL_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char key[512];
+  int tb, v;
+  double rate;
+  while (std::fscanf(f, "%511s %d %d %lf", key, &tb, &v, &rate) == 4)
+    if (tb > 0 && v > 0 && v < kVariantCount) g_tune[key] = {tb, v};
+  std::fclose(f);
+}
+
+void tune_store(const std::string& key, int tb, int v, double rate) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  g_tune[key] = {tb, v};
+  const char* path = std::getenv("STENCIL_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %.3f\n", key.c_str(), tb, v, rate);
+  std::fclose(f);
+}
+
+bool tune_lookup(const std::string& key, int& tb, int& v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return false;
+  tb = it->second.first;
+  v = it->second.second;
+  return true;
 }
 
 // The kernel (and Tb) a constant-weight plan uses when nothing was tuned or
@@ -211,6 +293,7 @@ void choose(const stencil_plan_s* p, int& Tb, int& variant) {
     variant = p->tuned_variant;
     return;
   }
+  if (tune_mode() != "off" && tune_lookup(plan_key(p), Tb, variant)) return;
   variant = default_variant(p, &Tb);
 }
 
@@ -235,6 +318,21 @@ int ensure_status(stencil_plan_s* p) {
 
 int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   int Tb, variant;
+  if (tune_mode() == "full" && p->user_Tb == 0 && p->user_variant == 0 && p->tuned_Tb == 0) {
+    int tb0, v0;
+    if (!tune_lookup(plan_key(p), tb0, v0)) {
+      // tune on a scratch copy of the grid (the candidates' runs destroy it)
+      double* scratch = nullptr;
+      if (cudaMalloc(&scratch, (size_t)p->cells() * sizeof(double)) == cudaSuccess) {
+        cudaMemcpyAsync(scratch, d_grid, (size_t)p->cells() * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        stencil_autotune(p, scratch, 4, s, nullptr);
+        cudaStreamSynchronize(s);
+        cudaFree(scratch);
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
   choose(p, Tb, variant);
   const bool forced = p->user_Tb > 0 || p->user_variant > 0;
   int rc = ensure(&p->d_tmp, (size_t)p->cells(), "allocating the ping-pong buffer");
@@ -798,6 +896,7 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
   if (best < 0) return g_err.empty() ? fail(STENCIL_ERR_CUDA, "no candidate ran") : STENCIL_ERR_CUDA;
   p->tuned_Tb = best_c.Tb;
   p->tuned_variant = best_c.variant;
+  tune_store(plan_key(p), best_c.Tb, best_c.variant, best);
   if (best_gstencils) *best_gstencils = best;
   return STENCIL_OK;
 }

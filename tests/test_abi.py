@@ -85,3 +85,27 @@ def test_plan_lifecycle_and_tuning_checks_on_host(stencil):
     stencil.stencil_destroy(hv)
     with pytest.raises(stencil.StencilError):
         stencil.stencil_create_varcoef((4,), stencil.PERIODIC)
+
+
+def test_tuning_record_file_is_read(tmp_path):
+    """A record in STENCIL_TUNE_CACHE (key: GPU name, ndim, dims, radius,
+    stencil class, boundary) sets the choice of a new plan with that key;
+    STENCIL_TUNE=off ignores it.  Runs in child processes (the record is read
+    once per process)."""
+    import subprocess
+    import sys
+    code = ("import numpy as np, paper_2303_08365_gb300 as st\n"
+            "h = st.stencil_create((16, 32, 64), 1, np.ones(27) / 27, st.PERIODIC)\n"
+            "print(*st.stencil_get_tuning(h))\n")
+    cache = tmp_path / "tune.txt"
+    # without a GPU the device name reads 'unknown'
+    cache.write_text("unknown/d3/16x32x64/r1/boxeq/b1 2 3 12.5\n")
+    env = dict(os.environ, STENCIL_TUNE_CACHE=str(cache), PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    if out.stdout.split() == ["1", "2"]:
+        pytest.skip("a CUDA device is visible: the key carries its name")
+    assert out.stdout.split() == ["2", "3"]
+    env["STENCIL_TUNE"] = "off"
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
+    assert out.stdout.split() == ["1", "2"]

@@ -423,3 +423,15 @@ def test_fp32_twin_is_single_precision_and_close(st):
     err = normwise_rel(got, ref)
     assert 1e-9 < err <= 1e-5
     p.close()
+
+
+def test_tuning_record_is_shared_by_plans_with_the_same_key(st):
+    import torch
+    shape = (24, 64, 128)
+    w = synth.heat_weights(3, 0.1)
+    a = st.Plan(shape, 1, w, PERIODIC)
+    a.autotune(torch.from_numpy(synth.uniform(3, shape)).cuda(), 3)
+    b = st.Plan(shape, 1, w, PERIODIC)
+    assert b.get_tuning() == a.get_tuning()
+    a.close()
+    b.close()

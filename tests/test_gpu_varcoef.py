@@ -136,7 +136,7 @@ def test_autograd_function_matches_adjoint_and_oracle(st):
     loss = 0.5 * ((uT - TG) ** 2).sum()
     loss.backward()
     ref_loss, gu, gk = p.adjoint(cuda(u0), cuda(kappa), dt, TG, T, ckpt_every=ck)
-    assert abs(float(loss) - ref_loss) <= 1e-12 * ref_loss
+    assert abs(float(loss.detach()) - ref_loss) <= 1e-12 * ref_loss
     assert bool((U.grad == gu).all()) and bool((K.grad == gk).all())
     # linear functional L = sum(w u^T): lambda^T = w; the oracle sees target = u^T - w
     w = synth.normal(77, shape)
