@@ -194,18 +194,32 @@ def variant_kernel(variant, ndim):
     return variant
 
 
-def roofline(name, cells, T, ms, launches, peak_tflops, kernel):
+HBM_GBS = 6681.8  # MEASURED_PEAKS.json hbm_gbs (copy bandwidth on the GB300s)
+
+
+def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_cell=16,
+             instr=None):
+    """The stated roofline: min(FP64 peak / F, HBM bandwidth * Tb / bytes per
+    cell) in cell updates per second; `frac` = achieved FP64 flops / peak
+    (the FP64 term binds for every workload here)."""
     flops = FLOPS[name] * cells * T
     achieved = flops / (ms * 1e-3) / 1e12
     per_launch = FLOPS[name] * cells * T / max(launches, 1)
-    instr_rate = INSTR[name] * cells * T / (ms * 1e-3)       # FP64 instructions per second
+    instr = INSTR[name] if instr is None else instr
+    instr_rate = instr * cells * T / (ms * 1e-3)             # FP64 instructions per second
+    fp64_ceiling = peak_tflops * 1e12 / FLOPS[name] / 1e9
+    hbm_ceiling = HBM_GBS * 1e9 * Tb / bytes_per_cell / 1e9
+    rate = cells * T / (ms * 1e-3) / 1e9
     return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tflops, 4),
             "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-            "fp64_instr_per_cell": INSTR[name],
+            "fp64_ceiling_gstencil_per_s": round(fp64_ceiling, 3),
+            "hbm_ceiling_gstencil_per_s": round(hbm_ceiling, 3),
+            "frac_of_stated_roofline": round(rate / min(fp64_ceiling, hbm_ceiling), 4),
+            "fp64_instr_per_cell": round(instr, 4),
             "fp64_pipe_frac": round(instr_rate / (peak_tflops * 1e12 / 2), 4),
             "traffic": recorded_traffic(kernel, name),
             "algorithmic_flops_per_launch": per_launch,
-            "algorithmic_bytes_per_launch": 16 * cells * T / max(launches, 1),
+            "algorithmic_bytes_per_launch": bytes_per_cell * cells * T / Tb / max(launches, 1),
             "peak_source": "FP64 DFMA microbenchmark measured in this run (x2 flop/FMA); "
                            f"nominal {NOMINAL_FP64_TFLOPS:.3f} TFLOP/s"}
 
@@ -274,7 +288,7 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
             "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
             "Tb": tb, "variant": st.stencil_variant_name(v), "launches": launches,
             "roofline": roofline(name, cells, T, ms, launches, peak,
-                                 variant_kernel(st.stencil_variant_name(v), len(shape)))}
+                                 variant_kernel(st.stencil_variant_name(v), len(shape)), Tb=tb)}
 
 
 def form_batched(st, stream, peak, rank=0, world=1):
@@ -335,6 +349,11 @@ def form_adjoint(st, stream, peak):
     dt = 0.1 / float(kappa_h.max())
     plan = st.Plan.varcoef(shape, st.PERIODIC)
     cells = int(np.prod(shape))
+    # FP64 instructions per cell-step: forward 7, transposed step 7 + 3 faces x 3, and the
+    # recompute of every segment but the last (the forward sweep keeps that one's states)
+    nseg = -(-T // ck)
+    recomputed = (nseg - 1) * (ck - 1)
+    instr = 7 + 7 * recomputed / T + 7 + 9
     plan.adjoint(u0, kappa, dt, target, T, ckpt_every=ck, stream=stream)  # warm-up
     l0 = st.stencil_launch_count()
     ms = cuda_time(lambda: plan.adjoint(u0, kappa, dt, target, T, ckpt_every=ck, stream=stream), stream)
@@ -343,6 +362,22 @@ def form_adjoint(st, stream, peak):
     plan.run(grid, T, kappa, dt, stream=stream)
     ms_fwd = cuda_time(lambda: plan.run(grid, T, kappa, dt, stream=stream), stream)
     plan.close()
+    # the same gradients with every forward state kept (ckpt_every = 1: no
+    # recompute; T + 10 grids of scratch, 126 GiB here) when HBM holds it
+    store_all = None
+    need = (T + 10) * cells * 8
+    if torch.cuda.mem_get_info()[0] > 1.1 * need:
+        plan = st.Plan.varcoef(shape, st.PERIODIC)
+        plan.adjoint(u0, kappa, dt, target, T, ckpt_every=1, stream=stream)  # warm-up
+        ms_all = cuda_time(lambda: plan.adjoint(u0, kappa, dt, target, T, ckpt_every=1,
+                                                stream=stream), stream)
+        plan.close()
+        store_all = {"ms": round(ms_all, 3),
+                     "gstencil_per_s": round(cells * T / (ms_all * 1e-3) / 1e9, 3),
+                     "ratio_vs_forward": round(ms_all / ms_fwd, 3),
+                     "scratch_gib": round(need / 2**30, 1),
+                     "roofline": roofline("adjoint-7pt", cells, T, ms_all, 2 * T, peak, "adjoint",
+                                          bytes_per_cell=48 + 104, instr=7 + 7 + 9)}
     del u0, kappa, target, grid
     torch.cuda.empty_cache()
     return {"workload": "adjoint varcoef-7pt 256^3 T=1000 periodic, checkpoints every 32",
@@ -350,8 +385,15 @@ def form_adjoint(st, stream, peak):
             "forward_ms": round(ms_fwd, 3),
             "forward_gstencil_per_s": round(cells * T / (ms_fwd * 1e-3) / 1e9, 3),
             "ratio_vs_forward": round(ms / ms_fwd, 3), "launches": launches,
-            "roofline": roofline("adjoint-7pt", cells, T, ms, launches, peak, "adjoint"),
-            "forward_roofline": roofline("varcoef-7pt", cells, T, ms_fwd, T, peak, "varcoef")}
+            # bytes per cell-step: forward and recompute read u, c0, cx, cy, cz and write u'
+            # (48 each); the transposed step reads lambda, u, c0..cz, reads and writes the
+            # three face-gradient accumulators and writes lambda' (104; periodic grids have no
+            # ghost faces, so the fourth accumulator is untouched)
+            "roofline": roofline("adjoint-7pt", cells, T, ms, launches, peak, "adjoint",
+                                 bytes_per_cell=48 + 48 * recomputed / T + 104, instr=instr),
+            "forward_roofline": roofline("varcoef-7pt", cells, T, ms_fwd, T, peak, "varcoef",
+                                         bytes_per_cell=48),
+            "every_state_kept": store_all}
 
 
 # ------------------------------------------------------------ CPU baseline
@@ -370,10 +412,25 @@ def cpu_baseline(u0, budget_s=12.0):
     oracle.run(u0, w, 1, 1, steps, nthreads=cores)
     el = time.perf_counter() - t0
     cells = u0.size
+    # one core: the 2D 5-point 256^2 case in full, and the 27-point box with the 384^3
+    # case's weights and boundary on a 128^3 grid for 2 steps (a bounded sample)
+    single = []
+    for label, shp, w, bnd, T, u in (
+            ("heat2d-5pt 256^2 T=100 dirichlet0 (all steps)", (256, 256),
+             synth.heat_weights(2, 0.1), 0, 100, synth.uniform(synth.SEED_HEAT2D, (256, 256))),
+            ("box3d-27pt dirichlet0, 128^3 sample, 2 steps", (128, 128, 128),
+             synth.box_weights(3, seed=synth.SEED_BOX3D), 0, 2,
+             synth.normal(synth.SEED_BOX3D, (128, 128, 128)))):
+        t1 = time.perf_counter()
+        oracle.run(u, w, 1, bnd, T, nthreads=1)
+        e1 = time.perf_counter() - t1
+        single.append({"workload": label, "value": round(int(np.prod(shp)) * T / e1 / 1e9, 5),
+                       "unit": "GStencil/s", "seconds": round(e1, 3)})
     return {"value": round(cells * steps / el / 1e9, 5), "unit": "GStencil/s", "cores": cores,
             "kind": "oracle",
             "sample": f"{HEADLINE['name']} 512^3 periodic, {steps} of the 1000 steps "
-                      f"({el:.1f} s), plain C loop nest, OpenMP over rows"}
+                      f"({el:.1f} s), plain C loop nest, OpenMP over rows",
+            "single_core": single}
 
 
 # ------------------------------------------------------------------ main
@@ -407,7 +464,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": "heat3d-7pt 512^3 periodic (each step: 2 of the 1000 time steps)",
-                       "global_batch": 1, "seq_len": HEADLINE["T"], "parallelism": "none (host cores)",
+                       "shape": list(HEADLINE["shape"]), "T": HEADLINE["T"], "grids": 1,
+                       "parallelism": "none (host cores)",
                        "l2_flush": "input 1 GiB > L2"},
             "cpu_baseline": {"value": round(value, 5), "unit": "GStencil/s", "cores": cores,
                              "kind": "oracle",
@@ -520,7 +578,8 @@ def run_case(args):
             fn = lambda: plan.run(grid, args.T, kappa, dt, stream=stream)
         else:
             target = torch.from_numpy(synth.normal(synth.SEED_ADJOINT + 2, shape)).cuda()
-            fn = lambda: plan.adjoint(grid, kappa, dt, target, args.T, ckpt_every=0, stream=stream)
+            fn = lambda: plan.adjoint(grid, kappa, dt, target, args.T, ckpt_every=args.ckpt,
+                                      stream=stream)
     else:
         plan = st.Plan(shape, 1, w, bnd)
         if args.variant:
@@ -551,6 +610,8 @@ def main():
     ap.add_argument("--T", type=int, default=4)
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--Tb", type=int, default=0)
+    ap.add_argument("--ckpt", type=int, default=0, help="adjoint case: checkpoint interval "
+                    "(0 = about sqrt(T), 1 = keep every state)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)
@@ -579,12 +640,12 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "heat3d-7pt 512^3 T=1000 periodic, u0 = U[0,1) + sin mode (3,5,7)",
-                   "global_batch": world, "seq_len": T,
+                   "shape": list(HEADLINE["shape"]), "T": T, "grids": world,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "Tb": h["Tb"], "variant": h["variant"],
                    "l2_flush": "none needed: each launch streams 2 GiB > 129 MB L2"},
         "roofline": roofline("heat3d-7pt", cells, T, h["ms"], h["launches"] // args.steps,
-                             peak_tflops, variant_kernel(h["variant"], 3)),
+                             peak_tflops, variant_kernel(h["variant"], 3), Tb=h["Tb"]),
         "fp64_peak_tflops_measured": round(peak_tflops, 4),
         "e2e": {"value": round(e2e_value, 4), "unit": "GStencil/s",
                 "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"]},

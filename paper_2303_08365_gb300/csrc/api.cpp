@@ -730,11 +730,18 @@ int adjoint_core(stencil_plan_s* p, const double* d_u0, const double* d_kappa, d
   cudaError_t e = launch_varcoef_prepare(p->ndim, p->boundary, p->g, d_kappa, dt, cb, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the coefficient preparation");
   const size_t bytes = n * sizeof(double);
-  // forward sweep, keeping u at every multiple of c
+  // forward sweep, keeping u at every multiple of c; the states inside the
+  // last segment go straight to the segment buffer, so the reverse sweep
+  // starts without recomputing them
+  const int64_t nseg = (T + c - 1) / c;
+  const int64_t t_last = (nseg - 1) * c;  // first step of the last segment
   CUDA_TRY(cudaMemcpyAsync(ck, d_u0, bytes, cudaMemcpyDeviceToDevice, s), "copying u0");
   const double* src = ck;
   for (int64_t t = 0; t < T; ++t) {
-    double* dst = ((t + 1) % c == 0) ? ck + n * (size_t)((t + 1) / c) : (src == cur ? nxt : cur);
+    const int64_t k = t + 1;  // index of the state this step produces
+    double* dst = (k % c == 0)            ? ck + n * (size_t)(k / c)
+                  : (k > t_last && k < T) ? seg + n * (size_t)(k - t_last)
+                                          : (src == cur ? nxt : cur);
     e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, src, dst, p->d_w, s);
     if (e != cudaSuccess) return cuda_fail(e, "launching the forward step");
     src = dst;
@@ -748,12 +755,12 @@ int adjoint_core(stencil_plan_s* p, const double* d_u0, const double* d_kappa, d
   }
   CUDA_TRY(cudaMemsetAsync(gx, 0, 4 * bytes, s), "clearing the gradient accumulators");
   // reverse sweep, one segment [t0, t1) at a time
-  const int64_t nseg = (T + c - 1) / c;
   for (int64_t sg = nseg - 1; sg >= 0; --sg) {
     const int64_t t0 = sg * c, t1 = std::min(T, t0 + c);
     const double* base = ck + n * (size_t)sg;
-    // seg[k] = u^{t0+k} for k = 1 .. t1-t0-1 (k = 0 is the checkpoint itself)
-    for (int64_t t = t0 + 1; t < t1; ++t) {
+    // seg[k] = u^{t0+k} for k = 1 .. t1-t0-1 (k = 0 is the checkpoint itself);
+    // the forward sweep already left the last segment's states there
+    for (int64_t t = t0 + 1; t < t1 && sg < nseg - 1; ++t) {
       const double* from = (t == t0 + 1) ? base : seg + n * (size_t)(t - t0 - 1);
       e = launch_varcoef_step(p->ndim, p->boundary, p->g, cb, from, seg + n * (size_t)(t - t0), p->d_w, s);
       if (e != cudaSuccess) return cuda_fail(e, "launching the segment recompute");

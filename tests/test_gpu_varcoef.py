@@ -72,11 +72,14 @@ def test_checkpoint_interval_is_bitwise_neutral(st):
     shape = (20, 18, 22)
     u0, kappa, target, dt = inputs(shape, 31)
     p = st.Plan.varcoef(shape, PERIODIC)
-    ref = p.adjoint(cuda(u0), cuda(kappa), dt, cuda(target), 37, ckpt_every=1)
-    for c in (0, 5, 37, 50):
-        got = p.adjoint(cuda(u0), cuda(kappa), dt, cuda(target), 37, ckpt_every=c)
-        assert got[0] == ref[0]
-        assert bool((got[1] == ref[1]).all()) and bool((got[2] == ref[2]).all())
+    # T = 37 leaves a last segment of 1..c steps; T = 36 with c = 6 or 12 a full one
+    # (the forward sweep keeps the last segment's states, the others are recomputed)
+    for T, cs in ((37, (0, 2, 5, 36, 37, 50)), (36, (6, 12, 35))):
+        ref = p.adjoint(cuda(u0), cuda(kappa), dt, cuda(target), T, ckpt_every=1)
+        for c in cs:
+            got = p.adjoint(cuda(u0), cuda(kappa), dt, cuda(target), T, ckpt_every=c)
+            assert got[0] == ref[0]
+            assert bool((got[1] == ref[1]).all()) and bool((got[2] == ref[2]).all())
     p.close()
 
 
