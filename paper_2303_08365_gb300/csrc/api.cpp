@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -96,7 +97,8 @@ struct stencil_plan_s {
   double* d_adj = nullptr;     // adjoint scratch
   size_t adj_cells = 0;
   int* d_status = nullptr;     // device status word (bounded waits that gave up)
-  unsigned int* d_ctl = nullptr;  // barrier words of the persistent temporal kernel
+  unsigned int* d_flags = nullptr;  // per-tile flags of the persistent temporal kernel
+  int flags_cap = 0;
   double* d_w = nullptr;       // weights in tap order, then kZeroSlots zeros and kOneSlots ones
   stencil_batch_s* persist = nullptr;  // one-item batch for the persistent 2D path
   const double* persist_grid = nullptr;
@@ -178,13 +180,22 @@ int ensure(double** buf, size_t count, const char* what) {
   return STENCIL_OK;
 }
 
+constexpr int kMaxDevices = 64;
+
+int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+  return dev;
+}
+
+// SM count of the current device (cached per device).
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
+  static std::atomic<int> cache[kMaxDevices];
+  const int dev = current_device();
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev].store(n, std::memory_order_relaxed);
   }
   return n;
 }
@@ -199,15 +210,16 @@ std::mutex g_tune_mu;
 std::map<std::string, std::pair<int, int>> g_tune;
 bool g_tune_loaded = false;
 
+// Name of the current device with blanks replaced (cached per device).
 std::string device_name() {
-  static std::string name;
+  static std::mutex mu;
+  static std::string cache[kMaxDevices];
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(mu);
+  std::string& name = cache[dev];
   if (name.empty()) {
-    int dev = 0;
     cudaDeviceProp prop;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
-      name = prop.name;
-    else
-      name = "unknown";
+    name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? std::string(prop.name) : "unknown";
     for (char& c : name)
       if (c == ' ') c = '_';
   }
@@ -257,16 +269,22 @@ bool tune_lookup(const std::string& key, int& tb, int& v) {
 }
 
 // The kernel (and Tb) a constant-weight plan uses when nothing was tuned or
-// forced.  Small 2D grids are latency-bound: they run as one persistent
-// launch with Tb steps in shared memory between device-wide barriers.
+// forced.  Small 2D grids are latency-bound: they run as one persistent launch,
+// with Tb = 4 steps in shared memory per exchange up to 2^18 cells, and one
+// step per device-wide barrier (5-point star) up to 3 * 2^20 cells; larger
+// grids stream one launch per step (measured on GB300, 2D 5-point heat,
+// T = 100: 512^2 53.6 vs 43.3 GStencil/s, 1024^2 76.2 vs 54.3 and 68.1 for
+// streaming, 2048^2 streaming 102.3 vs 99.7).
 int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
   if (Tb) *Tb = 1;
   if (p->ndim == 3 && p->radius == 1) return kVariantStream;
   if (p->ndim == 2 && p->radius == 1) {
-    if (p->cells() <= ((int64_t)1 << 20)) {
-      if (Tb) *Tb = p->cells() <= ((int64_t)1 << 17) ? 8 : 4;
+    if (p->cells() <= ((int64_t)1 << 18)) {
+      if (Tb) *Tb = 4;
       return kVariantPersistent;
     }
+    if (p->cells() <= ((int64_t)3 << 20) && p->shape == Shape::kStar && p->taps.n == 5)
+      return kVariantPersistent;
     return kVariantStream;
   }
   if (p->ndim == 2 && p->radius == 2) return kVariantStream;
@@ -361,16 +379,24 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
       variant = kVariantDirect;
       Tb = 1;
     } else {
-      if (!p->d_ctl) CUDA_TRY(cudaMalloc(&p->d_ctl, 4 * sizeof(unsigned int)), "allocating barrier words");
-      CUDA_TRY(cudaMemsetAsync(p->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing barrier words");
       PersistTbLaunch L;
+      persist_tiling(p->g.ny, p->g.nx, Tb, sm_count(), &L.tiles_y, &L.tiles_x, &L.reach_y, &L.reach_x);
+      const int ntiles = L.tiles_y * L.tiles_x;
+      if (p->flags_cap < ntiles) {
+        cudaFree(p->d_flags);
+        p->d_flags = nullptr;
+        p->flags_cap = 0;
+        CUDA_TRY(cudaMalloc(&p->d_flags, ntiles * sizeof(unsigned int)), "allocating the tile flags");
+        p->flags_cap = ntiles;
+      }
+      CUDA_TRY(cudaMemsetAsync(p->d_flags, 0, ntiles * sizeof(unsigned int), s), "clearing the tile flags");
       L.a = d_grid;
       L.b = p->d_tmp;
       L.ny = p->g.ny;
       L.nx = p->g.nx;
       L.T = T;
       L.wdev = p->d_w;
-      L.barrier = p->d_ctl;
+      L.flags = p->d_flags;
       L.status = p->d_status;
       L.spin_limit = 2000000000LL;
       cudaError_t e = launch_persist_tb(p->shape, p->boundary, Tb, L, sm_count(), s);
@@ -634,7 +660,7 @@ void stencil_destroy(stencil_plan p) {
   cudaFree(p->d_coef);
   cudaFree(p->d_adj);
   cudaFree(p->d_status);
-  cudaFree(p->d_ctl);
+  cudaFree(p->d_flags);
   cudaFree(p->d_w);
   if (p->persist) {
     p->persist->d_partner = nullptr;  // the plan's own ping-pong buffer
@@ -869,7 +895,7 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   struct Cand { int Tb, variant; };
   std::vector<Cand> cands = {{1, kVariantDirect}, {1, kVariantStream}, {1, kVariantPersistent},
-                             {4, kVariantPersistent}, {8, kVariantPersistent},
+                             {2, kVariantPersistent}, {4, kVariantPersistent}, {8, kVariantPersistent},
                              {2, kVariantTemporal}, {4, kVariantTemporal}, {8, kVariantTemporal}};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0), "creating an event");

@@ -151,14 +151,19 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchLaunch L) {
 
 
 // ---------------------------------------------------------------------------
-// Persistent temporal blocking for one small 2D grid: every CTA owns tiles of
-// kPTH x kPTW cells, loads each with a halo of Tb cells, advances it Tb steps
-// in shared memory (the region shrinks by one cell per side per step: the
-// overlapped-tile recompute of the paper's temporal tiling, Sec. 4.1), writes
-// the tile back, and only then meets the other CTAs at the device-wide
-// barrier -- one barrier per Tb steps instead of one per step.  Every cell
-// applies the lexicographic tap chain of the single-step kernels (bitwise
-// equal results).  Loads after a barrier bypass L1 (other SMs wrote them).
+// Persistent temporal blocking for one small 2D grid.  The grid is cut into
+// tiles_y x tiles_x tiles of near-equal size (at most kPTH x kPTW; the host
+// picks the cut so that the tiles cover the SMs evenly).  Every CTA owns
+// tiles, loads each with a halo of Tb cells, advances it Tb steps in shared
+// memory (the region shrinks by one cell per side per step: the overlapped-
+// tile recompute of the paper's temporal tiling, Sec. 4.1) and writes the tile
+// back.  There is no device-wide barrier: each tile publishes the number of
+// blocks it has finished in its own flag, and a tile starts block k once every
+// tile its halo reaches has finished block k-1.  That also keeps a tile from
+// overwriting data a slower neighbour is still reading, since the neighbour's
+// reads of block k-1 come before its flag.  Every cell applies the
+// lexicographic tap chain of the single-step kernels (bitwise equal
+// results).  Loads of other tiles' data bypass L1 (other SMs wrote them).
 constexpr int kPTH = 16, kPTW = 32;
 constexpr int kPThreads = 512;  // one CTA per SM on small grids: 16 warps to hide FP64 latency
 
@@ -180,25 +185,77 @@ __device__ __forceinline__ double ptb_cell(const RegWeights<NT>& W, const double
   return acc;
 }
 
+// Waits until every tile within (reach_y, reach_x) tiles of (ty, tx) has
+// published at least `target` finished blocks.  The wait is bounded by wall
+// time and gives up at once when another CTA has reported an error; returns
+// false (for every thread of the CTA) when it gave up.
+template <bool PERIODIC>
+__device__ bool wait_reach(const PersistTbLaunch& L, int ty, int tx, unsigned int target) {
+  const int wy = 2 * L.reach_y + 1, wx = 2 * L.reach_x + 1;
+  int ok = 1;
+  for (int i = threadIdx.x; i < wy * wx; i += blockDim.x) {
+    int yy = ty + i / wx - L.reach_y, xx = tx + i % wx - L.reach_x;
+    if (PERIODIC) {
+      yy %= L.tiles_y;
+      yy += yy < 0 ? L.tiles_y : 0;
+      xx %= L.tiles_x;
+      xx += xx < 0 ? L.tiles_x : 0;
+    } else if ((unsigned)yy >= (unsigned)L.tiles_y || (unsigned)xx >= (unsigned)L.tiles_x) {
+      continue;
+    }
+    const unsigned int* f = L.flags + yy * L.tiles_x + xx;
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    if (v >= target) continue;
+    const unsigned long long t0 = global_ns();
+    for (unsigned int spin = 0;; ++spin) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+      if (v >= target) break;
+      if ((spin & 31) == 31) {
+        if (*(volatile int*)L.status != 0) {
+          ok = 0;
+          break;
+        }
+        if ((long long)(global_ns() - t0) > L.spin_limit) {
+          atomicCAS(L.status, 0, (int)-5 /* STENCIL_ERR_TIMEOUT */);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    if (!ok) break;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// Rows [y0, y1) of tile row ty when ny rows are cut into `tiles` near-equal parts.
+__device__ __forceinline__ int cut(int i, int n, int tiles) {
+  return (int)((long long)i * n / tiles);
+}
+
 template <int NT, bool BOX, bool PERIODIC, int TB>
-__global__ void __launch_bounds__(kPThreads) k_persist_tb(PersistTbLaunch L) {
-  constexpr int RH = kPTH + 2 * TB, RW = kPTW + 2 * TB;
+__global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) {
+  constexpr int RW = kPTW + 2 * TB;
+  constexpr int RH = kPTH + 2 * TB;
   __shared__ double buf[2][RH * RW];
   RegWeights<NT> W;
   W.load(L.wdev);
-  const unsigned int G = gridDim.x;
+  const int G = gridDim.x;
   const int ny = L.ny, nx = L.nx;
-  const int tiles_x = (nx + kPTW - 1) / kPTW, tiles_y = (ny + kPTH - 1) / kPTH;
-  const int ntiles = tiles_x * tiles_y;
-  double* src = L.a;
-  double* dst = L.b;
-  for (long long t0 = 0; t0 < L.T; t0 += TB) {
-    const int tb = (int)(L.T - t0 < TB ? L.T - t0 : TB);
+  const int ntiles = L.tiles_y * L.tiles_x;
+  const long long nblk = (L.T + TB - 1) / TB;
+  for (long long blk = 0; blk < nblk; ++blk) {
+    const int tb = (int)(L.T - blk * TB < TB ? L.T - blk * TB : TB);
+    const double* src = (blk & 1) ? L.b : L.a;
+    double* dst = (blk & 1) ? L.a : L.b;
     for (int j = blockIdx.x; j < ntiles; j += G) {
-      const int y0 = (j / tiles_x) * kPTH, x0 = (j % tiles_x) * kPTW;
+      const int ty = j / L.tiles_x, tx = j % L.tiles_x;
+      const int y0 = cut(ty, ny, L.tiles_y), x0 = cut(tx, nx, L.tiles_x);
+      const int th = cut(ty + 1, ny, L.tiles_y) - y0, tw = cut(tx + 1, nx, L.tiles_x) - x0;
+      if (blk > 0 && !wait_reach<PERIODIC>(L, ty, tx, (unsigned int)blk)) return;
       // load the tile with a halo of tb cells (region offset TB - tb inside the buffer)
       const int off = TB - tb;
-      const int lh = kPTH + 2 * tb, lw = kPTW + 2 * tb;
+      const int lh = th + 2 * tb, lw = tw + 2 * tb;
       for (int c = threadIdx.x; c < lh * lw; c += kPThreads) {
         const int ry = c / lw, rx = c % lw;
         int y = y0 - tb + ry, x = x0 - tb + rx;
@@ -216,7 +273,7 @@ __global__ void __launch_bounds__(kPThreads) k_persist_tb(PersistTbLaunch L) {
       int cur = 0;
       for (int s = 1; s <= tb; ++s) {
         const int m = tb - s;  // remaining halo after this step
-        const int h = kPTH + 2 * m, w = kPTW + 2 * m;
+        const int h = th + 2 * m, w = tw + 2 * m;
         const double* in = buf[cur];
         double* out = buf[cur ^ 1];
         // two cells per thread per pass: two independent FMA chains in flight
@@ -235,26 +292,31 @@ __global__ void __launch_bounds__(kPThreads) k_persist_tb(PersistTbLaunch L) {
         __syncthreads();
         cur ^= 1;
       }
-      // the tile itself back to global memory
-      for (int c = threadIdx.x; c < kPTH * kPTW; c += kPThreads) {
-        const int ry = c / kPTW, rx = c % kPTW;
-        const int y = y0 + ry, x = x0 + rx;
-        if (y < ny && x < nx) dst[(int64_t)y * nx + x] = buf[cur][(TB + ry) * RW + TB + rx];
+      // the tile itself back to global memory, then its flag (release: the
+      // CTA barrier orders every thread's stores before thread 0's release)
+      for (int c = threadIdx.x; c < th * tw; c += kPThreads) {
+        const int ry = c / tw, rx = c % tw;
+        dst[(int64_t)(y0 + ry) * nx + x0 + rx] = buf[cur][(TB + ry) * RW + TB + rx];
       }
       __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(L.flags + j), "r"((unsigned int)(blk + 1))
+                     : "memory");
+      }
     }
-    if (!grid_barrier(L.barrier, G, L.spin_limit, L.status)) return;
-    double* tmp = src;
-    src = dst;
-    dst = tmp;
   }
-  // the result is in `src`; if that is the partner buffer, copy it back
-  if (src != L.a) {
+  // an odd number of blocks leaves the result in the partner buffer: copy each
+  // tile back once every tile that reads it in the last block is done
+  if (nblk & 1) {
     for (int j = blockIdx.x; j < ntiles; j += G) {
-      const int y0 = (j / tiles_x) * kPTH, x0 = (j % tiles_x) * kPTW;
-      for (int c = threadIdx.x; c < kPTH * kPTW; c += kPThreads) {
-        const int y = y0 + c / kPTW, x = x0 + c % kPTW;
-        if (y < ny && x < nx) L.a[(int64_t)y * nx + x] = __ldcg(src + (int64_t)y * nx + x);
+      const int ty = j / L.tiles_x, tx = j % L.tiles_x;
+      const int y0 = cut(ty, ny, L.tiles_y), x0 = cut(tx, nx, L.tiles_x);
+      const int th = cut(ty + 1, ny, L.tiles_y) - y0, tw = cut(tx + 1, nx, L.tiles_x) - x0;
+      if (!wait_reach<PERIODIC>(L, ty, tx, (unsigned int)nblk)) return;
+      for (int c = threadIdx.x; c < th * tw; c += kPThreads) {
+        const int64_t k = (int64_t)(y0 + c / tw) * nx + x0 + c % tw;
+        L.a[k] = __ldcg(L.b + k);
       }
     }
   }
@@ -267,7 +329,10 @@ cudaError_t launch_ptb(const PersistTbLaunch& L, int sms, cudaStream_t stream) {
   if (occ < 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPThreads, 0) != cudaSuccess)
     occ = 0;
   if (occ < 1) return cudaErrorInvalidConfiguration;
-  const int tiles = ((L.nx + kPTW - 1) / kPTW) * ((L.ny + kPTH - 1) / kPTH);
+  const int tiles = L.tiles_y * L.tiles_x;
+  if (L.tiles_y < 1 || L.tiles_x < 1 || (L.ny + L.tiles_y - 1) / L.tiles_y > kPTH ||
+      (L.nx + L.tiles_x - 1) / L.tiles_x > kPTW)
+    return cudaErrorInvalidValue;
   int grid = sms * (occ < 2 ? occ : 2);
   if (tiles < grid) grid = tiles;
   cudaLaunchConfig_t cfg = {};
@@ -295,6 +360,31 @@ cudaError_t ptb_by_tb(int Tb, const PersistTbLaunch& L, int sms, cudaStream_t st
 }
 
 }  // namespace
+
+void persist_tiling(int ny, int nx, int Tb, int sms, int* tiles_y, int* tiles_x, int* reach_y,
+                    int* reach_x) {
+  const int ty0 = (ny + kPTH - 1) / kPTH, tx0 = (nx + kPTW - 1) / kPTW;
+  long long best = -1;
+  int bty = ty0, btx = tx0;
+  for (int ty = ty0; ty <= ny && ty <= 3 * ty0 + 8; ++ty)
+    for (int tx = tx0; tx <= nx && tx <= 3 * tx0 + 8; ++tx) {
+      const long long h = (ny + ty - 1) / ty, w = (nx + tx - 1) / tx;
+      long long work = 0;  // cell updates of the largest tile over one block
+      for (int m = 0; m < Tb; ++m) work += (h + 2 * m) * (w + 2 * m);
+      const long long per_sm = ((long long)ty * tx + sms - 1) / sms;
+      const long long cost = per_sm * work;
+      if (best < 0 || cost < best || (cost == best && (long long)ty * tx < (long long)bty * btx)) {
+        best = cost;
+        bty = ty;
+        btx = tx;
+      }
+    }
+  *tiles_y = bty;
+  *tiles_x = btx;
+  const int hmin = ny / bty, wmin = nx / btx;
+  *reach_y = (Tb + hmin - 1) / hmin;
+  *reach_x = (Tb + wmin - 1) / wmin;
+}
 
 cudaError_t launch_persist_tb(Shape shape, int boundary, int Tb, const PersistTbLaunch& L, int sms,
                               cudaStream_t stream) {

@@ -159,17 +159,23 @@ int batched_tile_h();
 int batched_tile_w();
 
 // Persistent temporal blocking for one small 2D grid (radius 1, star or box):
-// Tb in {2, 4, 8} steps per device-wide barrier.
+// Tb in {2, 4, 8} steps per exchange, tiles synchronised by per-tile flags.
 struct PersistTbLaunch {
   double* a;             // the caller's grid
   double* b;             // partner buffer
   int ny, nx;
   long long T;
   const double* wdev;    // weights, then the zero and one slots
-  unsigned int* barrier; // two words, zero before the launch
+  int tiles_y, tiles_x;  // near-equal cut of the grid (from persist_tiling)
+  int reach_y, reach_x;  // tiles a Tb-cell halo can reach on each side
+  unsigned int* flags;   // tiles_y * tiles_x words, zero before the launch
   int* status;
   long long spin_limit;  // ns
 };
+// Picks the cut of an ny x nx grid into tiles of at most 16 x 32 cells that
+// minimises the FP64 work of the busiest SM for Tb steps per block, and the
+// reach of a Tb-cell halo in tiles.
+void persist_tiling(int ny, int nx, int Tb, int sms, int* tiles_y, int* tiles_x, int* reach_y, int* reach_x);
 cudaError_t launch_persist_tb(Shape shape, int boundary, int Tb, const PersistTbLaunch& L, int sms,
                               cudaStream_t stream);
 

@@ -60,7 +60,7 @@ def test_create_rejects_bad_arguments_on_host(stencil):
 
 def test_plan_lifecycle_and_tuning_checks_on_host(stencil):
     h = stencil.stencil_create((8, 9), 1, np.ones(9) / 9, stencil.PERIODIC)
-    assert stencil.stencil_get_tuning(h) == (8, stencil.VARIANT_PERSISTENT)  # small 2D grid
+    assert stencil.stencil_get_tuning(h) == (4, stencil.VARIANT_PERSISTENT)  # small 2D grid
     with pytest.raises(stencil.StencilError):
         stencil.stencil_set_tuning(h, 3, 0)
     with pytest.raises(stencil.StencilError):
@@ -68,13 +68,20 @@ def test_plan_lifecycle_and_tuning_checks_on_host(stencil):
     stencil.stencil_set_tuning(h, 2, stencil.VARIANT_TEMPORAL)
     assert stencil.stencil_get_tuning(h) == (2, stencil.VARIANT_TEMPORAL)
     stencil.stencil_set_tuning(h, 0, 0)
-    assert stencil.stencil_get_tuning(h) == (8, stencil.VARIANT_PERSISTENT)
+    assert stencil.stencil_get_tuning(h) == (4, stencil.VARIANT_PERSISTENT)
     mid = stencil.stencil_create((1024, 1024), 1, np.array([0, .1, 0, .1, .6, .1, 0, .1, 0]),
                                  stencil.DIRICHLET_ZERO)
-    assert stencil.stencil_get_tuning(mid) == (4, stencil.VARIANT_PERSISTENT)
+    assert stencil.stencil_get_tuning(mid) == (1, stencil.VARIANT_PERSISTENT)
     stencil.stencil_destroy(mid)
+    heat = np.array([0, .1, 0, .1, .6, .1, 0, .1, 0])
+    for dims, want in [((512, 512), (4, stencil.VARIANT_PERSISTENT)),
+                       ((2048, 1536), (1, stencil.VARIANT_PERSISTENT)),
+                       ((2048, 2048), (1, stencil.VARIANT_STREAM))]:
+        q = stencil.stencil_create(dims, 1, heat, stencil.DIRICHLET_ZERO)
+        assert stencil.stencil_get_tuning(q) == want, dims
+        stencil.stencil_destroy(q)
     big = stencil.stencil_create((2048, 1024), 1, np.ones(9) / 9, stencil.PERIODIC)
-    assert stencil.stencil_get_tuning(big) == (1, stencil.VARIANT_STREAM)
+    assert stencil.stencil_get_tuning(big) == (1, stencil.VARIANT_STREAM)  # box: no one-step persistent form
     stencil.stencil_destroy(big)
     r2 = stencil.stencil_create((9, 10, 11), 2, np.ones(125) / 125, stencil.PERIODIC)
     assert stencil.stencil_get_tuning(r2) == (1, stencil.VARIANT_DIRECT)

@@ -363,13 +363,21 @@ def test_autotune_picks_a_candidate_and_keeps_results(st):
 
 
 @pytest.mark.parametrize("shape,boundary,kind,Tb,T", [((256, 256), DIRICHLET, "heat", 8, 100),
+                                                      ((256, 256), PERIODIC, "heat", 4, 37),
                                                       ((37, 53), DIRICHLET, "star_rand", 4, 17),
                                                       ((48, 64), PERIODIC, "box_rand", 8, 21),
                                                       ((5, 3), PERIODIC, "heat", 8, 9),
-                                                      ((300, 257), DIRICHLET, "box_eq", 2, 7)])
+                                                      ((300, 257), DIRICHLET, "box_eq", 2, 7),
+                                                      ((1024, 1024), DIRICHLET, "star_rand", 4, 13),
+                                                      ((1030, 998), PERIODIC, "box_rand", 2, 9),
+                                                      ((1, 700), PERIODIC, "star_rand", 8, 24),
+                                                      ((700, 2), DIRICHLET, "box_rand", 4, 11),
+                                                      ((2, 2), DIRICHLET, "heat", 2, 5)])
 def test_persistent_temporal_matches_single_steps_bitwise(st, shape, boundary, kind, Tb, T):
-    """Tb steps in shared memory between device-wide barriers: bitwise equal to
-    single steps (same per-cell chain), remainder blocks included."""
+    """Tb steps in shared memory per exchange, tiles synchronised by per-tile
+    flags: bitwise equal to single steps (same per-cell chain), remainder
+    blocks, odd block counts (result copied back), several tiles per CTA and
+    halos that reach past the nearest tile included."""
     w = weights_for(kind, 2, 1, 700 + Tb) if kind != "box_eq" else synth.box_weights(2, 1.0 / 9.0)
     u0 = synth.uniform(13, shape)
     a = gpu_run(st, u0, w, 1, boundary, T, Tb=Tb, variant=st.VARIANT_PERSISTENT)
