@@ -250,13 +250,19 @@ def headline(st, steps, warmup, world, stream):
     launches = st.stencil_launch_count() - l0
     clocks = sampler.stop()
     ms = barrier_max(world, ms)
-    # end to end through the host-buffer entry point (pinned memory), 1 step
+    # end to end through the host-buffer entry point (pinned memory): one
+    # untimed call (the plan's staging buffer is allocated there), then
+    # `steps` timed calls, each copying the grid in, sweeping T steps and
+    # copying the result out
     host = torch.from_numpy(u0).pin_memory()
     h2d = host.numel() * 8
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
     plan.run_host(host, T, stream=stream)
-    e2e_ms = (time.perf_counter() - t0) * 1e3
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.run_host(host, T, stream=stream)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
     e2e_ms = barrier_max(world, e2e_ms)
     plan.close()
     del grid
@@ -273,22 +279,36 @@ def time_plan(st, plan, grid, T, reps, stream, warm=1):
     return ms / reps, (st.stencil_launch_count() - l0) // reps
 
 
-def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, reps=2):
+def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, reps=2,
+               tb_sweep=None):
+    """One constant-weight workload with the plan's own choice of kernel and Tb;
+    `tb_sweep` ([(Tb, variant), ...]) also times each listed Tb (GStencil/s)."""
     import torch
     grid = torch.from_numpy(u0).cuda()
     plan = st.Plan(shape, radius, weights, boundary)
     ms, launches = time_plan(st, plan, grid, T, reps, stream)
     cells = int(np.prod(shape))
     tb, v = plan.get_tuning()
+    sweep = None
+    if tb_sweep:
+        sweep = {}
+        for tbs, vs in tb_sweep:
+            plan.set_tuning(tbs, vs)
+            ms_s, _ = time_plan(st, plan, grid, T, 1, stream)
+            sweep[f"Tb={tbs} {st.stencil_variant_name(vs)}"] = round(cells * T / (ms_s * 1e-3) / 1e9, 3)
+        plan.set_tuning(0, 0)
     plan.close()
     del grid
     torch.cuda.empty_cache()
-    return {"workload": f"{name} {'x'.join(map(str, shape))} T={T} "
-                        f"{'periodic' if boundary else 'dirichlet0'}",
-            "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
-            "Tb": tb, "variant": st.stencil_variant_name(v), "launches": launches,
-            "roofline": roofline(name, cells, T, ms, launches, peak,
-                                 variant_kernel(st.stencil_variant_name(v), len(shape)), Tb=tb)}
+    out = {"workload": f"{name} {'x'.join(map(str, shape))} T={T} "
+                       f"{'periodic' if boundary else 'dirichlet0'}",
+           "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
+           "Tb": tb, "variant": st.stencil_variant_name(v), "launches": launches,
+           "roofline": roofline(name, cells, T, ms, launches, peak,
+                                variant_kernel(st.stencil_variant_name(v), len(shape)), Tb=tb)}
+    if sweep is not None:
+        out["tb_sweep_gstencil_per_s"] = sweep
+    return out
 
 
 def form_batched(st, stream, peak, rank=0, world=1):
@@ -655,7 +675,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h["u0"])
     forms = {}
-    want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2", "onedim", "thermal"]) \
+    want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2", "onedim", "thermal",
+                "heat3d_tb"]) \
         if args.forms == "all" else \
         set() if args.forms == "none" else set(args.forms.split(","))
     if "batched" in want:
@@ -666,10 +687,22 @@ def main():
             forms["heat2d"] = form_const(st, "heat2d-5pt", shp, 1, synth.heat_weights(2, 0.1), 0, 100,
                                          synth.uniform(synth.SEED_HEAT2D, shp), stream, peak_tflops,
                                          reps=20)
+        if "heat3d_tb" in want:
+            # the headline grid at every Tb the 3D kernels offer, 100 of its 1000 steps each
+            shp = HEADLINE["shape"]
+            u0 = h["u0"]
+            r = form_const(st, "heat3d-7pt", shp, 1, synth.heat_weights(3, HEADLINE["alpha"]), 1, 100, u0,
+                           stream, peak_tflops, reps=1,
+                           tb_sweep=[(1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
+                                     (4, st.VARIANT_TEMPORAL)])
+            forms["heat3d_tb_sweep"] = {"workload": r["workload"],
+                                        "tb_sweep_gstencil_per_s": r["tb_sweep_gstencil_per_s"]}
         if "box2d" in want:
             shp = (16384, 16384)
             forms["box2d"] = form_const(st, "box2d-9pt", shp, 1, synth.box_weights(2, 1.0 / 9.0), 1, 1000,
-                                        synth.uniform(synth.SEED_BOX2D, shp), stream, peak_tflops)
+                                        synth.uniform(synth.SEED_BOX2D, shp), stream, peak_tflops,
+                                        tb_sweep=[(1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
+                                                  (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL)])
         if "radius2" in want:
             # Table 1's radius-2 shapes (Star-2D9P, Box-2D25P), seeded random weights summing to 1
             shp = (8192, 8192)
@@ -695,8 +728,11 @@ def main():
                                            peak_tflops)
         if "box3d" in want:
             shp = (384, 384, 384)
+            # every Tb the 3D kernels offer (the temporal kernel covers Tb 2 and 4 in 3D)
             forms["box3d"] = form_const(st, "box3d-27pt", shp, 1, synth.box_weights(3, seed=synth.SEED_BOX3D),
-                                        0, 500, synth.normal(synth.SEED_BOX3D, shp), stream, peak_tflops)
+                                        0, 500, synth.normal(synth.SEED_BOX3D, shp), stream, peak_tflops,
+                                        tb_sweep=[(1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
+                                                  (4, st.VARIANT_TEMPORAL)])
         if "adjoint" in want:
             forms["adjoint"] = form_adjoint(st, stream, peak_tflops)
         line["forms"] = forms

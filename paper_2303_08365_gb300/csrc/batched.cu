@@ -233,6 +233,28 @@ __device__ __forceinline__ int cut(int i, int n, int tiles) {
   return (int)((long long)i * n / tiles);
 }
 
+// Row and column of a flat index k = r * w + c that advances by a fixed
+// stride: one division when the walk starts, none per step.
+struct FlatWalk {
+  int r, c, dr, dc, w;
+  __device__ __forceinline__ FlatWalk(int start, int stride, int width)
+      : r(start / width), c(start % width), dr(stride / width), dc(stride % width), w(width) {}
+  __device__ __forceinline__ void next() {
+    r += dr;
+    c += dc;
+    if (c >= w) {
+      c -= w;
+      ++r;
+    }
+  }
+};
+
+__device__ __forceinline__ int wrap_into(int v, int n) {
+  while (v < 0) v += n;
+  while (v >= n) v -= n;
+  return v;
+}
+
 template <int NT, bool BOX, bool PERIODIC, int TB>
 __global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) {
   constexpr int RW = kPTW + 2 * TB;
@@ -256,13 +278,14 @@ __global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) 
       // load the tile with a halo of tb cells (region offset TB - tb inside the buffer)
       const int off = TB - tb;
       const int lh = th + 2 * tb, lw = tw + 2 * tb;
-      for (int c = threadIdx.x; c < lh * lw; c += kPThreads) {
-        const int ry = c / lw, rx = c % lw;
+      FlatWalk lwk(threadIdx.x, kPThreads, lw);
+      for (int c = threadIdx.x; c < lh * lw; c += kPThreads, lwk.next()) {
+        const int ry = lwk.r, rx = lwk.c;
         int y = y0 - tb + ry, x = x0 - tb + rx;
         double v = 0.0;
         if (PERIODIC) {
-          y %= ny; y += y < 0 ? ny : 0;
-          x %= nx; x += x < 0 ? nx : 0;
+          y = wrap_into(y, ny);
+          x = wrap_into(x, nx);
           v = __ldcg(src + (int64_t)y * nx + x);
         } else if ((unsigned)y < (unsigned)ny && (unsigned)x < (unsigned)nx) {
           v = __ldcg(src + (int64_t)y * nx + x);
@@ -277,10 +300,11 @@ __global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) 
         const double* in = buf[cur];
         double* out = buf[cur ^ 1];
         // two cells per thread per pass: two independent FMA chains in flight
-        for (int c = threadIdx.x; c < h * w; c += 2 * kPThreads) {
+        FlatWalk wa(threadIdx.x, 2 * kPThreads, w), wb(threadIdx.x + kPThreads, 2 * kPThreads, w);
+        for (int c = threadIdx.x; c < h * w; c += 2 * kPThreads, wa.next(), wb.next()) {
           const int c2 = c + kPThreads;
-          const int ry = TB - m + c / w, rx = TB - m + c % w;  // buffer coordinates
-          const int ry2 = TB - m + c2 / w, rx2 = TB - m + c2 % w;
+          const int ry = TB - m + wa.r, rx = TB - m + wa.c;  // buffer coordinates
+          const int ry2 = TB - m + wb.r, rx2 = TB - m + wb.c;
           const double v1 = ptb_cell<NT, BOX, PERIODIC, TB>(W, in, ry, rx, y0 - TB + ry, x0 - TB + rx, ny,
                                                            nx, 0);
           double v2 = 0.0;
@@ -294,8 +318,9 @@ __global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) 
       }
       // the tile itself back to global memory, then its flag (release: the
       // CTA barrier orders every thread's stores before thread 0's release)
-      for (int c = threadIdx.x; c < th * tw; c += kPThreads) {
-        const int ry = c / tw, rx = c % tw;
+      FlatWalk swk(threadIdx.x, kPThreads, tw);
+      for (int c = threadIdx.x; c < th * tw; c += kPThreads, swk.next()) {
+        const int ry = swk.r, rx = swk.c;
         dst[(int64_t)(y0 + ry) * nx + x0 + rx] = buf[cur][(TB + ry) * RW + TB + rx];
       }
       __syncthreads();
