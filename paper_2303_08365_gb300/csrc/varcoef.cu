@@ -103,14 +103,78 @@ __device__ __forceinline__ double apply_a(const double* __restrict__ u, const do
   return acc;
 }
 
+// Two cells per thread, (x, y0) and (x, y0 + 1): the pair shares the two
+// centre values and the coefficient of the face between them, and a thread
+// carries two independent FMA chains.  Each cell's chain is the same as in
+// apply_a (centre, then -/+ x, -/+ y, -/+ z), so results are bitwise equal.
+#define PAIR_COORDS                                                     \
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;                  \
+  const int y = 2 * (blockIdx.y * blockDim.y + threadIdx.y);            \
+  const int z = blockIdx.z;                                             \
+  if (x >= nx || y >= ny) return;                                       \
+  const bool has1 = y + 1 < ny;                                         \
+  const int64_t sy = nx, sz = (int64_t)nx * ny;                         \
+  const int64_t i = (int64_t)z * sz + (int64_t)y * sy + x;              \
+  const int64_t i1 = i + sy;
+
+template <int NDIM>
+__device__ __forceinline__ void apply_a_pair(const double* __restrict__ u, const double* __restrict__ c0,
+                                             const double* __restrict__ cx, const double* __restrict__ cy,
+                                             const double* __restrict__ cz, bool periodic, int x, int y,
+                                             int z, int nx, int ny, int nz, int64_t i, int64_t i1,
+                                             int64_t sy, int64_t sz, bool has1, double zero, double u0,
+                                             double u1, double& a0, double& a1) {
+  a0 = fma(__ldg(c0 + i), u0, zero);
+  if (has1) a1 = fma(__ldg(c0 + i1), u1, zero);
+  {  // x
+    Nbr lo = nbr(x, nx, -1, periodic, i, 1);
+    Nbr hi = nbr(x, nx, +1, periodic, i, 1);
+    if (lo.in) a0 = fma(__ldg(cx + lo.idx), __ldg(u + lo.idx), a0);
+    if (hi.in) a0 = fma(__ldg(cx + i), __ldg(u + hi.idx), a0);
+    if (has1) {
+      if (lo.in) a1 = fma(__ldg(cx + lo.idx + sy), __ldg(u + lo.idx + sy), a1);
+      if (hi.in) a1 = fma(__ldg(cx + i1), __ldg(u + hi.idx + sy), a1);
+    }
+  }
+  if (NDIM >= 2) {  // y: the face between the two cells is cy[i]
+    Nbr lo = nbr(y, ny, -1, periodic, i, sy);
+    if (lo.in) a0 = fma(__ldg(cy + lo.idx), __ldg(u + lo.idx), a0);
+    const double cyi = __ldg(cy + i);
+    if (has1) {
+      a0 = fma(cyi, u1, a0);
+      a1 = fma(cyi, u0, a1);
+      Nbr hi1 = nbr(y + 1, ny, +1, periodic, i1, sy);
+      if (hi1.in) a1 = fma(__ldg(cy + i1), __ldg(u + hi1.idx), a1);
+    } else {
+      Nbr hi = nbr(y, ny, +1, periodic, i, sy);
+      if (hi.in) a0 = fma(cyi, __ldg(u + hi.idx), a0);
+    }
+  }
+  if (NDIM >= 3) {  // z
+    Nbr lo = nbr(z, nz, -1, periodic, i, sz);
+    Nbr hi = nbr(z, nz, +1, periodic, i, sz);
+    if (lo.in) a0 = fma(__ldg(cz + lo.idx), __ldg(u + lo.idx), a0);
+    if (hi.in) a0 = fma(__ldg(cz + i), __ldg(u + hi.idx), a0);
+    if (has1) {
+      if (lo.in) a1 = fma(__ldg(cz + lo.idx + sy), __ldg(u + lo.idx + sy), a1);
+      if (hi.in) a1 = fma(__ldg(cz + i1), __ldg(u + hi.idx + sy), a1);
+    }
+  }
+}
+
 template <int NDIM>
 __global__ void __launch_bounds__(256) k_step(const double* __restrict__ src, double* __restrict__ dst,
                                               const double* __restrict__ c0, const double* __restrict__ cx,
                                               const double* __restrict__ cy, const double* __restrict__ cz,
                                               bool periodic, int nz, int ny, int nx,
                                               const double* __restrict__ zp) {
-  CELL_COORDS
-  dst[i] = apply_a<NDIM>(src, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, sy, sz, __ldg(zp));
+  PAIR_COORDS
+  const double u0 = __ldg(src + i), u1 = has1 ? __ldg(src + i1) : 0.0;
+  double a0, a1 = 0.0;
+  apply_a_pair<NDIM>(src, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, i1, sy, sz, has1, __ldg(zp), u0,
+                     u1, a0, a1);
+  dst[i] = a0;
+  if (has1) dst[i1] = a1;
 }
 
 template <int NDIM>
@@ -124,29 +188,51 @@ __global__ void __launch_bounds__(256) k_adjoint(const double* __restrict__ lam,
                                                  double* __restrict__ gy, double* __restrict__ gz,
                                                  double* __restrict__ gg, bool periodic, int nz,
                                                  int ny, int nx, const double* __restrict__ zp) {
-  CELL_COORDS
-  lam_out[i] = apply_a<NDIM>(lam, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, sy, sz, __ldg(zp));
+  PAIR_COORDS
+  const double l0 = __ldg(lam + i), l1 = has1 ? __ldg(lam + i1) : 0.0;
+  double a0, a1 = 0.0;
+  apply_a_pair<NDIM>(lam, c0, cx, cy, cz, periodic, x, y, z, nx, ny, nz, i, i1, sy, sz, has1, __ldg(zp), l0,
+                     l1, a0, a1);
+  lam_out[i] = a0;
+  if (has1) lam_out[i1] = a1;
   // differences as fma(a, 1, -b): the rounding of a - b at the FMA's full rate
   const double one = __ldg(zp + kZeroSlots);
-  const double ui = __ldg(u + i), li = __ldg(lam + i);
-  const int cs[3] = {x, y, z};
+  const double u0 = __ldg(u + i), u1 = has1 ? __ldg(u + i1) : 0.0;
+  double* g[3] = {gx, gy, gz};
   const int ns[3] = {nx, ny, nz};
   const int64_t st[3] = {1, sy, sz};
-  double* g[3] = {gx, gy, gz};
-  int ghosts = 0;
 #pragma unroll
-  for (int d = 0; d < NDIM; ++d) {
-    Nbr hi = nbr(cs[d], ns[d], +1, periodic, i, st[d]);
-    if (hi.in) {
-      const double du = fma(__ldg(u + hi.idx), one, -ui);
-      const double dl = fma(li, one, -__ldg(lam + hi.idx));
-      g[d][i] = fma(du, dl, g[d][i]);
-    } else {
-      ++ghosts;
+  for (int c = 0; c < 2; ++c) {
+    if (c == 1 && !has1) break;
+    const int64_t ic = c ? i1 : i;
+    const double ui = c ? u1 : u0, li = c ? l1 : l0;
+    const int cs[3] = {x, y + c, z};
+    int ghosts = 0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      double un, ln;
+      bool in;
+      if (d == 1 && c == 0 && has1) {  // the face between the pair: both centres at hand
+        un = u1;
+        ln = l1;
+        in = true;
+      } else {
+        Nbr hi = nbr(cs[d], ns[d], +1, periodic, ic, st[d]);
+        in = hi.in;
+        un = in ? __ldg(u + hi.idx) : 0.0;
+        ln = in ? __ldg(lam + hi.idx) : 0.0;
+      }
+      if (in) {
+        const double du = fma(un, one, -ui);
+        const double dl = fma(li, one, -ln);
+        g[d][ic] = fma(du, dl, g[d][ic]);
+      } else {
+        ++ghosts;
+      }
+      if (!periodic && cs[d] == 0) ++ghosts;
     }
-    if (!periodic && cs[d] == 0) ++ghosts;
+    if (ghosts) gg[ic] = fma(-(double)ghosts * ui, li, gg[ic]);
   }
-  if (ghosts) gg[i] = fma(-(double)ghosts * ui, li, gg[i]);
 }
 
 template <int NDIM>
@@ -218,6 +304,12 @@ void cell_launch_shape(const Geom& g, dim3& grid, dim3& block) {
   grid = dim3((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
 }
 
+// Launch shape of the two-cells-per-thread kernels (k_step, k_adjoint).
+void pair_launch_shape(const Geom& g, dim3& grid, dim3& block) {
+  block = dim3(32, 8, 1);
+  grid = dim3((g.nx + 31) / 32, (g.ny + 15) / 16, g.nz);
+}
+
 }  // namespace
 
 cudaError_t launch_varcoef_prepare(int ndim, int boundary, const Geom& g, const double* kappa,
@@ -239,7 +331,7 @@ cudaError_t launch_varcoef_step(int ndim, int boundary, const Geom& g, VarcoefBu
                                 const double* src, double* dst, const double* zero,
                                 cudaStream_t stream) {
   dim3 grid, block;
-  cell_launch_shape(g, grid, block);
+  pair_launch_shape(g, grid, block);
   bool per = boundary == kPeriodic;
   if (ndim == 3)
     k_step<3><<<grid, block, 0, stream>>>(src, dst, b.c0, b.cx, b.cy, b.cz, per, g.nz, g.ny, g.nx, zero);
@@ -256,7 +348,7 @@ cudaError_t launch_adjoint_step(int ndim, int boundary, const Geom& g, VarcoefBu
                                 double* gx, double* gy, double* gz, double* gg, const double* zero,
                                 cudaStream_t stream) {
   dim3 grid, block;
-  cell_launch_shape(g, grid, block);
+  pair_launch_shape(g, grid, block);
   bool per = boundary == kPeriodic;
   if (ndim == 3)
     k_adjoint<3><<<grid, block, 0, stream>>>(lam_in, u, lam_out, b.c0, b.cx, b.cy, b.cz, gx, gy, gz,
