@@ -502,7 +502,7 @@ THERMAL = dict(mu=0.23, n=9600, T_full=3_800_000,
                        "hardware": "AMD EPYC 7V13 (24 cores) + NVIDIA A100-80GB, FP64"})
 
 
-def thermal_case(st, n, T, stream, fp32=True):
+def thermal_case(st, n, T, stream, fp32=True, peak=None):
     """The paper's copper-plate case study (Sec. 5.5) on an n x n grid: heat
     stencil with mu = 0.23 (Eq. 3 weights 0.08 / 0.23), Dirichlet 0 at the
     edges, Gaussian initial field peaked at 100 degrees.  FP64 production
@@ -522,6 +522,9 @@ def thermal_case(st, n, T, stream, fp32=True):
            "gstencil_per_s": round(n * n * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
            "centre_C": round(float(g[n // 2, n // 2]), 4)}
     rate = n * n * T / (ms * 1e-3)
+    if peak:
+        out["roofline"] = roofline("heat2d-5pt", n * n, T, ms, T, peak,
+                                   variant_kernel(st.stencil_variant_name(v), 2), Tb=tb)
     if n == THERMAL["n"]:
         full = THERMAL["n"] ** 2 * THERMAL["T_full"] / rate
         out["extrapolated_full_run_s"] = round(full, 1)
@@ -716,7 +719,7 @@ def main():
             forms["star2d9p"] = form_const(st, "star2d-9pt", shp, 2, star9, 1, 100, u0, stream, peak_tflops)
             forms["box2d25p"] = form_const(st, "box2d-25pt", shp, 2, box25, 1, 100, u0, stream, peak_tflops)
         if "thermal" in want:
-            forms["thermal"] = thermal_case(st, THERMAL["n"], 1000, stream, fp32=False)
+            forms["thermal"] = thermal_case(st, THERMAL["n"], 1000, stream, fp32=False, peak=peak_tflops)
         if "onedim" in want:
             # Table 1's 1D shapes: Heat-1D (alpha = 0.25) and Star-1D5P, 10^7 cells
             n1 = 10_000_000
