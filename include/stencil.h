@@ -206,7 +206,7 @@ const char* stencil_variant_name(int variant);
  * the 2D 5-point star stencil given by the dense 3x3 weights (host; the four
  * corner weights must be 0), with the given boundary rule, in one launch of
  * the persistent kernel.  It allocates nothing: the partner grid, tile list
- * and barrier words live in one array of about 10 MB (9.5 MiB) that every GPU loading
+ * and barrier words live in one array of about 8.4 MB (8.0 MiB) that every GPU loading
  * the library reserves until the process exits.
  *   - ny * nx must not exceed STENCIL_STATIC_MAX_CELLS (STENCIL_ERR_UNSUPPORTED
  *     otherwise, with a message naming the limit).

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -531,11 +532,12 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return hi[a].T > hi[c].T; });
   std::vector<BatchTile> tiles;
-  const int th = batched_tile_h(), tw = batched_tile_w();
+  const int tc = batched_tile_cells();
   for (int i : order) {
     if (hi[i].T == 0) continue;
-    for (int y0 = 0; y0 < hi[i].ny; y0 += th)
-      for (int x0 = 0; x0 < hi[i].nx; x0 += tw) tiles.push_back(BatchTile{i, y0, x0});
+    const int64_t cells = (int64_t)hi[i].ny * hi[i].nx;
+    for (int64_t k0 = 0; k0 < cells; k0 += tc)
+      tiles.push_back(BatchTile{i, (int)k0, (int)std::min<int64_t>(tc, cells - k0)});
   }
   b->ntiles = (int)tiles.size();
   CUDA_TRY(cudaMalloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n), "allocating the item table");
@@ -948,6 +950,8 @@ int stencil_batch_create(const stencil_batch_item* items, int n, int boundary, s
     const stencil_batch_item& it = items[i];
     if (it.ny < 1 || it.nx < 1 || it.ny > (1 << 30) || it.nx > (1 << 30))
       return fail(STENCIL_ERR_ARG, "item %d: bad shape %lld x %lld", i, (long long)it.ny, (long long)it.nx);
+    if (it.ny * it.nx > INT32_MAX)
+      return fail(STENCIL_ERR_UNSUPPORTED, "item %d: a batched grid holds at most 2^31 - 1 cells", i);
     if (it.T < 0 || it.T > (1 << 30)) return fail(STENCIL_ERR_ARG, "item %d: bad T", i);
     if (!is_finite(it.alpha)) return fail(STENCIL_ERR_ARG, "item %d: alpha not finite", i);
     if (!it.d_grid || ((uintptr_t)it.d_grid & 7)) return fail(STENCIL_ERR_ARG, "item %d: bad d_grid", i);
@@ -1087,7 +1091,7 @@ int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream) {
   it.nx = 64;
   it.T = 2;
   it.w[2] = 1.0;
-  BatchTile tl{0, 0, 0};
+  BatchTile tl{0, 0, 64};
   cudaMemsetAsync(grid, 0, 2 * 64 * sizeof(double), s);
   cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned int), s);
   cudaMemcpyAsync(d_item, &it, sizeof(it), cudaMemcpyHostToDevice, s);

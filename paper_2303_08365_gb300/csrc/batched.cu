@@ -22,8 +22,11 @@ namespace gbst {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTileH = 8;
-constexpr int kTileW = 64;  // kThreads = kTileW * 4 rows; each thread does 2 rows
+// A tile is a run of kTileCells consecutive cells of one grid in row-major
+// order (two per thread, kThreads apart), so every warp is full except at a
+// grid's last tile: the FP64 unit charges a warp instruction the same time
+// whatever the number of active lanes.
+constexpr int kTileCells = 2 * kThreads;
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -72,33 +75,27 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, long long 
   return ok != 0;
 }
 
-// One step of one tile: rows y0 .. y0+kTileH-1, columns x0 .. x0+kTileW-1.
+// One step of one tile: cells k0 .. k0+n-1 of the item (row-major), two per
+// thread.  The per-cell chain is the generic sweep's tap order.
 __device__ __forceinline__ void tile_step(const BatchItemDev& it, const double* __restrict__ src,
-                                          double* __restrict__ dst, int y0, int x0, bool periodic) {
-  const int tx = threadIdx.x % kTileW;
-  const int ty = threadIdx.x / kTileW;  // 0..3
-  const int x = x0 + tx;
-  if (x >= it.nx) return;
+                                          double* __restrict__ dst, int k0, int n, bool periodic) {
   const int ny = it.ny, nx = it.nx;
-  int xw = x - 1, xe = x + 1;
-  bool inw = true, ine = true;
-  if (periodic) {
-    xw = xw < 0 ? xw + nx : xw;
-    xe = xe >= nx ? xe - nx : xe;
-  } else {
-    inw = xw >= 0;
-    ine = xe < nx;
-  }
 #pragma unroll
-  for (int r = 0; r < kTileH / 4; ++r) {
-    const int y = y0 + ty + 4 * r;
-    if (y >= ny) break;
-    int yn = y - 1, ys = y + 1;
-    bool inn = true, ins = true;
+  for (int r = 0; r < 2; ++r) {
+    const int c = threadIdx.x + r * kThreads;
+    if (c >= n) break;
+    const int k = k0 + c;
+    const int y = k / nx, x = k - y * nx;
+    int xw = x - 1, xe = x + 1, yn = y - 1, ys = y + 1;
+    bool inw = true, ine = true, inn = true, ins = true;
     if (periodic) {
+      xw = xw < 0 ? xw + nx : xw;
+      xe = xe >= nx ? xe - nx : xe;
       yn = yn < 0 ? yn + ny : yn;
       ys = ys >= ny ? ys - ny : ys;
     } else {
+      inw = xw >= 0;
+      ine = xe < nx;
       inn = yn >= 0;
       ins = ys < ny;
     }
@@ -113,7 +110,7 @@ __device__ __forceinline__ void tile_step(const BatchItemDev& it, const double* 
     acc = fma(it.w[2], vc, acc);
     acc = fma(it.w[3], ve, acc);
     acc = fma(it.w[4], vs, acc);
-    dst[(int64_t)y * nx + x] = acc;
+    dst[k] = acc;
   }
 }
 
@@ -128,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchLaunch L) {
       if (it.T <= t) break;  // tiles are sorted by T, largest first
       const double* src = (t & 1) ? it.b : it.a;
       double* dst = (t & 1) ? it.a : it.b;
-      tile_step(it, src, dst, tl.y0, tl.x0, periodic);
+      tile_step(it, src, dst, tl.k0, tl.n, periodic);
     }
     if (!grid_barrier(L.barrier, arrivals, L.spin_limit, L.status)) return;
   }
@@ -137,13 +134,8 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchLaunch L) {
     const BatchTile tl = L.tiles[j];
     const BatchItemDev it = L.items[tl.item];
     if ((it.T & 1) == 0) continue;
-    const int tx = threadIdx.x % kTileW, ty = threadIdx.x / kTileW;
-    const int x = tl.x0 + tx;
-    if (x >= it.nx) continue;
-    for (int r = 0; r < kTileH / 4; ++r) {
-      const int y = tl.y0 + ty + 4 * r;
-      if (y >= it.ny) break;
-      const int64_t k = (int64_t)y * it.nx + x;
+    for (int c = threadIdx.x; c < tl.n; c += kThreads) {
+      const int k = tl.k0 + c;
       it.a[k] = __ldcg(it.b + k);
     }
   }
@@ -423,8 +415,7 @@ namespace {
 }  // namespace
 
 int batched_block_size() { return kThreads; }
-int batched_tile_h() { return kTileH; }
-int batched_tile_w() { return kTileW; }
+int batched_tile_cells() { return kTileCells; }
 
 cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};

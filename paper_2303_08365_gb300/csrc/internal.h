@@ -130,7 +130,8 @@ cudaError_t launch_loss_residual(int64_t n, const double* u, const double* targe
 // Batched persistent sweep over many 2D heat grids.
 struct BatchTile {
   int item;     // index into the item table
-  int y0, x0;   // tile origin
+  int k0;       // first cell of the tile (row-major index within the item)
+  int n;        // cells in the tile (batched_tile_cells(), fewer at an item's end)
 };
 struct BatchItemDev {
   double* a;     // the caller's grid (time level parity 0)
@@ -155,8 +156,7 @@ struct BatchLaunch {
 };
 cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, cudaStream_t stream);
 int batched_block_size();
-int batched_tile_h();
-int batched_tile_w();
+int batched_tile_cells();
 
 // Persistent temporal blocking for one small 2D grid (radius 1, star or box):
 // Tb in {2, 4, 8} steps per exchange, tiles synchronised by per-tile flags.

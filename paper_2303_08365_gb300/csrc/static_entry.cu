@@ -37,10 +37,9 @@ using namespace gbst;
 namespace {
 
 constexpr int64_t kMaxCells = STENCIL_STATIC_MAX_CELLS;
-// Tiles of the persistent kernel are 8 rows x 64 columns; a grid of at most
-// kMaxCells cells has at most kMaxCells / 8 + 64 of them (one row of cells
-// per tile row in the worst, one-column case).
-constexpr int64_t kMaxTiles = kMaxCells / 8 + 64;
+// Tiles of the persistent kernel are runs of 512 consecutive cells: a grid of
+// at most kMaxCells cells has at most kMaxCells / 512 + 1 of them.
+constexpr int64_t kMaxTiles = kMaxCells / 512 + 1;
 constexpr size_t kPartnerBytes = (size_t)kMaxCells * sizeof(double);
 constexpr size_t kItemOff = kPartnerBytes;
 constexpr size_t kTileOff = kItemOff + 256;
@@ -63,15 +62,14 @@ std::mutex g_setup_mu;
 
 int sfail(int code, const char* msg) { return set_error(code, msg); }
 
-// Writes the item descriptor and the tile list (rows of 8, columns of 64 --
-// the persistent kernel's tile shape) into the static scratch on the device.
+// Writes the item descriptor and the tile list (runs of `tc` consecutive
+// cells -- the persistent kernel's tile) into the static scratch on the device.
 __global__ void k_fill_static(BatchItemDev item, BatchItemDev* __restrict__ d_item,
-                              BatchTile* __restrict__ d_tiles, int tiles_y, int tiles_x, int th,
-                              int tw) {
-  const long long n = (long long)tiles_y * tiles_x;
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-       j += (long long)gridDim.x * blockDim.x)
-    d_tiles[j] = BatchTile{0, (int)(j / tiles_x) * th, (int)(j % tiles_x) * tw};
+                              BatchTile* __restrict__ d_tiles, int ntiles, int cells, int tc) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ntiles; j += gridDim.x * blockDim.x) {
+    const int k0 = j * tc;
+    d_tiles[j] = BatchTile{0, k0, cells - k0 < tc ? cells - k0 : tc};
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) *d_item = item;
 }
 
@@ -137,18 +135,16 @@ int stencil_run_2d_static(int64_t ny, int64_t nx, const double* weights, int bou
   item.w[2] = weights[4];  // centre
   item.w[3] = weights[5];  // east (x+1)
   item.w[4] = weights[7];  // south (y+1)
-  // the tile list is a pure function of the shape: rows of 8, columns of 64
-  const int th = batched_tile_h(), tw = batched_tile_w();
-  const int64_t tiles_y = (ny + th - 1) / th, tiles_x = (nx + tw - 1) / tw;
-  const int64_t ntiles = tiles_y * tiles_x;
+  // the tile list is a pure function of the shape: runs of tc consecutive cells
+  const int tc = batched_tile_cells();
+  const int64_t ntiles = (ny * nx + tc - 1) / tc;
   if (ntiles > kMaxTiles) return sfail(STENCIL_ERR_UNSUPPORTED, "tile list exceeds the static scratch");
   BatchTile* d_tiles = reinterpret_cast<BatchTile*>(s.base + kTileOff);
   BatchItemDev* d_item = reinterpret_cast<BatchItemDev*>(s.base + kItemOff);
   unsigned int* d_ctl = reinterpret_cast<unsigned int*>(s.base + kCtlOff);
   {
     const int fill_blocks = (int)((ntiles + 255) / 256 < 1024 ? (ntiles + 255) / 256 : 1024);
-    k_fill_static<<<fill_blocks, 256, 0, stream>>>(item, d_item, d_tiles, (int)tiles_y, (int)tiles_x, th,
-                                                   tw);
+    k_fill_static<<<fill_blocks, 256, 0, stream>>>(item, d_item, d_tiles, (int)ntiles, (int)(ny * nx), tc);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (cudaGetLastError() != cudaSuccess)
       return sfail(STENCIL_ERR_CUDA, "launching the static scratch fill failed");
