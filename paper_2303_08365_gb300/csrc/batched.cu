@@ -411,9 +411,6 @@ cudaError_t launch_persist_tb(Shape shape, int boundary, int Tb, const PersistTb
   return per ? ptb_by_tb<5, false, true>(Tb, L, sms, stream) : ptb_by_tb<5, false, false>(Tb, L, sms, stream);
 }
 
-namespace {
-}  // namespace
-
 int batched_block_size() { return kThreads; }
 int batched_tile_cells() { return kTileCells; }
 
