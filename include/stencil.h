@@ -238,6 +238,15 @@ int64_t stencil_launch_count(void);
  * bytes of device memory. */
 int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream);
 
+/* Host-side fault injection for tests: after `after` more device allocations
+ * by this library succeed, every later one fails as if the device were out
+ * of memory, without calling the driver, until the injection is turned off
+ * with a negative value (the default).  The call that needed the allocation
+ * returns STENCIL_ERR_OOM at that point and launches nothing after it; the
+ * plan or batch keeps what it had already allocated.  Process-wide; no GPU
+ * is faulted. */
+void stencil_debug_fail_allocations(int after);
+
 /* FP64 fused multiply-add throughput of the current device, measured with a
  * kernel of independent DFMA chains on every SM for about `millis` ms.
  * *dfma_per_s receives DFMA instructions per second (2 flops each). */

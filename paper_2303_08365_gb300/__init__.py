@@ -73,6 +73,7 @@ SIGNATURES = [
     ("stencil_launch_count", ctypes.c_int64, []),
     ("stencil_fp64_peak", ctypes.c_int, [ctypes.c_double, _DP, _VP]),
     ("stencil_selftest_barrier_timeout", ctypes.c_int, [ctypes.c_double, _VP]),
+    ("stencil_debug_fail_allocations", None, [ctypes.c_int]),
     ("stencil_run_2d_static", ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _DP, ctypes.c_int, _VP,
                                              ctypes.c_int64, _VP]),
 ]
@@ -288,6 +289,11 @@ def stencil_run_2d_static(grid, weights, boundary, T, stream=None):
         raise ValueError("weights must be a dense 3x3 array")
     _check(lib().stencil_run_2d_static(int(grid.shape[0]), int(grid.shape[1]), w.ctypes.data_as(_DP),
                                        int(boundary), _dev_ptr(grid, "grid"), int(T), _stream(stream)))
+
+
+def stencil_debug_fail_allocations(after):
+    """Test hook: the allocation after `after` more successful ones fails (< 0: off)."""
+    lib().stencil_debug_fail_allocations(int(after))
 
 
 def stencil_selftest_barrier_timeout(limit_ms=20.0, stream=None):

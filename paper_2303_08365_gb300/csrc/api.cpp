@@ -54,6 +54,27 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
+// Host-side fault injection for tests (stencil_debug_fail_allocations): when
+// g_fail_after >= 0, that many more device allocations succeed and the next
+// one reports cudaErrorMemoryAllocation without calling the driver.
+std::atomic<int> g_fail_after{-1};
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+  int left = g_fail_after.load();
+  while (left >= 0) {
+    if (left == 0) {
+      *ptr = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    if (g_fail_after.compare_exchange_weak(left, left - 1)) break;
+  }
+  return cudaMalloc(ptr, bytes);
+}
+template <typename T>
+cudaError_t dev_malloc(T** ptr, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(ptr), bytes);
+}
+
 bool is_finite(double v) { return std::isfinite(v); }
 
 // Pads a shape to three axes; rejects axes beyond the kernels' 32-bit indexing.
@@ -173,7 +194,7 @@ std::string plan_key(const stencil_plan_s* p) {
 
 int ensure(double** buf, size_t count, const char* what) {
   if (*buf) return STENCIL_OK;
-  cudaError_t e = cudaMalloc((void**)buf, count * sizeof(double));
+  cudaError_t e = dev_malloc(buf, count * sizeof(double));
   if (e != cudaSuccess) {
     *buf = nullptr;
     return cuda_fail(e, what);
@@ -322,7 +343,7 @@ int ensure_weights(stencil_plan_s* p) {
   std::vector<double> h(p->taps.n + kExtraSlots, 0.0);
   for (int k = 0; k < p->taps.n; ++k) h[k] = p->taps.w[k];
   for (int k = 0; k < kOneSlots; ++k) h[p->taps.n + kZeroSlots + k] = 1.0;
-  CUDA_TRY(cudaMalloc(&p->d_w, h.size() * sizeof(double)), "allocating the weight array");
+  CUDA_TRY(dev_malloc(&p->d_w, h.size() * sizeof(double)), "allocating the weight array");
   CUDA_TRY(cudaMemcpy(p->d_w, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice),
            "copying the weights");
   return STENCIL_OK;
@@ -330,7 +351,7 @@ int ensure_weights(stencil_plan_s* p) {
 
 int ensure_status(stencil_plan_s* p) {
   if (p->d_status) return STENCIL_OK;
-  CUDA_TRY(cudaMalloc(&p->d_status, sizeof(int)), "allocating the status word");
+  CUDA_TRY(dev_malloc(&p->d_status, sizeof(int)), "allocating the status word");
   CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "clearing the status word");
   return STENCIL_OK;
 }
@@ -342,7 +363,7 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
     if (!tune_lookup(plan_key(p), tb0, v0)) {
       // tune on a scratch copy of the grid (the candidates' runs destroy it)
       double* scratch = nullptr;
-      if (cudaMalloc(&scratch, (size_t)p->cells() * sizeof(double)) == cudaSuccess) {
+      if (dev_malloc(&scratch, (size_t)p->cells() * sizeof(double)) == cudaSuccess) {
         cudaMemcpyAsync(scratch, d_grid, (size_t)p->cells() * sizeof(double), cudaMemcpyDeviceToDevice, s);
         stencil_autotune(p, scratch, 4, s, nullptr);
         cudaStreamSynchronize(s);
@@ -387,7 +408,7 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
         cudaFree(p->d_flags);
         p->d_flags = nullptr;
         p->flags_cap = 0;
-        CUDA_TRY(cudaMalloc(&p->d_flags, ntiles * sizeof(unsigned int)), "allocating the tile flags");
+        CUDA_TRY(dev_malloc(&p->d_flags, ntiles * sizeof(unsigned int)), "allocating the tile flags");
         p->flags_cap = ntiles;
       }
       CUDA_TRY(cudaMemsetAsync(p->d_flags, 0, ntiles * sizeof(unsigned int), s), "clearing the tile flags");
@@ -540,15 +561,15 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
       tiles.push_back(BatchTile{i, (int)k0, (int)std::min<int64_t>(tc, cells - k0)});
   }
   b->ntiles = (int)tiles.size();
-  CUDA_TRY(cudaMalloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n), "allocating the item table");
+  CUDA_TRY(dev_malloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n), "allocating the item table");
   CUDA_TRY(cudaMemcpy(b->d_items, hi.data(), sizeof(BatchItemDev) * (size_t)n, cudaMemcpyHostToDevice),
            "copying the item table");
-  CUDA_TRY(cudaMalloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(1, tiles.size())),
+  CUDA_TRY(dev_malloc(&b->d_tiles, sizeof(BatchTile) * std::max<size_t>(1, tiles.size())),
            "allocating the tile list");
   if (!tiles.empty())
     CUDA_TRY(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice),
              "copying the tile list");
-  CUDA_TRY(cudaMalloc(&b->d_ctl, 4 * sizeof(unsigned int)), "allocating the barrier words");
+  CUDA_TRY(dev_malloc(&b->d_ctl, 4 * sizeof(unsigned int)), "allocating the barrier words");
   CUDA_TRY(cudaMemset(b->d_ctl, 0, 4 * sizeof(unsigned int)), "clearing the barrier words");
   const int per_sm = batched_blocks_per_sm();
   if (per_sm < 1) return fail(STENCIL_ERR_CUDA, "the batched kernel does not fit on an SM");
@@ -580,6 +601,8 @@ int batch_enqueue(stencil_batch_s* b, cudaStream_t s) {
 extern "C" {
 
 const char* stencil_last_error(void) { return g_err.c_str(); }
+
+void stencil_debug_fail_allocations(int after) { g_fail_after.store(after < 0 ? -1 : after); }
 
 int64_t stencil_launch_count(void) { return g_launches.load(); }
 
@@ -960,7 +983,7 @@ int stencil_batch_create(const stencil_batch_item* items, int n, int boundary, s
   auto* b = new (std::nothrow) stencil_batch_s();
   if (!b) return fail(STENCIL_ERR_OOM, "allocating the batch");
   b->items.assign(items, items + n);
-  cudaError_t e = cudaMalloc(&b->d_partner, (size_t)total_cells * sizeof(double));
+  cudaError_t e = dev_malloc(&b->d_partner, (size_t)total_cells * sizeof(double));
   if (e != cudaSuccess) {
     int rc = cuda_fail(e, "allocating the partner buffers");
     stencil_batch_destroy(b);
@@ -1077,10 +1100,10 @@ int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream) {
     cudaFree(d_item);
     cudaFree(d_tile);
   };
-  if (cudaMalloc(&grid, 2 * 64 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&ctl, 4 * sizeof(unsigned int)) != cudaSuccess ||
-      cudaMalloc(&d_item, sizeof(BatchItemDev)) != cudaSuccess ||
-      cudaMalloc(&d_tile, sizeof(BatchTile)) != cudaSuccess) {
+  if (dev_malloc(&grid, 2 * 64 * sizeof(double)) != cudaSuccess ||
+      dev_malloc(&ctl, 4 * sizeof(unsigned int)) != cudaSuccess ||
+      dev_malloc(&d_item, sizeof(BatchItemDev)) != cudaSuccess ||
+      dev_malloc(&d_tile, sizeof(BatchTile)) != cudaSuccess) {
     cleanup();
     return fail(STENCIL_ERR_OOM, "allocating the self-test buffers");
   }
@@ -1126,7 +1149,7 @@ int stencil_fp64_peak(double millis, double* dfma_per_s, void* cuda_stream) {
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int blocks = sm_count() * 8;
   double* out = nullptr;
-  CUDA_TRY(cudaMalloc(&out, sizeof(double) * blocks * 256), "allocating the output");
+  CUDA_TRY(dev_malloc(&out, sizeof(double) * blocks * 256), "allocating the output");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
