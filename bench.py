@@ -250,6 +250,13 @@ def headline(st, steps, warmup, world, stream):
     launches = st.stencil_launch_count() - l0
     clocks = sampler.stop()
     ms = barrier_max(world, ms)
+    # properties the result keeps at any size (periodic, weights >= 0 summing to 1):
+    # the mean is conserved and every value stays within the initial range
+    m0 = float(np.mean(u0))
+    checks = {"steps_applied": (warmup + steps) * T,
+              "mean_drift_rel": abs(float(grid.mean()) - m0) / abs(m0),
+              "within_initial_range": bool(float(grid.min()) >= float(u0.min()) and
+                                           float(grid.max()) <= float(u0.max()))}
     # end to end through the host-buffer entry point (pinned memory): one
     # untimed call (the plan's staging buffer is allocated there), then
     # `steps` timed calls, each copying the grid in, sweeping T steps and
@@ -268,7 +275,7 @@ def headline(st, steps, warmup, world, stream):
     del grid
     torch.cuda.empty_cache()
     return dict(ms=ms / steps, launches=launches, clocks=clocks, e2e_ms=e2e_ms, h2d=h2d, d2h=h2d,
-                Tb=tb, variant=st.stencil_variant_name(variant), u0=u0)
+                Tb=tb, variant=st.stencil_variant_name(variant), u0=u0, checks=checks)
 
 
 def time_plan(st, plan, grid, T, reps, stream, warm=1):
@@ -674,6 +681,7 @@ def main():
                 "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"]},
         "gpu_launches": int(h["launches"]),
         "clocks": h["clocks"],
+        "result_checks": h["checks"],
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(h["u0"])
