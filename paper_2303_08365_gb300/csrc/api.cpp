@@ -98,6 +98,12 @@ int make_geom(int ndim, const int64_t* dims, Geom& g) {
 
 }  // namespace
 
+int gbst::device_ordinal() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDeviceOrdinals) dev = 0;
+  return dev;
+}
+
 // Lets other translation units report through stencil_last_error.
 int gbst::set_error(int code, const char* msg) {
   g_err = msg ? msg : "";
@@ -202,13 +208,9 @@ int ensure(double** buf, size_t count, const char* what) {
   return STENCIL_OK;
 }
 
-constexpr int kMaxDevices = 64;
+constexpr int kMaxDevices = kMaxDeviceOrdinals;
 
-int current_device() {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
-  return dev;
-}
+int current_device() { return device_ordinal(); }
 
 // SM count of the current device (cached per device).
 int sm_count() {

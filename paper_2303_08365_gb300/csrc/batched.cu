@@ -342,9 +342,12 @@ __global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) 
 template <int NT, bool BOX, bool PERIODIC, int TB>
 cudaError_t launch_ptb(const PersistTbLaunch& L, int sms, cudaStream_t stream) {
   auto kern = k_persist_tb<NT, BOX, PERIODIC, TB>;
-  static int occ = -1;
-  if (occ < 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPThreads, 0) != cudaSuccess)
-    occ = 0;
+  static std::atomic<int> cache[kMaxDeviceOrdinals];
+  const int occ = cached_per_device(cache, [kern] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kPThreads, 0) != cudaSuccess) n = 0;
+    return n;
+  });
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const int tiles = L.tiles_y * L.tiles_x;
   if (L.tiles_y < 1 || L.tiles_x < 1 || (L.ny + L.tiles_y - 1) / L.tiles_y > kPTH ||

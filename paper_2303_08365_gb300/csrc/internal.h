@@ -186,4 +186,23 @@ cudaError_t launch_fp64_peak(int blocks, int iters, double* out, cudaStream_t st
 // Launch accounting (every kernel launch of the library adds one).
 extern std::atomic<int64_t> g_launches;
 
+// Ordinal of the current device, clamped to [0, kMaxDeviceOrdinals).
+constexpr int kMaxDeviceOrdinals = 64;
+int device_ordinal();
+
+// Per-device cache of a kernel's launch property (occupancy after its
+// attributes are set): `compute` runs on the first call for each device and
+// must be idempotent (concurrent first calls may both run it).  `cache` is a
+// zero-initialised static array owned by the call site.
+template <typename F>
+int cached_per_device(std::atomic<int> (&cache)[kMaxDeviceOrdinals], F&& compute) {
+  const int dev = device_ordinal();
+  int v = cache[dev].load(std::memory_order_acquire);
+  if (v == 0) {
+    v = compute() + 1;
+    cache[dev].store(v, std::memory_order_release);
+  }
+  return v - 1;
+}
+
 }  // namespace gbst

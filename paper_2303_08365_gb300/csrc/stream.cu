@@ -36,17 +36,16 @@ namespace gbst {
 // cuTensorMapEncodeTiled from the driver, fetched once through the runtime's
 // entry-point query (no link-time dependency on libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // a function-local static: initialised once, thread-safe
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -299,16 +298,18 @@ constexpr size_t ws_smem_bytes() { return sizeof(WsSmem<BOX>); }
 
 template <int NT, bool BOX, bool PERIODIC>
 int ws_occupancy() {
-  static int n = -1;
-  if (n < 0) {
+  static std::atomic<int> cache[kMaxDeviceOrdinals];
+  const int n = cached_per_device(cache, [] {
+    int occ = 0;
     cudaFuncSetAttribute(k_stream3d_ws<NT, BOX, PERIODIC>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          cudaSharedmemCarveoutMaxShared);
     if (cudaFuncSetAttribute(k_stream3d_ws<NT, BOX, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ws_smem_bytes<BOX>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream3d_ws<NT, BOX, PERIODIC>, kThreads + 32,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream3d_ws<NT, BOX, PERIODIC>, kThreads + 32,
                                                       ws_smem_bytes<BOX>()) != cudaSuccess)
-      n = 0;
-  }
+      occ = 0;
+    return occ;
+  });
   return n;
 }
 

@@ -313,11 +313,14 @@ cudaError_t launch2(const Geom& g, const double* wdev, const double* src, double
   P.work = (long long)P.strips * P.blocks;
   P.status = status;
   P.wdev = wdev;
-  static int occ = -1;
-  if (occ < 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream2d<NT, BOX, R, PERIODIC, EQUAL>,
-                                                    kThreads + 32, 0) != cudaSuccess)
-    occ = 0;
+  static std::atomic<int> cache[kMaxDeviceOrdinals];
+  const int occ = cached_per_device(cache, [] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stream2d<NT, BOX, R, PERIODIC, EQUAL>,
+                                                      kThreads + 32, 0) != cudaSuccess)
+      n = 0;
+    return n;
+  });
   if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)sms * occ;
   if (grid > P.work) grid = P.work;

@@ -220,12 +220,14 @@ cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, doub
                       cudaStream_t stream) {
   using D = PlaneDims<NDIM, TB>;
   auto kern = k_temporal<NDIM, NT, BOX, PERIODIC, TB>;
-  static int occ = -1;
-  if (occ < 0) {
+  static std::atomic<int> cache[kMaxDeviceOrdinals];
+  const int occ = cached_per_device(cache, [kern] {
+    int n = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D::bytes) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, D::bytes) != cudaSuccess)
-      occ = 0;
-  }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, D::bytes) != cudaSuccess)
+      n = 0;
+    return n;
+  });
   if (occ < 1) return cudaErrorInvalidConfiguration;
   TParams P;
   P.src = src;
