@@ -299,10 +299,14 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
     sweep = None
     if tb_sweep:
         sweep = {}
+        fp64_ceiling = peak * 1e12 / FLOPS[name] / 1e9
         for tbs, vs in tb_sweep:
             plan.set_tuning(tbs, vs)
             ms_s, _ = time_plan(st, plan, grid, T, 1, stream)
-            sweep[f"Tb={tbs} {st.stencil_variant_name(vs)}"] = round(cells * T / (ms_s * 1e-3) / 1e9, 3)
+            rate = cells * T / (ms_s * 1e-3) / 1e9
+            ceiling = min(fp64_ceiling, HBM_GBS * tbs / 16)
+            sweep[f"Tb={tbs} {st.stencil_variant_name(vs)}"] = {
+                "gstencil_per_s": round(rate, 3), "frac_of_stated_roofline": round(rate / ceiling, 4)}
         plan.set_tuning(0, 0)
     plan.close()
     del grid
