@@ -194,7 +194,18 @@ def variant_kernel(variant, ndim):
     return variant
 
 
-HBM_GBS = 6681.8  # MEASURED_PEAKS.json hbm_gbs (copy bandwidth on the GB300s)
+def _measured_hbm_gbs(default=6681.8):
+    """HBM copy bandwidth (GB/s) from MEASURED_PEAKS.json beside this script
+    when present (a STREAM-style copy measured on GB300), else `default`,
+    the value that file held when this script was written."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return default
+
+
+HBM_GBS = _measured_hbm_gbs()
 
 
 def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_cell=16,
