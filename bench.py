@@ -440,9 +440,11 @@ def form_adjoint(st, stream, peak):
 
 # ------------------------------------------------------------ CPU baseline
 
-def cpu_baseline(u0, budget_s=12.0):
+def cpu_baseline(u0, budget_s=12.0, gpu_run=None):
     """The oracle as it stands, on all host cores, on a bounded number of
-    steps of the headline grid; GStencil/s."""
+    steps of the headline grid; GStencil/s.  With `gpu_run(u0, steps)` (the
+    library's sweep of the same grid) the oracle's sample is also compared
+    with the GPU result, element by element over the whole 512^3 grid."""
     import oracle
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     w = synth.heat_weights(3, HEADLINE["alpha"])
@@ -451,9 +453,16 @@ def cpu_baseline(u0, budget_s=12.0):
     one = time.perf_counter() - t0
     steps = max(1, min(200, int(budget_s / max(one, 1e-3))))
     t0 = time.perf_counter()
-    oracle.run(u0, w, 1, 1, steps, nthreads=cores)
+    ref = oracle.run(u0, w, 1, 1, steps, nthreads=cores)
     el = time.perf_counter() - t0
     cells = u0.size
+    parity = None
+    if gpu_run is not None:
+        got = gpu_run(u0, steps)
+        parity = {"steps": steps, "cells": int(cells),
+                  "normwise_rel_err": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+                  "bar": 1e-12}
+    del ref
     # one core: the 2D 5-point 256^2 case in full, and the 27-point box with the 384^3
     # case's weights and boundary on a 128^3 grid for 2 steps (a bounded sample)
     single = []
@@ -472,7 +481,7 @@ def cpu_baseline(u0, budget_s=12.0):
             "kind": "oracle",
             "sample": f"{HEADLINE['name']} 512^3 periodic, {steps} of the 1000 steps "
                       f"({el:.1f} s), plain C loop nest, OpenMP over rows",
-            "single_core": single}
+            "single_core": single, "parity_vs_gpu": parity}
 
 
 # ------------------------------------------------------------------ main
@@ -688,6 +697,9 @@ def main():
                    "shape": list(HEADLINE["shape"]), "T": T, "grids": world,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "Tb": h["Tb"], "variant": h["variant"],
+                   "tile": {"stream": "64 x 32 cells of (x, y), streamed along z, 4-plane TMA ring",
+                            "temporal": "64 x 16 cells of (x, y) plus a Tb halo, streamed along z",
+                            "direct": "one cell per thread, 32 x 8 threads"}.get(h["variant"], h["variant"]),
                    "l2_flush": "none needed: each launch streams 2 GiB > 129 MB L2"},
         "roofline": roofline("heat3d-7pt", cells, T, h["ms"], h["launches"] // args.steps,
                              peak_tflops, variant_kernel(h["variant"], 3), Tb=h["Tb"]),
@@ -699,7 +711,14 @@ def main():
         "result_checks": h["checks"],
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(h["u0"])
+        def gpu_run(u, steps):
+            g = torch.from_numpy(u).cuda()
+            p = st.Plan(u.shape, 1, synth.heat_weights(3, HEADLINE["alpha"]), st.PERIODIC)
+            p.run(g, steps, stream=stream)
+            out = g.cpu().numpy()
+            p.close()
+            return out
+        line["cpu_baseline"] = cpu_baseline(h["u0"], gpu_run=gpu_run)
     forms = {}
     want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2", "onedim", "thermal",
                 "heat3d_tb"]) \
