@@ -333,6 +333,66 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
     return out
 
 
+# The paper's eight benchmark stencils at its own problem sizes (Table 1),
+# each for a bounded number of steps (the rate per step does not depend on T).
+# Weights: Eq. 3 heat weights for the Heat shapes, seeded random weights
+# summing to 1 for the others; Dirichlet zero (Table 1 states no boundary).
+TABLE1 = [
+    ("Heat-1D", "heat1d-3pt", (10_000_000,), 1, "heat", 1000),
+    ("Star-1D5P", "star1d-5pt", (10_000_000,), 2, "star", 1000),
+    ("Heat-2D", "heat2d-5pt", (10_000, 10_000), 1, "heat", 100),
+    ("Star-2D9P", "star2d-9pt", (10_000, 10_000), 2, "star", 50),
+    ("Box-2D9P", "box2d-9pt", (10_000, 10_000), 1, "box", 50),
+    ("Box-2D25P", "box2d-25pt", (10_000, 10_000), 2, "box", 20),
+    ("Heat-3D", "heat3d-7pt", (1024, 1024, 1024), 1, "heat", 10),
+    ("Box-3D27P", "box3d-27pt", (1024, 1024, 1024), 1, "box", 3),
+]
+
+
+def table1_weights(ndim, radius, kind, seed):
+    if kind == "heat":
+        return synth.heat_weights(ndim, 0.1 if ndim > 1 else 0.25)
+    side = 2 * radius + 1
+    v = synth.uniform(seed, (side,) * ndim)
+    if kind == "star":
+        c = (radius,) * ndim
+        mask = np.zeros_like(v, dtype=bool)
+        for d in range(ndim):
+            idx = list(c)
+            for o in range(side):
+                idx[d] = o
+                mask[tuple(idx)] = True
+        v = np.where(mask, v, 0.0)
+    return v / v.sum()
+
+
+def form_table1(st, stream, peak):
+    """GStencil/s of each Table 1 stencil at Table 1's grid size.  The input
+    is drawn on the device from a seeded generator (a 1024^3 grid is 8 GiB)."""
+    import torch
+    out = {}
+    gen = torch.Generator(device="cuda")
+    for i, (label, name, shape, radius, kind, T) in enumerate(TABLE1):
+        gen.manual_seed(synth.SEED_HEAT3D + 100 + i)
+        grid = torch.rand(shape, dtype=torch.float64, device="cuda", generator=gen)
+        w = table1_weights(len(shape), radius, kind, synth.SEED_HEAT3D + 200 + i)
+        plan = st.Plan(shape, radius, w, st.DIRICHLET_ZERO)
+        ms, launches = time_plan(st, plan, grid, T, 1, stream)
+        tb, v = plan.get_tuning()
+        cells = int(np.prod(shape))
+        # the shared-partial-sum count of INSTR holds only for equal box weights
+        instr = 9 if name == "box2d-9pt" and not np.all(w == w.flat[0]) else None
+        r = roofline(name, cells, T, ms, max(launches, 1), peak,
+                     variant_kernel(st.stencil_variant_name(v), len(shape)), Tb=tb, instr=instr)
+        out[label] = {"shape": list(shape), "T": T, "variant": st.stencil_variant_name(v), "Tb": tb,
+                      "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3),
+                      "frac": r["frac"], "fp64_pipe_frac": r["fp64_pipe_frac"]}
+        plan.close()
+        del grid
+        torch.cuda.empty_cache()
+    return out
+
+
 def form_batched(st, stream, peak, rank=0, world=1):
     """The 96-grid batch; with N ranks each advances its own shard (greedy
     packing on cells x T) and the rate is all updates / the slowest rank."""
@@ -722,7 +782,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline(h["u0"], gpu_run=gpu_run)
     forms = {}
     want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2", "onedim", "thermal",
-                "heat3d_tb"]) \
+                "heat3d_tb", "table1"]) \
         if args.forms == "all" else \
         set() if args.forms == "none" else set(args.forms.split(","))
     if "batched" in want:
@@ -763,6 +823,8 @@ def main():
             forms["box2d25p"] = form_const(st, "box2d-25pt", shp, 2, box25, 1, 100, u0, stream, peak_tflops)
         if "thermal" in want:
             forms["thermal"] = thermal_case(st, THERMAL["n"], 1000, stream, fp32=False, peak=peak_tflops)
+        if "table1" in want:
+            forms["table1"] = form_table1(st, stream, peak_tflops)
         if "onedim" in want:
             # Table 1's 1D shapes: Heat-1D (alpha = 0.25) and Star-1D5P, 10^7 cells
             n1 = 10_000_000
