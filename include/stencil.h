@@ -61,8 +61,11 @@ typedef enum {
  * ndim in {1,2,3}; dims[ndim] >= 1; radius in {1, 2}; weights as above
  * (copied, host memory); boundary a stencil_boundary.  *out receives the
  * plan.  Errors: STENCIL_ERR_ARG for a bad shape, radius, boundary or a
- * non-finite weight; STENCIL_ERR_UNSUPPORTED if the grid needs more than
- * 2^31 cells along one axis.  No device memory is allocated here. */
+ * non-finite weight; STENCIL_ERR_UNSUPPORTED for an axis longer than 2^30
+ * cells, or a grid whose slowest of three axes exceeds 65535 cells or whose
+ * middle axis exceeds 524280 (limits of the kernels' launch grids).  The
+ * total cell count may exceed 2^31 (64-bit offsets).  No device memory is
+ * allocated here. */
 int stencil_create(int ndim, const int64_t* dims, int radius, const double* weights,
                    int boundary, stencil_plan* out);
 
@@ -133,8 +136,9 @@ int stencil_adjoint_vjp(stencil_plan p, const double* d_u0, const double* d_kapp
 /* ----------------------------------------------------------- batched form */
 
 /* One independent 2D heat grid of a batch: ny x nx cells (row-major, device,
- * in place), Eq. 3 weights (1-4*alpha at the centre, alpha at the four
- * neighbours), T >= 0 steps. */
+ * in place; at most 2^31 - 1 cells, STENCIL_ERR_UNSUPPORTED otherwise), Eq. 3
+ * weights (1-4*alpha at the centre, alpha at the four neighbours), T >= 0
+ * steps. */
 typedef struct {
   int64_t ny, nx;
   double alpha;
@@ -142,11 +146,12 @@ typedef struct {
   double* d_grid;
 } stencil_batch_item;
 
-/* Builds a batch plan: packs the items' tiles into one persistent kernel's
- * device work list, allocates the per-item ping-pong buffers and per-tile
- * step counters, and captures the whole advance (every item by its own T)
- * as one CUDA graph on first run.  items is copied.  All items share the
- * boundary rule. */
+/* Builds a batch plan: cuts every item into tiles of 512 consecutive cells,
+ * lists them by the item's T (largest first) as one persistent kernel's
+ * device work list, allocates one partner buffer for all items, the item
+ * table and the barrier words, and captures the whole advance (every item
+ * by its own T, a bounded device-wide barrier between steps) as one CUDA
+ * graph on first run.  items is copied.  All items share the boundary rule. */
 int stencil_batch_create(const stencil_batch_item* items, int n, int boundary,
                          stencil_batch* out);
 
@@ -172,8 +177,28 @@ int stencil_plan_status(stencil_plan p, void* cuda_stream);
 
 /* ------------------------------------------------------------- tuning */
 
-/* Fixes the fused step count Tb (1, 2, 4 or 8) and kernel variant (0 = let
- * the library choose; see stencil_variant_name) for later runs of p.
+/* Kernel variants (ids are stable).  Defaults when nothing is forced or
+ * tuned: 3D radius 1 -> STREAM; 2D radius 1 -> PERSISTENT with Tb = 4 up to
+ * 2^18 cells, PERSISTENT with Tb = 1 (5-point star) up to 3 * 2^20 cells,
+ * else STREAM; 2D radius 2 -> STREAM; 1D -> TEMPORAL with Tb = 8; anything
+ * else -> DIRECT.  A variant a plan cannot use falls back to DIRECT unless
+ * it was forced, in which case stencil_run returns STENCIL_ERR_UNSUPPORTED. */
+typedef enum {
+  STENCIL_VARIANT_AUTO = 0,
+  STENCIL_VARIANT_DIRECT = 1,     /* one launch per step, any shape */
+  STENCIL_VARIANT_STREAM = 2,     /* one launch per step, TMA-fed tiles streamed
+                                     along the slowest axis (2D/3D, radius 1;
+                                     2D radius 2) */
+  STENCIL_VARIANT_TEMPORAL = 3,   /* Tb fused steps per launch (overlapped
+                                     tiles): Tb 2, 4 (3D), 2, 4, 8 (1D, 2D) */
+  STENCIL_VARIANT_PERSISTENT = 4  /* one launch for all T steps (2D radius 1):
+                                     Tb = 1 with a device-wide barrier per step
+                                     (5-point star), Tb > 1 with Tb steps in
+                                     shared memory per exchange */
+} stencil_variant;
+
+/* Fixes the fused step count Tb (1, 2, 4 or 8) and kernel variant (a
+ * stencil_variant; 0 = let the library choose) for later runs of p.
  * Tb = 0 returns the plan to the tuned / default choice. */
 int stencil_set_tuning(stencil_plan p, int Tb, int variant);
 

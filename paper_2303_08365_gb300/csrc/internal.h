@@ -31,7 +31,7 @@ enum Variant : int {
   kVariantDirect = 1,     // one cell per thread per plane, taps from L1
   kVariantStream = 2,     // slowest-axis streaming through a TMA-fed SMEM ring
   kVariantTemporal = 3,   // Tb fused steps per HBM round trip (overlapped tiles)
-  kVariantPersistent = 4, // one persistent launch with a device-wide barrier per step
+  kVariantPersistent = 4, // one launch for all steps: barrier per step (Tb 1) or tile flags (Tb > 1)
   kVariantCount = 5
 };
 
