@@ -141,6 +141,12 @@ FULL = [
     ((512, 512, 512), 1, PERIODIC, "heat", 3, synth.SEED_HEAT3D),
     ((16384, 16384), 1, PERIODIC, "box_eq", 3, synth.SEED_BOX2D),
     ((384, 384, 384), 1, DIRICHLET, "box_rand", 3, synth.SEED_BOX3D),
+    # the widened workloads, in the launch configuration the benchmark times
+    ((8192, 8192), 2, PERIODIC, "star_rand", 3, synth.SEED_BOX2D + 11),
+    ((8192, 8192), 2, PERIODIC, "box_rand", 3, synth.SEED_BOX2D + 11),
+    ((9600, 9600), 1, DIRICHLET, "heat", 4, synth.SEED_HEAT2D + 30),
+    ((10_000_000,), 1, DIRICHLET, "heat", 16, synth.SEED_HEAT2D + 20),
+    ((10_000_000,), 2, PERIODIC, "star_rand", 17, synth.SEED_HEAT2D + 21),
 ]
 
 
