@@ -87,7 +87,14 @@ void stencil_destroy(stencil_plan p);
  * need d_kappa (device, same shape) and dt > 0.  The library alternates
  * between d_grid and a plan-owned buffer and leaves the result in d_grid.
  * The fused step count Tb and kernel variant come from stencil_set_tuning,
- * the autotuner record, or a default (see stencil_autotune). */
+ * the autotuner record, or a default (see stencil_variant).
+ * CUDA graphs: the first run of a plan allocates its scratch; later runs only
+ * enqueue stream-ordered work (kernels, memsets, device-to-device copies) on
+ * cuda_stream, so they can be captured in a CUDA graph and replayed.  The
+ * graph uses the plan's buffers: it stays valid until the plan is destroyed
+ * or re-tuned.  (The one-step persistent variant keeps a work list for each
+ * of the last 8 (grid, T) pairs it ran; a graph captured around a run whose
+ * pair has since been evicted by 8 newer pairs is no longer valid.) */
 int stencil_run(stencil_plan p, double* d_grid, int64_t T, const double* d_kappa, double dt,
                 void* cuda_stream);
 

@@ -110,6 +110,8 @@ int gbst::set_error(int code, const char* msg) {
   return code;
 }
 
+constexpr int kPersistCache = 8;
+
 struct stencil_plan_s {
   int ndim = 0;
   Geom g{1, 1, 1};
@@ -128,9 +130,17 @@ struct stencil_plan_s {
   unsigned int* d_flags = nullptr;  // per-tile flags of the persistent temporal kernel
   int flags_cap = 0;
   double* d_w = nullptr;       // weights in tap order, then kZeroSlots zeros and kOneSlots ones
-  stencil_batch_s* persist = nullptr;  // one-item batch for the persistent 2D path
-  const double* persist_grid = nullptr;
-  int64_t persist_T = -1;
+  // one-item batches of the one-step persistent path, one per (grid, T) the
+  // plan has run recently (least recently used evicted beyond kPersistCache):
+  // a CUDA graph captured around a run keeps using its entry's buffers
+  struct PersistEntry {
+    const double* grid;
+    int64_t T;
+    stencil_batch_s* batch;
+    uint64_t last_use;
+  };
+  std::vector<PersistEntry> persist;
+  uint64_t persist_clock = 0;
   // tuning
   int user_Tb = 0, user_variant = 0;
   int tuned_Tb = 0, tuned_variant = 0;
@@ -434,11 +444,19 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
         return fail(STENCIL_ERR_UNSUPPORTED, "the persistent kernel covers 2D 5-point star plans");
       variant = kVariantDirect;
     } else {
-      if (!p->persist || p->persist_grid != d_grid || p->persist_T != T) {
-        if (p->persist) {
-          p->persist->d_partner = nullptr;
-          stencil_batch_destroy(p->persist);
-          p->persist = nullptr;
+      stencil_batch_s* hit = nullptr;
+      for (auto& e : p->persist)
+        if (e.grid == d_grid && e.T == T) {
+          e.last_use = ++p->persist_clock;
+          hit = e.batch;
+        }
+      if (!hit) {
+        if ((int)p->persist.size() >= kPersistCache) {
+          auto lru = std::min_element(p->persist.begin(), p->persist.end(),
+                                      [](const auto& x, const auto& y) { return x.last_use < y.last_use; });
+          lru->batch->d_partner = nullptr;  // the plan's own ping-pong buffer
+          stencil_batch_destroy(lru->batch);
+          p->persist.erase(lru);
         }
         auto* b = new (std::nothrow) stencil_batch_s();
         if (!b) return fail(STENCIL_ERR_OOM, "allocating the persistent plan");
@@ -455,11 +473,10 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
           stencil_batch_destroy(b);
           return rc;
         }
-        p->persist = b;
-        p->persist_grid = d_grid;
-        p->persist_T = T;
+        p->persist.push_back({d_grid, T, b, ++p->persist_clock});
+        hit = b;
       }
-      return batch_enqueue(p->persist, s);
+      return batch_enqueue(hit, s);
     }
   }
   if (variant == kVariantTemporal && !temporal_supported(p->ndim, p->radius, Tb)) {
@@ -689,9 +706,9 @@ void stencil_destroy(stencil_plan p) {
   cudaFree(p->d_status);
   cudaFree(p->d_flags);
   cudaFree(p->d_w);
-  if (p->persist) {
-    p->persist->d_partner = nullptr;  // the plan's own ping-pong buffer
-    stencil_batch_destroy(p->persist);
+  for (auto& e : p->persist) {
+    e.batch->d_partner = nullptr;  // the plan's own ping-pong buffer
+    stencil_batch_destroy(e.batch);
   }
   delete p;
 }
