@@ -116,3 +116,11 @@ def test_tuning_record_file_is_read(tmp_path):
     env["STENCIL_TUNE"] = "off"
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
     assert out.stdout.split() == ["1", "2"]
+
+
+def test_plan_is_a_context_manager(stencil):
+    with stencil.Plan((6, 7), 1, np.ones(9) / 9, stencil.PERIODIC) as p:
+        assert p.handle
+        assert p.get_tuning() == (4, stencil.VARIANT_PERSISTENT)
+    assert p.handle is None
+    p.close()  # closing twice is harmless
