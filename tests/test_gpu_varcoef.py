@@ -56,7 +56,10 @@ def test_forward_parity(st, shape, boundary, T):
 
 
 @pytest.mark.parametrize("shape,boundary,T,ck", [((16, 16, 16), PERIODIC, 20, 0), ((12, 14, 10), DIRICHLET, 21, 4),
-                                                 ((32, 32, 32), PERIODIC, 64, 8), ((20, 24), DIRICHLET, 30, 0)])
+                                                 ((32, 32, 32), PERIODIC, 64, 8), ((20, 24), DIRICHLET, 30, 0),
+                                                 # odd rows: the kernels pair cells along y
+                                                 ((9, 13, 11), PERIODIC, 17, 5), ((15, 21), DIRICHLET, 19, 3),
+                                                 ((7, 1, 9), DIRICHLET, 6, 2)])
 def test_adjoint_parity(st, shape, boundary, T, ck):
     u0, kappa, target, dt = inputs(shape, 21)
     rl, rgu, rgk = oracle.varcoef_adjoint(u0, kappa, dt, target, boundary, T, ckpt_every=ck, nthreads=0)
