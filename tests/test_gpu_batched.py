@@ -99,3 +99,23 @@ def test_bounded_wait_reports_timeout_and_context_survives(st):
     ref = oracle.run(g0, synth.heat_weights(2, 0.1), 1, DIRICHLET, 5)
     assert normwise_rel(d.cpu().numpy(), ref) <= TOL
     b.close()
+
+
+def test_one_call_entry_matches_batch_object(st):
+    """stencil_run_batched (create, run once, wait, destroy) gives the same
+    bits as a Batch object, periodic boundary included."""
+    import torch
+    items = [(45, 64, 0.2, 11), (17, 29, 0.07, 3), (64, 33, 0.24, 8)]
+    grids = [synth.uniform(70 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
+    for boundary in (DIRICHLET, PERIODIC):
+        a = [torch.from_numpy(g.copy()).cuda() for g in grids]
+        b = [torch.from_numpy(g.copy()).cuda() for g in grids]
+        st.stencil_run_batched(a, [x[2] for x in items], [x[3] for x in items], boundary)
+        batch = st.Batch(b, [x[2] for x in items], [x[3] for x in items], boundary)
+        batch.run()
+        assert batch.status() == 0
+        batch.close()
+        for x, y, g0, (_, _, al, T) in zip(a, b, grids, items):
+            assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
+            ref = oracle.run(g0, synth.heat_weights(2, al), 1, boundary, T)
+            assert normwise_rel(x.cpu().numpy(), ref) <= TOL
