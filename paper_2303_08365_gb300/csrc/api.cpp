@@ -311,7 +311,11 @@ bool tune_lookup(const std::string& key, int& tb, int& v) {
 // streaming, 2048^2 streaming 102.3 vs 99.7).
 int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
   if (Tb) *Tb = 1;
-  if (p->ndim == 3 && p->radius == 1) return kVariantStream;
+  // shapes the streaming kernels cannot take (odd nx; periodic sizes off their tile) go direct
+  if (p->ndim == 3 && p->radius == 1)
+    return stream3d_shape_ok(p->ndim, p->radius, p->shape, p->boundary, p->g) ? kVariantStream
+                                                                               : kVariantDirect;
+  const bool stream2d = stream2d_shape_ok(p->ndim, p->radius, p->boundary, p->g);
   if (p->ndim == 2 && p->radius == 1) {
     if (p->cells() <= ((int64_t)1 << 18)) {
       if (Tb) *Tb = 4;
@@ -319,9 +323,9 @@ int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
     }
     if (p->cells() <= ((int64_t)3 << 20) && p->shape == Shape::kStar && p->taps.n == 5)
       return kVariantPersistent;
-    return kVariantStream;
+    return stream2d ? kVariantStream : kVariantDirect;
   }
-  if (p->ndim == 2 && p->radius == 2) return kVariantStream;
+  if (p->ndim == 2 && p->radius == 2) return stream2d ? kVariantStream : kVariantDirect;
   if (p->ndim == 1) {
     if (Tb) *Tb = 8;  // 8 steps per launch in shared memory, 0.4-0.8% halo recompute
     return kVariantTemporal;

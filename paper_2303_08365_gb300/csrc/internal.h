@@ -73,6 +73,8 @@ cudaError_t launch_direct_f32(int ndim, int radius, int boundary, const Geom& g,
 // nx % 64 == 0 and ny a multiple of the tile height (32 star, 16 box).
 bool stream3d_eligible(int ndim, int radius, Shape shape, int boundary, const Geom& g, const void* a,
                        const void* b);
+// The shape part of that rule (no buffers, no driver query).
+bool stream3d_shape_ok(int ndim, int radius, Shape shape, int boundary, const Geom& g);
 cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const HostTaps& taps,
                             const double* wdev, const double* src, double* dst, int* status,
                             int sms, cudaStream_t stream);
@@ -82,6 +84,7 @@ cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const Host
 // the shared-partial-sum form for a box whose weights are all equal.
 bool stream2d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
                        const void* b);
+bool stream2d_shape_ok(int ndim, int radius, int boundary, const Geom& g);
 bool taps_all_equal(const HostTaps& t);
 cudaError_t launch_stream2d(Shape shape, int radius, int boundary, bool equal, const Geom& g,
                             const HostTaps& taps, const double* wdev, const double* src, double* dst,

@@ -342,13 +342,17 @@ cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, doubl
 
 }  // namespace
 
+bool stream3d_shape_ok(int ndim, int radius, Shape shape, int boundary, const Geom& g) {
+  if (ndim != 3 || radius != 1) return false;
+  if (g.nx % 2 != 0) return false;  // TMA: row pitch multiple of 16 bytes
+  const int ty = shape == Shape::kBox ? Tile<true>::TY : Tile<false>::TY;
+  return !(boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % ty != 0));
+}
+
 bool stream3d_eligible(int ndim, int radius, Shape shape, int boundary, const Geom& g, const void* a,
                        const void* b) {
-  if (ndim != 3 || radius != 1) return false;
-  if (g.nx % 2 != 0) return false;                        // TMA: row pitch multiple of 16 bytes
+  if (!stream3d_shape_ok(ndim, radius, shape, boundary, g)) return false;
   if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return false;  // TMA base and 16-byte stores
-  const int ty = shape == Shape::kBox ? Tile<true>::TY : Tile<false>::TY;
-  if (boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % ty != 0)) return false;
   return tensor_map_encoder() != nullptr;
 }
 

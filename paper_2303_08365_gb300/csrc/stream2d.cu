@@ -331,12 +331,16 @@ cudaError_t launch2(const Geom& g, const double* wdev, const double* src, double
 
 }  // namespace
 
-bool stream2d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
-                       const void* b) {
+bool stream2d_shape_ok(int ndim, int radius, int boundary, const Geom& g) {
   if (ndim != 2 || (radius != 1 && radius != 2)) return false;
   if (g.nx % 2 != 0) return false;
+  return !(boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % kRB != 0));
+}
+
+bool stream2d_eligible(int ndim, int radius, int boundary, const Geom& g, const void* a,
+                       const void* b) {
+  if (!stream2d_shape_ok(ndim, radius, boundary, g)) return false;
   if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return false;
-  if (boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % kRB != 0)) return false;
   return tensor_map_encoder() != nullptr;
 }
 

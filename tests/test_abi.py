@@ -124,3 +124,21 @@ def test_plan_is_a_context_manager(stencil):
         assert p.get_tuning() == (4, stencil.VARIANT_PERSISTENT)
     assert p.handle is None
     p.close()  # closing twice is harmless
+
+
+def test_default_goes_direct_for_shapes_the_streaming_kernels_cannot_take(stencil):
+    heat3 = np.zeros((3, 3, 3))
+    heat3[1, 1, 1] = 0.4
+    for d in range(3):
+        for e in (0, 2):
+            i = [1, 1, 1]
+            i[d] = e
+            heat3[tuple(i)] = 0.1
+    cases = [((64, 64, 64), heat3, stencil.PERIODIC, stencil.VARIANT_STREAM),
+             ((63, 63, 63), heat3, stencil.DIRICHLET_ZERO, stencil.VARIANT_DIRECT),   # odd nx
+             ((64, 64, 96), heat3, stencil.PERIODIC, stencil.VARIANT_DIRECT),         # nx % 64 != 0
+             ((2048, 2047), np.ones(9) / 9, stencil.DIRICHLET_ZERO, stencil.VARIANT_DIRECT),
+             ((2048, 2048), np.ones(9) / 9, stencil.DIRICHLET_ZERO, stencil.VARIANT_STREAM)]
+    for dims, w, boundary, want in cases:
+        with stencil.Plan(dims, 1, w, boundary) as p:
+            assert p.get_tuning() == (1, want), dims
