@@ -120,11 +120,14 @@ int stencil_run_f32(stencil_plan p, float* d_grid, float* d_work, int64_t T, voi
  *   dL/dkappa_i = -(dt/2) sum_t sum_{faces n} (lambda^{t+1}_i - lambda^{t+1}_n)(u^t_i - u^t_n)
  *   (ghost faces under Dirichlet: -dt sum_t lambda^{t+1}_i u^t_i per face),
  * with dt held constant.  The forward states are checkpointed every
- * ckpt_every steps (0 = about sqrt(T)) and recomputed one segment at a time
- * in reverse, so device memory grows with sqrt(T), not T; the last segment's
- * states are kept by the forward sweep and never recomputed.  ckpt_every = 1
- * keeps every state (no recompute, T + 10 grids of scratch: 126 GiB for
- * 256^3 and T = 1000, which an HBM3e part of 288 GB holds).
+ * ckpt_every steps and recomputed one segment at a time in reverse, so
+ * device memory grows with sqrt(T) rather than T when ckpt_every is about
+ * sqrt(T); the last segment's states are kept by the forward sweep and never
+ * recomputed.  ckpt_every = 1 keeps every state (no recompute, T + 10 grids
+ * of scratch: 126 GiB for 256^3 and T = 1000, which an HBM3e part of 288 GB
+ * holds).  ckpt_every = 0 chooses: every state when those T + 10 grids fit
+ * in half of the free device memory, else about sqrt(T).  The results do not
+ * depend on the interval (bitwise).
  * d_grad_u0 and d_grad_kappa (device, caller-owned, same shape) are
  * overwritten; *h_loss (host) receives L and the call waits for the stream. */
 int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,

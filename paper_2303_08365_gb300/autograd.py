@@ -5,8 +5,9 @@ field after T explicit steps of du/dt = div(kappa grad u) (the paper's Eq. 1
 with a per-cell diffusivity).  Its backward takes the upstream gradient
 dL/du^T as lambda^T and sweeps the transposed stencil backward in time
 (stencil_adjoint_vjp), recomputing the forward states from checkpoints every
-ckpt_every steps, so memory grows with sqrt(T).  dt is a constant (no
-gradient).  Every step runs in the library's CUDA kernels.
+ckpt_every steps (0: every state kept when it fits in half of the free
+device memory, else about sqrt(T)).  dt is a constant (no gradient).  Every
+step runs in the library's CUDA kernels.
 """
 import torch
 

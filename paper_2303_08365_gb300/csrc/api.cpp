@@ -769,7 +769,18 @@ int adjoint_core(stencil_plan_s* p, const double* d_u0, const double* d_kappa, d
   if (T < 0) return fail(STENCIL_ERR_ARG, "T must be >= 0");
   if (ckpt_every < 0) return fail(STENCIL_ERR_ARG, "ckpt_every must be >= 0");
   const size_t n = (size_t)p->cells();
-  int64_t c = ckpt_every > 0 ? ckpt_every : std::max<int64_t>(1, (int64_t)llround(std::sqrt((double)T)));
+  int64_t c = ckpt_every;
+  if (c == 0) {
+    // automatic: keep every state (no recompute) when T + 10 grids fit in half
+    // of the free device memory -- on a 288 GB part that covers most runs --
+    // else checkpoint about every sqrt(T) steps
+    size_t free_b = 0, total_b = 0;
+    const double need = ((double)T + 10.0) * (double)n * sizeof(double);
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= 0.5 * (double)free_b)
+      c = 1;
+    else
+      c = std::max<int64_t>(1, (int64_t)llround(std::sqrt((double)T)));
+  }
   if (T > 0 && c > T) c = T;
   const int64_t nck = T / c + 1;        // u at t = 0, c, 2c, ... (<= T)
   const int64_t nseg_states = c;        // u^{t0} .. u^{t0+c-1} of one segment
