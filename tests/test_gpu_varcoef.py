@@ -154,3 +154,30 @@ def test_autograd_function_matches_adjoint_and_oracle(st):
     assert normwise_rel(U.grad.cpu().numpy(), rgu) <= TOL
     assert normwise_rel(K.grad.cpu().numpy(), rgk) <= TOL
     p.close()
+
+
+@pytest.mark.parametrize("shape,radius,boundary,T", [((23, 31), 1, DIRICHLET, 9), ((9, 10, 11), 1, PERIODIC, 7),
+                                                     ((29, 33), 2, DIRICHLET, 5), ((400,), 2, PERIODIC, 12)])
+def test_constant_weight_autograd_is_the_reflected_stencil(st, shape, radius, boundary, T):
+    """d<v, S^T u0>/du0 = (S^T)^T v: the transposed stencil (reflected weights)
+    swept T steps over v.  Checked against the oracle with reflected weights and
+    by the dot-product identity <(S^T)^T v, w> = <v, S^T w> with the oracle's S."""
+    import torch
+    from paper_2303_08365_gb300 import autograd as ag
+    ndim = len(shape)
+    side = 2 * radius + 1
+    w = synth.uniform(500 + ndim + radius, (side,) * ndim)
+    w /= w.sum()
+    u0 = synth.uniform(501, shape)
+    v = synth.normal(502, shape)
+    x = torch.from_numpy(u0.copy()).cuda().requires_grad_(True)
+    uT = ag.sweep(x, shape, radius, w, boundary, T)
+    loss = (uT * torch.from_numpy(v).cuda()).sum()
+    loss.backward()
+    g = x.grad.cpu().numpy()
+    assert normwise_rel(uT.detach().cpu().numpy(), oracle.run(u0, w, radius, boundary, T, nthreads=0)) <= TOL
+    assert normwise_rel(g, oracle.run(v, ag.reflected(w), radius, boundary, T, nthreads=0)) <= TOL
+    z = synth.normal(503, shape)
+    lhs = float(np.sum(g * z))
+    rhs = float(np.sum(v * oracle.run(z, w, radius, boundary, T, nthreads=0)))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs), 1.0)

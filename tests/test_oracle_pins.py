@@ -276,3 +276,33 @@ def test_bad_arguments_are_rejected():
         oracle.run(u, np.ones((3, 3)), 1, 2, 1)
     with pytest.raises(ValueError):
         oracle.run_window(u, np.ones((3, 3)), 1, 0, 1, (0, 0), (5, 1))
+
+
+@pytest.mark.parametrize("shape,radius,boundary,T", [((7, 9), 1, 0, 3), ((5, 6, 7), 1, 1, 2), ((11,), 2, 0, 4),
+                                                     ((6, 8), 2, 1, 3)])
+def test_transpose_is_the_reflected_stencil(shape, radius, boundary, T):
+    """<S_refl^T v, z> = <v, S^T z> (S^T: T steps; S_refl: the weights w_{-o}),
+    for both boundary rules: the adjoint of the sweep is the sweep with
+    reflected weights.  Also checked entry by entry against the transposed
+    dense matrix."""
+    ndim = len(shape)
+    side = 2 * radius + 1
+    w = synth.uniform(800 + ndim, (side,) * ndim)
+    wr = np.ascontiguousarray(w[(slice(None, None, -1),) * ndim])
+    v = synth.normal(801, shape)
+    z = synth.normal(802, shape)
+    lhs = float(np.sum(oracle.run(v, wr, radius, boundary, T) * z))
+    rhs = float(np.sum(v * oracle.run(z, w, radius, boundary, T)))
+    assert abs(lhs - rhs) <= 1e-13 * max(abs(lhs), abs(rhs))
+    n = int(np.prod(shape))
+    A = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        A[:, j] = oracle.run(e.reshape(shape), w, radius, boundary, 1).reshape(-1)
+    AT = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        AT[:, j] = oracle.run(e.reshape(shape), wr, radius, boundary, 1).reshape(-1)
+    assert np.allclose(AT, A.T, rtol=0, atol=1e-15)
