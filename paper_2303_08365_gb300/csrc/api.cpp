@@ -372,127 +372,94 @@ int ensure_status(stencil_plan_s* p) {
   return STENCIL_OK;
 }
 
-int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
-  int Tb, variant;
-  if (tune_mode() == "full" && p->user_Tb == 0 && p->user_variant == 0 && p->tuned_Tb == 0) {
-    int tb0, v0;
-    if (!tune_lookup(plan_key(p), tb0, v0)) {
-      // tune on a scratch copy of the grid (the candidates' runs destroy it)
-      double* scratch = nullptr;
-      if (dev_malloc(&scratch, (size_t)p->cells() * sizeof(double)) == cudaSuccess) {
-        cudaMemcpyAsync(scratch, d_grid, (size_t)p->cells() * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        stencil_autotune(p, scratch, 4, s, nullptr);
-        cudaStreamSynchronize(s);
-        cudaFree(scratch);
-      } else {
-        cudaGetLastError();
-      }
+// STENCIL_TUNE=full: the first run of an untuned shape times the candidates
+// on a scratch copy of the grid (their runs destroy it) and records the best.
+void tune_on_first_run(stencil_plan_s* p, const double* d_grid, cudaStream_t s) {
+  if (tune_mode() != "full" || p->user_Tb != 0 || p->user_variant != 0 || p->tuned_Tb != 0) return;
+  int tb0, v0;
+  if (tune_lookup(plan_key(p), tb0, v0)) return;
+  double* scratch = nullptr;
+  if (dev_malloc(&scratch, (size_t)p->cells() * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaMemcpyAsync(scratch, d_grid, (size_t)p->cells() * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  stencil_autotune(p, scratch, 4, s, nullptr);
+  cudaStreamSynchronize(s);
+  cudaFree(scratch);
+}
+
+// Persistent temporal kernel: Tb steps in shared memory per exchange, tiles
+// synchronised by per-tile flags, one launch for all T steps.
+int run_persistent_tb(stencil_plan_s* p, double* d_grid, int64_t T, int Tb, cudaStream_t s) {
+  PersistTbLaunch L;
+  persist_tiling(p->g.ny, p->g.nx, Tb, sm_count(), &L.tiles_y, &L.tiles_x, &L.reach_y, &L.reach_x);
+  const int ntiles = L.tiles_y * L.tiles_x;
+  if (p->flags_cap < ntiles) {
+    cudaFree(p->d_flags);
+    p->d_flags = nullptr;
+    p->flags_cap = 0;
+    CUDA_TRY(dev_malloc(&p->d_flags, ntiles * sizeof(unsigned int)), "allocating the tile flags");
+    p->flags_cap = ntiles;
+  }
+  CUDA_TRY(cudaMemsetAsync(p->d_flags, 0, ntiles * sizeof(unsigned int), s), "clearing the tile flags");
+  L.a = d_grid;
+  L.b = p->d_tmp;
+  L.ny = p->g.ny;
+  L.nx = p->g.nx;
+  L.T = T;
+  L.wdev = p->d_w;
+  L.flags = p->d_flags;
+  L.status = p->d_status;
+  L.spin_limit = kSpinLimitNs;
+  cudaError_t e = launch_persist_tb(p->shape, p->boundary, Tb, L, sm_count(), s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the persistent temporal kernel");
+  return STENCIL_OK;
+}
+
+// One-step persistent kernel (the batched kernel with a single item): its
+// device work list for (d_grid, T) comes from the plan's LRU cache.
+int run_persistent_step(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
+  stencil_batch_s* hit = nullptr;
+  for (auto& e : p->persist)
+    if (e.grid == d_grid && e.T == T) {
+      e.last_use = ++p->persist_clock;
+      hit = e.batch;
     }
-  }
-  choose(p, Tb, variant);
-  const bool forced = p->user_Tb > 0 || p->user_variant > 0;
-  int rc = ensure(&p->d_tmp, (size_t)p->cells(), "allocating the ping-pong buffer");
-  if (rc) return rc;
-  rc = ensure_status(p);
-  if (rc) return rc;
-  rc = ensure_weights(p);
-  if (rc) return rc;
-  const bool stream_ok = p->ndim == 3
-                             ? stream3d_eligible(p->ndim, p->radius, p->shape, p->boundary, p->g, d_grid,
-                                                 p->d_tmp)
-                             : stream2d_eligible(p->ndim, p->radius, p->boundary, p->g, d_grid, p->d_tmp);
-  if (variant == kVariantStream && !stream_ok) {
-    if (forced)
-      return fail(STENCIL_ERR_UNSUPPORTED,
-                  "the streaming kernel needs a 2D or 3D radius-1 plan, even nx, 16-byte aligned "
-                  "buffers and, for periodic grids, nx %% 64 == 0 and ny a multiple of the tile "
-                  "height (16; 32 for the 3D star)");
-    variant = kVariantDirect;
-  }
-  if (variant == kVariantPersistent && Tb > 1) {
-    // Tb steps in shared memory per device-wide barrier (2D radius 1, star or box)
-    if (p->ndim != 2 || p->radius != 1 || (p->taps.n != 5 && p->taps.n != 9) || Tb > 8) {
-      if (forced)
-        return fail(STENCIL_ERR_UNSUPPORTED, "the persistent temporal kernel covers 2D radius-1 plans");
-      variant = kVariantDirect;
-      Tb = 1;
-    } else {
-      PersistTbLaunch L;
-      persist_tiling(p->g.ny, p->g.nx, Tb, sm_count(), &L.tiles_y, &L.tiles_x, &L.reach_y, &L.reach_x);
-      const int ntiles = L.tiles_y * L.tiles_x;
-      if (p->flags_cap < ntiles) {
-        cudaFree(p->d_flags);
-        p->d_flags = nullptr;
-        p->flags_cap = 0;
-        CUDA_TRY(dev_malloc(&p->d_flags, ntiles * sizeof(unsigned int)), "allocating the tile flags");
-        p->flags_cap = ntiles;
-      }
-      CUDA_TRY(cudaMemsetAsync(p->d_flags, 0, ntiles * sizeof(unsigned int), s), "clearing the tile flags");
-      L.a = d_grid;
-      L.b = p->d_tmp;
-      L.ny = p->g.ny;
-      L.nx = p->g.nx;
-      L.T = T;
-      L.wdev = p->d_w;
-      L.flags = p->d_flags;
-      L.status = p->d_status;
-      L.spin_limit = 2000000000LL;
-      cudaError_t e = launch_persist_tb(p->shape, p->boundary, Tb, L, sm_count(), s);
-      if (e != cudaSuccess) return cuda_fail(e, "launching the persistent temporal kernel");
-      return STENCIL_OK;
+  if (!hit) {
+    if ((int)p->persist.size() >= kPersistCache) {
+      auto lru = std::min_element(p->persist.begin(), p->persist.end(),
+                                  [](const auto& x, const auto& y) { return x.last_use < y.last_use; });
+      lru->batch->d_partner = nullptr;  // the plan's own ping-pong buffer
+      stencil_batch_destroy(lru->batch);
+      p->persist.erase(lru);
     }
-  }
-  if (variant == kVariantPersistent) {
-    if (!persistent_eligible(p) || T > (1 << 30)) {
-      if (forced)
-        return fail(STENCIL_ERR_UNSUPPORTED, "the persistent kernel covers 2D 5-point star plans");
-      variant = kVariantDirect;
-    } else {
-      stencil_batch_s* hit = nullptr;
-      for (auto& e : p->persist)
-        if (e.grid == d_grid && e.T == T) {
-          e.last_use = ++p->persist_clock;
-          hit = e.batch;
-        }
-      if (!hit) {
-        if ((int)p->persist.size() >= kPersistCache) {
-          auto lru = std::min_element(p->persist.begin(), p->persist.end(),
-                                      [](const auto& x, const auto& y) { return x.last_use < y.last_use; });
-          lru->batch->d_partner = nullptr;  // the plan's own ping-pong buffer
-          stencil_batch_destroy(lru->batch);
-          p->persist.erase(lru);
-        }
-        auto* b = new (std::nothrow) stencil_batch_s();
-        if (!b) return fail(STENCIL_ERR_OOM, "allocating the persistent plan");
-        BatchItemDev it;
-        it.a = d_grid;
-        it.b = p->d_tmp;
-        it.ny = p->g.ny;
-        it.nx = p->g.nx;
-        it.T = (int)T;
-        for (int k = 0; k < 5; ++k) it.w[k] = p->taps.w[k];
-        it.zero[0] = it.zero[1] = 0.0;
-        rc = batch_init(b, std::vector<BatchItemDev>{it}, p->boundary);
-        if (rc) {
-          stencil_batch_destroy(b);
-          return rc;
-        }
-        p->persist.push_back({d_grid, T, b, ++p->persist_clock});
-        hit = b;
-      }
-      return batch_enqueue(hit, s);
+    auto* b = new (std::nothrow) stencil_batch_s();
+    if (!b) return fail(STENCIL_ERR_OOM, "allocating the persistent plan");
+    BatchItemDev it;
+    it.a = d_grid;
+    it.b = p->d_tmp;
+    it.ny = p->g.ny;
+    it.nx = p->g.nx;
+    it.T = (int)T;
+    for (int k = 0; k < 5; ++k) it.w[k] = p->taps.w[k];
+    it.zero[0] = it.zero[1] = 0.0;
+    const int rc = batch_init(b, std::vector<BatchItemDev>{it}, p->boundary);
+    if (rc) {
+      stencil_batch_destroy(b);
+      return rc;
     }
+    p->persist.push_back({d_grid, T, b, ++p->persist_clock});
+    hit = b;
   }
-  if (variant == kVariantTemporal && !temporal_supported(p->ndim, p->radius, Tb)) {
-    if (forced)
-      return fail(STENCIL_ERR_UNSUPPORTED,
-                  "temporal blocking covers radius-1 plans with Tb in {2, 4} (3D) or {2, 4, 8} (2D), "
-                  "and 1D plans of radius 1 or 2 with Tb in {2, 4, 8}");
-    variant = default_variant(p) == kVariantStream && stream_ok ? kVariantStream : kVariantDirect;
-  }
-  if (variant != kVariantTemporal) Tb = 1;
-  if (variant != kVariantDirect && variant != kVariantStream && variant != kVariantTemporal)
-    return fail(STENCIL_ERR_UNSUPPORTED, "variant %s is not available", stencil_variant_name(variant));
+  return batch_enqueue(hit, s);
+}
+
+// One launch per step (direct or streaming) or per Tb steps (temporal, with
+// single steps for the remainder), ping-ponging with the plan's buffer; the
+// result ends in d_grid.
+int run_steps(stencil_plan_s* p, double* d_grid, int64_t T, int Tb, int variant, bool stream_ok,
+              cudaStream_t s) {
   const int sms = sm_count();
   const bool equal_box = p->shape == Shape::kBox && taps_all_equal(p->taps);
   // the single-step kernel for the steps that do not fill a whole Tb block
@@ -521,10 +488,60 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
     t += steps;
   }
   if (a != d_grid)
-    CUDA_TRY(cudaMemcpyAsync(d_grid, a, (size_t)p->cells() * sizeof(double),
-                             cudaMemcpyDeviceToDevice, s),
+    CUDA_TRY(cudaMemcpyAsync(d_grid, a, (size_t)p->cells() * sizeof(double), cudaMemcpyDeviceToDevice, s),
              "copying the result back");
   return STENCIL_OK;
+}
+
+// A constant-weight sweep: resolve (Tb, variant), make sure the plan's
+// buffers exist, fall back from a variant the grid cannot use (an error when
+// the caller forced it) and dispatch.
+int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
+  tune_on_first_run(p, d_grid, s);
+  int Tb, variant;
+  choose(p, Tb, variant);
+  const bool forced = p->user_Tb > 0 || p->user_variant > 0;
+  int rc = ensure(&p->d_tmp, (size_t)p->cells(), "allocating the ping-pong buffer");
+  if (rc) return rc;
+  rc = ensure_status(p);
+  if (rc) return rc;
+  rc = ensure_weights(p);
+  if (rc) return rc;
+  const bool stream_ok = p->ndim == 3
+                             ? stream3d_eligible(p->ndim, p->radius, p->shape, p->boundary, p->g, d_grid,
+                                                 p->d_tmp)
+                             : stream2d_eligible(p->ndim, p->radius, p->boundary, p->g, d_grid, p->d_tmp);
+  if (variant == kVariantStream && !stream_ok) {
+    if (forced)
+      return fail(STENCIL_ERR_UNSUPPORTED,
+                  "the streaming kernel needs a 2D or 3D radius-1 plan, even nx, 16-byte aligned "
+                  "buffers and, for periodic grids, nx %% 64 == 0 and ny a multiple of the tile "
+                  "height (16; 32 for the 3D star)");
+    variant = kVariantDirect;
+  }
+  if (variant == kVariantPersistent && Tb > 1) {
+    if (p->ndim == 2 && p->radius == 1 && (p->taps.n == 5 || p->taps.n == 9) && Tb <= 8)
+      return run_persistent_tb(p, d_grid, T, Tb, s);
+    if (forced) return fail(STENCIL_ERR_UNSUPPORTED, "the persistent temporal kernel covers 2D radius-1 plans");
+    variant = kVariantDirect;
+    Tb = 1;
+  }
+  if (variant == kVariantPersistent) {
+    if (persistent_eligible(p) && T <= (1 << 30)) return run_persistent_step(p, d_grid, T, s);
+    if (forced) return fail(STENCIL_ERR_UNSUPPORTED, "the persistent kernel covers 2D 5-point star plans");
+    variant = kVariantDirect;
+  }
+  if (variant == kVariantTemporal && !temporal_supported(p->ndim, p->radius, Tb)) {
+    if (forced)
+      return fail(STENCIL_ERR_UNSUPPORTED,
+                  "temporal blocking covers radius-1 plans with Tb in {2, 4} (3D) or {2, 4, 8} (2D), "
+                  "and 1D plans of radius 1 or 2 with Tb in {2, 4, 8}");
+    variant = default_variant(p) == kVariantStream && stream_ok ? kVariantStream : kVariantDirect;
+  }
+  if (variant != kVariantTemporal) Tb = 1;
+  if (variant != kVariantDirect && variant != kVariantStream && variant != kVariantTemporal)
+    return fail(STENCIL_ERR_UNSUPPORTED, "variant %s is not available", stencil_variant_name(variant));
+  return run_steps(p, d_grid, T, Tb, variant, stream_ok, s);
 }
 
 VarcoefBufs coef_bufs(stencil_plan_s* p) {
@@ -610,7 +627,7 @@ int batch_enqueue(stencil_batch_s* b, cudaStream_t s) {
   L.boundary = b->boundary;
   L.barrier = b->d_ctl;
   L.status = (int*)(b->d_ctl + 2);
-  L.spin_limit = 2000000000LL;  // 2 s of wall time per barrier wait
+  L.spin_limit = kSpinLimitNs;
   L.barrier_blocks = 0;
   CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing the barrier words");
   cudaError_t e = launch_batched(L, b->blocks, s);

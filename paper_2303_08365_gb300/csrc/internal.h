@@ -186,6 +186,10 @@ cudaError_t launch_persist_tb(Shape shape, int boundary, int Tb, const PersistTb
 // blocks x 256 threads; out receives one double per thread.
 cudaError_t launch_fp64_peak(int blocks, int iters, double* out, cudaStream_t stream);
 
+// Wall-time limit of every bounded device-side wait the host configures
+// (barriers of the persistent kernels): 2 s.
+constexpr long long kSpinLimitNs = 2000000000LL;
+
 // Launch accounting (every kernel launch of the library adds one).
 extern std::atomic<int64_t> g_launches;
 

@@ -159,7 +159,7 @@ int stencil_run_2d_static(int64_t ny, int64_t nx, const double* weights, int bou
   L.boundary = boundary;
   L.barrier = d_ctl;
   L.status = reinterpret_cast<int*>(d_ctl + 2);
-  L.spin_limit = 2000000000LL;
+  L.spin_limit = kSpinLimitNs;
   L.barrier_blocks = 0;
   int blocks = s.blocks;
   if (ntiles < blocks) blocks = (int)ntiles;
