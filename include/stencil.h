@@ -176,6 +176,27 @@ int stencil_batch_status(stencil_batch b);
 
 void stencil_batch_destroy(stencil_batch b);
 
+/* Kernel configuration of a batch: cells_per_thread (1, 2 or 4; a tile is
+ * 256 * cells_per_thread consecutive cells of one item) and cooperative
+ * blocks per SM (1 .. the kernel's occupancy); 0 restores a default (2, and
+ * min(occupancy, 4)).  Rebuilds the tile list and recaptures the graph on
+ * the next run; waits for the device.  Results do not depend on it
+ * (bitwise). */
+int stencil_batch_set_tuning(stencil_batch b, int cells_per_thread, int blocks_per_sm);
+
+/* Reports the batch's cells per thread and blocks per SM. */
+int stencil_batch_get_tuning(stencil_batch b, int* cells_per_thread, int* blocks_per_sm);
+
+/* The batch autotuner: times every (cells_per_thread, blocks_per_sm) pair on
+ * scratch copies of the items (the caller's grids are not modified), each
+ * item advanced ceil(T * probe_steps / max T) steps so the probe keeps the
+ * batch's mix of step counts, keeps the fastest and rebuilds the batch for
+ * it.  Synchronous; allocates and frees two copies of the items' cells.
+ * *best_gstencils (may be NULL) receives the winner's rate in 1e9 cell
+ * updates per second. */
+int stencil_batch_autotune(stencil_batch b, int64_t probe_steps, void* cuda_stream,
+                           double* best_gstencils);
+
 /* Convenience: create, run once, wait, destroy. */
 int stencil_run_batched(const stencil_batch_item* items, int n, int boundary,
                         void* cuda_stream);

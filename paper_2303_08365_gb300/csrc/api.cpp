@@ -23,7 +23,6 @@
 
 namespace gbst {
 std::atomic<int64_t> g_launches{0};
-int batched_blocks_per_sm();
 int set_error(int code, const char* msg);
 }  // namespace gbst
 
@@ -164,6 +163,10 @@ struct stencil_batch_s {
   cudaStream_t capture_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   bool use_graph = true;
+  // kernel configuration (stencil_batch_set_tuning / stencil_batch_autotune)
+  int cpt = 0;             // cells per thread (1, 2, 4); 0 = the default
+  int per_sm = 0;          // cooperative blocks per SM; 0 = min(occupancy, 4)
+  std::vector<BatchItemDev> hi;  // the item descriptors, kept to rebuild the tile list
 };
 
 namespace {
@@ -592,8 +595,10 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return hi[a].T > hi[c].T; });
+  if (b->cpt == 0) b->cpt = batched_default_cpt();
+  b->hi = hi;
   std::vector<BatchTile> tiles;
-  const int tc = batched_tile_cells();
+  const int tc = batched_tile_cells(b->cpt);
   for (int i : order) {
     if (hi[i].T == 0) continue;
     const int64_t cells = (int64_t)hi[i].ny * hi[i].nx;
@@ -611,9 +616,10 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
              "copying the tile list");
   CUDA_TRY(dev_malloc(&b->d_ctl, 4 * sizeof(unsigned int)), "allocating the barrier words");
   CUDA_TRY(cudaMemset(b->d_ctl, 0, 4 * sizeof(unsigned int)), "clearing the barrier words");
-  const int per_sm = batched_blocks_per_sm();
-  if (per_sm < 1) return fail(STENCIL_ERR_CUDA, "the batched kernel does not fit on an SM");
-  b->blocks = sm_count() * std::min(per_sm, 4);
+  const int occ = batched_blocks_per_sm(b->cpt);
+  if (occ < 1) return fail(STENCIL_ERR_CUDA, "the batched kernel does not fit on an SM");
+  const int per_sm = b->per_sm > 0 ? std::min(b->per_sm, occ) : std::min(occ, 4);
+  b->blocks = sm_count() * per_sm;
   if (b->ntiles > 0 && b->ntiles < b->blocks) b->blocks = b->ntiles;
   return STENCIL_OK;
 }
@@ -630,7 +636,7 @@ int batch_enqueue(stencil_batch_s* b, cudaStream_t s) {
   L.spin_limit = kSpinLimitNs;
   L.barrier_blocks = 0;
   CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing the barrier words");
-  cudaError_t e = launch_batched(L, b->blocks, s);
+  cudaError_t e = launch_batched(L, b->blocks, b->cpt, s);
   if (e != cudaSuccess) return cuda_fail(e, "launching the batched kernel");
   return STENCIL_OK;
 }
@@ -1107,6 +1113,140 @@ int stencil_batch_status(stencil_batch b) {
   return STENCIL_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Frees a batch's tile list, item table and barrier words and drops its graph
+// (the partner buffer stays), after the device has finished with them.
+void batch_release_lists(stencil_batch_s* b) {
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->use_graph = true;
+  cudaFree(b->d_items);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_ctl);
+  b->d_items = nullptr;
+  b->d_tiles = nullptr;
+  b->d_ctl = nullptr;
+}
+
+// Rebuilds the tile list for the batch's current kernel configuration.
+int batch_rebuild(stencil_batch_s* b) {
+  batch_release_lists(b);
+  const std::vector<BatchItemDev> hi = b->hi;
+  return batch_init(b, hi, b->boundary);
+}
+
+}  // namespace
+
+extern "C" {
+
+int stencil_batch_set_tuning(stencil_batch b, int cells_per_thread, int blocks_per_sm) {
+  g_err.clear();
+  if (!b) return fail(STENCIL_ERR_ARG, "batch is NULL");
+  if (cells_per_thread != 0 && cells_per_thread != 1 && cells_per_thread != 2 && cells_per_thread != 4)
+    return fail(STENCIL_ERR_ARG, "cells_per_thread must be 0, 1, 2 or 4");
+  if (blocks_per_sm < 0 || blocks_per_sm > 32) return fail(STENCIL_ERR_ARG, "blocks_per_sm must be in [0, 32]");
+  b->cpt = cells_per_thread;
+  b->per_sm = blocks_per_sm;
+  return batch_rebuild(b);
+}
+
+int stencil_batch_get_tuning(stencil_batch b, int* cells_per_thread, int* blocks_per_sm) {
+  g_err.clear();
+  if (!b || !cells_per_thread || !blocks_per_sm) return fail(STENCIL_ERR_ARG, "NULL argument");
+  *cells_per_thread = b->cpt;
+  *blocks_per_sm = b->blocks / std::max(1, sm_count());
+  return STENCIL_OK;
+}
+
+int stencil_batch_autotune(stencil_batch b, int64_t probe_steps, void* cuda_stream, double* best_gstencils) {
+  g_err.clear();
+  if (!b) return fail(STENCIL_ERR_ARG, "batch is NULL");
+  if (probe_steps < 1 || probe_steps > (1 << 20)) return fail(STENCIL_ERR_ARG, "probe_steps must be in [1, 2^20]");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // scratch copies of every item (grid and partner): the probes leave the
+  // caller's grids untouched
+  int64_t total = 0, updates = 0;
+  for (const BatchItemDev& it : b->hi) total += (int64_t)it.ny * it.nx;
+  double* scratch = nullptr;
+  CUDA_TRY(dev_malloc(&scratch, 2 * (size_t)std::max<int64_t>(total, 1) * sizeof(double)),
+           "allocating the autotuner's scratch grids");
+  std::vector<BatchItemDev> probe = b->hi;
+  int64_t off = 0;
+  int rc = STENCIL_OK;
+  // each item's T scaled by probe_steps / max T (rounded up): the probe keeps
+  // the batch's mix of step counts, so the tail where few items are still
+  // active weighs in as it does in a full run
+  const int64_t max_T = std::max<int64_t>(1, b->max_T);
+  for (size_t i = 0; i < probe.size(); ++i) {
+    const int64_t cells = (int64_t)probe[i].ny * probe[i].nx;
+    probe[i].a = scratch + off;
+    probe[i].b = scratch + total + off;
+    probe[i].T = probe[i].T == 0 ? 0
+                                 : (int)std::max<int64_t>(1, (probe[i].T * std::min(probe_steps, max_T) + max_T - 1) /
+                                                                 max_T);
+    updates += cells * probe[i].T;
+    if (cudaMemcpyAsync(probe[i].a, b->hi[i].a, cells * sizeof(double), cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+      rc = fail(STENCIL_ERR_CUDA, "copying the items to the autotuner's scratch");
+    off += cells;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = fail(STENCIL_ERR_CUDA, "creating events");
+  double best = -1.0;
+  int best_cpt = batched_default_cpt(), best_per_sm = 0;
+  for (int cpt : {1, 2, 4}) {
+    const int occ = batched_blocks_per_sm(cpt);
+    for (int per_sm = 1; !rc && per_sm <= std::min(occ, 4); ++per_sm) {
+      auto* t = new (std::nothrow) stencil_batch_s();
+      if (!t) {
+        rc = fail(STENCIL_ERR_OOM, "allocating a probe batch");
+        break;
+      }
+      t->cpt = cpt;
+      t->per_sm = per_sm;
+      rc = batch_init(t, probe, b->boundary);
+      if (!rc) rc = batch_enqueue(t, s);  // warm-up
+      float best_ms = -1.f;               // the faster of two timed runs
+      for (int rep = 0; rep < 2 && !rc; ++rep) {
+        cudaEventRecord(e0, s);
+        rc = batch_enqueue(t, s);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) best_ms = ms;
+      }
+      if (!rc) {
+        const double rate = (double)updates / (std::max(best_ms, 1e-3f) * 1e-3) / 1e9;
+        if (rate > best) {
+          best = rate;
+          best_cpt = cpt;
+          best_per_sm = per_sm;
+        }
+      }
+      t->d_partner = nullptr;  // scratch, freed below
+      stencil_batch_destroy(t);
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(scratch);
+  if (rc) return rc;
+  if (best < 0) return fail(STENCIL_ERR_CUDA, "no batch configuration ran");
+  b->cpt = best_cpt;
+  b->per_sm = best_per_sm;
+  rc = batch_rebuild(b);
+  if (rc) return rc;
+  if (best_gstencils) *best_gstencils = best;
+  return STENCIL_OK;
+}
+
 void stencil_batch_destroy(stencil_batch b) {
   if (!b) return;
   cudaDeviceSynchronize();
@@ -1180,7 +1320,7 @@ int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream) {
   L.status = reinterpret_cast<int*>(ctl + 2);
   L.spin_limit = (long long)(limit_ms * 1e6);
   L.barrier_blocks = 2;  // the launch below has one block
-  cudaError_t e = launch_batched(L, 1, s);
+  cudaError_t e = launch_batched(L, 1, batched_default_cpt(), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   int st = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&st, ctl + 2, sizeof(int), cudaMemcpyDeviceToHost);

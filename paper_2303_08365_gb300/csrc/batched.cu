@@ -22,11 +22,12 @@ namespace gbst {
 namespace {
 
 constexpr int kThreads = 256;
-// A tile is a run of kTileCells consecutive cells of one grid in row-major
-// order (two per thread, kThreads apart), so every warp is full except at a
-// grid's last tile: the FP64 unit charges a warp instruction the same time
-// whatever the number of active lanes.
-constexpr int kTileCells = 2 * kThreads;
+// A tile is a run of CPT * kThreads consecutive cells of one grid in row-major
+// order (CPT cells per thread, kThreads apart), so every warp is full except
+// at a grid's last tile: the FP64 unit charges a warp instruction the same
+// time whatever the number of active lanes.  CPT (1, 2 or 4) is chosen by the
+// batch autotuner; 2 is the default.
+constexpr int kDefaultCpt = 2;
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -75,13 +76,14 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, long long 
   return ok != 0;
 }
 
-// One step of one tile: cells k0 .. k0+n-1 of the item (row-major), two per
+// One step of one tile: cells k0 .. k0+n-1 of the item (row-major), CPT per
 // thread.  The per-cell chain is the generic sweep's tap order.
+template <int CPT>
 __device__ __forceinline__ void tile_step(const BatchItemDev& it, const double* __restrict__ src,
                                           double* __restrict__ dst, int k0, int n, bool periodic) {
   const int ny = it.ny, nx = it.nx;
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < CPT; ++r) {
     const int c = threadIdx.x + r * kThreads;
     if (c >= n) break;
     const int k = k0 + c;
@@ -105,7 +107,7 @@ __device__ __forceinline__ void tile_step(const BatchItemDev& it, const double* 
     const double vc = __ldcg(row + x);
     const double ve = ine ? __ldcg(row + xe) : 0.0;
     const double vs = ins ? __ldcg(src + (int64_t)ys * nx + x) : 0.0;
-    double acc = fma(it.w[0], vn, it.zero[r]);
+    double acc = fma(it.w[0], vn, it.zero[r & 1]);
     acc = fma(it.w[1], vw, acc);
     acc = fma(it.w[2], vc, acc);
     acc = fma(it.w[3], ve, acc);
@@ -114,6 +116,7 @@ __device__ __forceinline__ void tile_step(const BatchItemDev& it, const double* 
   }
 }
 
+template <int CPT>
 __global__ void __launch_bounds__(kThreads) k_batched(BatchLaunch L) {
   const unsigned int G = gridDim.x;
   const unsigned int arrivals = L.barrier_blocks > 0 ? (unsigned int)L.barrier_blocks : G;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_batched(BatchLaunch L) {
       if (it.T <= t) break;  // tiles are sorted by T, largest first
       const double* src = (t & 1) ? it.b : it.a;
       double* dst = (t & 1) ? it.a : it.b;
-      tile_step(it, src, dst, tl.k0, tl.n, periodic);
+      tile_step<CPT>(it, src, dst, tl.k0, tl.n, periodic);
     }
     if (!grid_barrier(L.barrier, arrivals, L.spin_limit, L.status)) return;
   }
@@ -415,9 +418,12 @@ cudaError_t launch_persist_tb(Shape shape, int boundary, int Tb, const PersistTb
 }
 
 int batched_block_size() { return kThreads; }
-int batched_tile_cells() { return kTileCells; }
+int batched_default_cpt() { return kDefaultCpt; }
+int batched_tile_cells(int cpt) { return cpt * kThreads; }
 
-cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, cudaStream_t stream) {
+namespace {
+template <int CPT>
+cudaError_t launch_batched_cpt(const BatchLaunch& L, int grid_blocks, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid_blocks, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
@@ -428,17 +434,29 @@ cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, cudaStream_t s
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_batched, L);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_batched<CPT>, L);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return e;
 }
+}  // namespace
 
-// Blocks of k_batched that fit on one SM at once (for the cooperative grid size).
-int batched_blocks_per_sm() {
+cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, int cpt, cudaStream_t stream) {
+  switch (cpt) {
+    case 1: return launch_batched_cpt<1>(L, grid_blocks, stream);
+    case 2: return launch_batched_cpt<2>(L, grid_blocks, stream);
+    case 4: return launch_batched_cpt<4>(L, grid_blocks, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Blocks of k_batched<cpt> that fit on one SM at once (for the cooperative grid size).
+int batched_blocks_per_sm(int cpt) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched, kThreads, 0) != cudaSuccess)
-    return 0;
-  return n;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (cpt == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<1>, kThreads, 0);
+  if (cpt == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<2>, kThreads, 0);
+  if (cpt == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched<4>, kThreads, 0);
+  return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace gbst

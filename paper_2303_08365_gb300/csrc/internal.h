@@ -157,9 +157,12 @@ struct BatchLaunch {
   long long spin_limit;   // bounded waits: wall-time limit in ns
   int barrier_blocks;     // arrivals a device-wide barrier waits for (0: the grid size)
 };
-cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, cudaStream_t stream);
+// cpt: cells per thread of the kernel (1, 2 or 4); a tile holds cpt * 256 cells.
+cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, int cpt, cudaStream_t stream);
 int batched_block_size();
-int batched_tile_cells();
+int batched_default_cpt();
+int batched_tile_cells(int cpt);
+int batched_blocks_per_sm(int cpt);
 
 // Persistent temporal blocking for one small 2D grid (radius 1, star or box):
 // Tb in {2, 4, 8} steps per exchange, tiles synchronised by per-tile flags.

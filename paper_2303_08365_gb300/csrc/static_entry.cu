@@ -28,7 +28,6 @@
 #include <mutex>
 
 namespace gbst {
-int batched_blocks_per_sm();
 int set_error(int code, const char* msg);  // api.cpp: thread-local message for stencil_last_error
 }
 
@@ -80,7 +79,7 @@ int setup_device(int dev, DeviceSetup& out) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
     if (e != cudaSuccess) return sfail(STENCIL_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
-    int per_sm = batched_blocks_per_sm(), sms = 0;
+    int per_sm = batched_blocks_per_sm(batched_default_cpt()), sms = 0;
     if (per_sm < 1 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return sfail(STENCIL_ERR_CUDA, "querying the persistent kernel's occupancy failed");
     s.base = static_cast<unsigned char*>(ptr);
@@ -136,7 +135,7 @@ int stencil_run_2d_static(int64_t ny, int64_t nx, const double* weights, int bou
   item.w[3] = weights[5];  // east (x+1)
   item.w[4] = weights[7];  // south (y+1)
   // the tile list is a pure function of the shape: runs of tc consecutive cells
-  const int tc = batched_tile_cells();
+  const int tc = batched_tile_cells(batched_default_cpt());
   const int64_t ntiles = (ny * nx + tc - 1) / tc;
   if (ntiles > kMaxTiles) return sfail(STENCIL_ERR_UNSUPPORTED, "tile list exceeds the static scratch");
   BatchTile* d_tiles = reinterpret_cast<BatchTile*>(s.base + kTileOff);
@@ -163,7 +162,7 @@ int stencil_run_2d_static(int64_t ny, int64_t nx, const double* weights, int bou
   L.barrier_blocks = 0;
   int blocks = s.blocks;
   if (ntiles < blocks) blocks = (int)ntiles;
-  if (launch_batched(L, blocks, stream) != cudaSuccess)
+  if (launch_batched(L, blocks, batched_default_cpt(), stream) != cudaSuccess)
     return sfail(STENCIL_ERR_CUDA, "launching the persistent kernel failed");
   return STENCIL_OK;
 }

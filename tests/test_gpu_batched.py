@@ -119,3 +119,37 @@ def test_one_call_entry_matches_batch_object(st):
             assert np.array_equal(x.cpu().numpy(), y.cpu().numpy())
             ref = oracle.run(g0, synth.heat_weights(2, al), 1, boundary, T)
             assert normwise_rel(x.cpu().numpy(), ref) <= TOL
+
+
+def test_autotuner_leaves_grids_alone_and_every_configuration_agrees(st):
+    """The batch autotuner probes on scratch copies (the caller's grids are not
+    modified), keeps a valid configuration, and every (cells per thread,
+    blocks per SM) gives the same bits as single-grid runs."""
+    import torch
+    items = [(37, 91, 0.11, 13), (128, 64, 0.2, 6), (5, 3, 0.05, 9), (300, 257, 0.15, 21), (1, 1, 0.1, 4)]
+    grids = [synth.uniform(90 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
+    refs = [single(st, g0, a, T, DIRICHLET) for g0, (_, _, a, T) in zip(grids, items)]
+    dev = [torch.from_numpy(g.copy()).cuda() for g in grids]
+    b = st.Batch(dev, [x[2] for x in items], [x[3] for x in items])
+    rate = b.autotune(probe_steps=4)
+    assert rate > 0
+    for g0, d in zip(grids, dev):
+        assert np.array_equal(d.cpu().numpy(), g0)      # untouched by the probes
+    cpt, per_sm = b.get_tuning()
+    assert cpt in (1, 2, 4) and per_sm >= 1
+    b.run()
+    assert b.status() == 0
+    for d, r in zip(dev, refs):
+        assert np.array_equal(d.cpu().numpy(), r)
+    for cpt in (1, 2, 4):
+        for per_sm in (1, 3):
+            for g0, d in zip(grids, dev):
+                d.copy_(torch.from_numpy(g0))
+            b.set_tuning(cpt, per_sm)
+            b.run()
+            assert b.status() == 0
+            for d, r in zip(dev, refs):
+                assert np.array_equal(d.cpu().numpy(), r), (cpt, per_sm)
+    with pytest.raises(st.StencilError):
+        b.set_tuning(3, 0)
+    b.close()
