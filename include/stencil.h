@@ -212,8 +212,12 @@ int stencil_plan_status(stencil_plan p, void* cuda_stream);
  * tuned: 3D radius 1 -> STREAM; 2D radius 1 -> PERSISTENT with Tb = 4 up to
  * 2^18 cells, PERSISTENT with Tb = 1 (5-point star) up to 3 * 2^20 cells,
  * else STREAM; 2D radius 2 -> STREAM; 1D -> TEMPORAL with Tb = 8; anything
- * else -> DIRECT.  A variant a plan cannot use falls back to DIRECT unless
- * it was forced, in which case stencil_run returns STENCIL_ERR_UNSUPPORTED. */
+ * else -> DIRECT.  STREAM needs an even nx and, for periodic grids, nx a
+ * multiple of 64 and ny a multiple of the tile height (32 for the 3D star,
+ * 16 otherwise); other shapes default to DIRECT.  A variant a plan cannot
+ * use (including STREAM on buffers not 16-byte aligned) falls back to DIRECT
+ * unless it was forced, in which case stencil_run returns
+ * STENCIL_ERR_UNSUPPORTED. */
 typedef enum {
   STENCIL_VARIANT_AUTO = 0,
   STENCIL_VARIANT_DIRECT = 1,     /* one launch per step, any shape */
