@@ -176,18 +176,23 @@ int stencil_batch_status(stencil_batch b);
 
 void stencil_batch_destroy(stencil_batch b);
 
-/* Kernel configuration of a batch: cells_per_thread (1, 2 or 4; a tile is
- * 256 * cells_per_thread consecutive cells of one item) and cooperative
- * blocks per SM (1 .. the kernel's occupancy); 0 restores a default (2, and
- * min(occupancy, 4)).  Rebuilds the tile list and recaptures the graph on
- * the next run; waits for the device.  Results do not depend on it
- * (bitwise). */
-int stencil_batch_set_tuning(stencil_batch b, int cells_per_thread, int blocks_per_sm);
+/* Kernel configuration of a batch.  Tb = 1 (or 0): one step per device-wide
+ * barrier, with cells_per_thread (1, 2 or 4; a tile is 256 *
+ * cells_per_thread consecutive cells of one item) and cooperative blocks per
+ * SM (1 .. the kernel's occupancy; 0 restores the defaults 2 and
+ * min(occupancy, 4)).  Tb = 2, 4 or 8: Tb steps in shared memory per
+ * exchange, every item cut into tiles of at most 16 x 32 cells that
+ * synchronise through per-tile flags with the tiles of the same item their
+ * halo reaches (cells_per_thread and blocks_per_sm are then ignored).
+ * Rebuilds the work list and recaptures the graph on the next run; waits for
+ * the device.  Results do not depend on it (bitwise). */
+int stencil_batch_set_tuning(stencil_batch b, int Tb, int cells_per_thread, int blocks_per_sm);
 
-/* Reports the batch's cells per thread and blocks per SM. */
-int stencil_batch_get_tuning(stencil_batch b, int* cells_per_thread, int* blocks_per_sm);
+/* Reports the batch's Tb, cells per thread (0 when Tb > 1) and blocks per SM. */
+int stencil_batch_get_tuning(stencil_batch b, int* Tb, int* cells_per_thread, int* blocks_per_sm);
 
-/* The batch autotuner: times every (cells_per_thread, blocks_per_sm) pair on
+/* The batch autotuner: times every configuration (Tb = 1 with each
+ * (cells_per_thread, blocks_per_sm) pair, and Tb = 2, 4, 8) on
  * scratch copies of the items (the caller's grids are not modified), each
  * item advanced ceil(T * probe_steps / max T) steps so the probe keeps the
  * batch's mix of step counts, keeps the fastest and rebuilds the batch for

@@ -64,8 +64,8 @@ SIGNATURES = [
     ("stencil_batch_status", ctypes.c_int, [_VP]),
     ("stencil_batch_destroy", None, [_VP]),
     ("stencil_run_batched", ctypes.c_int, [ctypes.POINTER(BatchItem), ctypes.c_int, ctypes.c_int, _VP]),
-    ("stencil_batch_set_tuning", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
-    ("stencil_batch_get_tuning", ctypes.c_int, [_VP, _IP, _IP]),
+    ("stencil_batch_set_tuning", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("stencil_batch_get_tuning", ctypes.c_int, [_VP, _IP, _IP, _IP]),
     ("stencil_batch_autotune", ctypes.c_int, [_VP, ctypes.c_int64, _VP, _DP]),
     ("stencil_plan_status", ctypes.c_int, [_VP, _VP]),
     ("stencil_set_tuning", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
@@ -387,13 +387,14 @@ class Batch:
     def run(self, stream=None):
         stencil_batch_run(self.handle, stream)
 
-    def set_tuning(self, cells_per_thread=0, blocks_per_sm=0):
-        _check(lib().stencil_batch_set_tuning(self.handle, int(cells_per_thread), int(blocks_per_sm)))
+    def set_tuning(self, Tb=1, cells_per_thread=0, blocks_per_sm=0):
+        _check(lib().stencil_batch_set_tuning(self.handle, int(Tb), int(cells_per_thread), int(blocks_per_sm)))
 
     def get_tuning(self):
-        c, b = ctypes.c_int(0), ctypes.c_int(0)
-        _check(lib().stencil_batch_get_tuning(self.handle, ctypes.byref(c), ctypes.byref(b)))
-        return c.value, b.value
+        """(Tb, cells per thread, blocks per SM) of the batch's kernel."""
+        t, c, b = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().stencil_batch_get_tuning(self.handle, ctypes.byref(t), ctypes.byref(c), ctypes.byref(b)))
+        return t.value, c.value, b.value
 
     def autotune(self, probe_steps=8, stream=None):
         """Times the kernel configurations on scratch copies of the items and

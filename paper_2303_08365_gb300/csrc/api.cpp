@@ -164,8 +164,15 @@ struct stencil_batch_s {
   cudaStream_t last_stream = nullptr;
   bool use_graph = true;
   // kernel configuration (stencil_batch_set_tuning / stencil_batch_autotune)
-  int cpt = 0;             // cells per thread (1, 2, 4); 0 = the default
-  int per_sm = 0;          // cooperative blocks per SM; 0 = min(occupancy, 4)
+  int Tb = 1;              // 1: one step per device-wide barrier; 2, 4, 8: Tb steps per exchange
+  int cpt = 0;             // cells per thread (1, 2, 4; Tb = 1 only); 0 = the default
+  int per_sm = 0;          // cooperative blocks per SM (Tb = 1 only); 0 = min(occupancy, 4)
+  // Tb > 1: per-item tiles and per-tile flags of the batched temporal kernel
+  BatchTbItemDev* d_tb_items = nullptr;
+  BatchTbTile* d_tb_tiles = nullptr;
+  unsigned int* d_tb_flags = nullptr;
+  int ntb_tiles = 0;
+  int tb_max_blocks = 0;
   std::vector<BatchItemDev> hi;  // the item descriptors, kept to rebuild the tile list
 };
 
@@ -582,6 +589,54 @@ int run_varcoef(stencil_plan_s* p, double* d_grid, int64_t T, const double* d_ka
 // Fills a batch from device item descriptors (buffers and weights set):
 // the T-sorted tile list, the item table, the barrier words and the
 // cooperative grid size.
+// Tb > 1: every item cut into near-equal tiles of at most 16 x 32 cells (the
+// fewest such tiles: least halo recompute), listed item by item in the
+// order of decreasing T, with the reach of a Tb-cell halo in tiles.
+int batch_init_tb(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, const std::vector<int>& order) {
+  const int n = (int)hi.size();
+  const int Tb = b->Tb;
+  std::vector<BatchTbItemDev> items(n);
+  std::vector<BatchTbTile> tiles;
+  b->tb_max_blocks = 0;
+  for (int i : order) {
+    BatchTbItemDev& d = items[i];
+    d.a = hi[i].a;
+    d.b = hi[i].b;
+    d.ny = hi[i].ny;
+    d.nx = hi[i].nx;
+    d.T = hi[i].T;
+    for (int k = 0; k < 5; ++k) d.w[k] = hi[i].w[k];
+    d.zero = 0.0;
+    d.tiles_y = (d.ny + kBatchTbTileH - 1) / kBatchTbTileH;
+    d.tiles_x = (d.nx + kBatchTbTileW - 1) / kBatchTbTileW;
+    const int hmin = d.ny / d.tiles_y, wmin = d.nx / d.tiles_x;
+    d.reach_y = (Tb + hmin - 1) / hmin;
+    d.reach_x = (Tb + wmin - 1) / wmin;
+    d.tile_base = (int)tiles.size();
+    if (d.T == 0) continue;
+    b->tb_max_blocks = std::max(b->tb_max_blocks, (d.T + Tb - 1) / Tb);
+    for (int ty = 0; ty < d.tiles_y; ++ty)
+      for (int tx = 0; tx < d.tiles_x; ++tx) tiles.push_back(BatchTbTile{i, ty, tx});
+  }
+  b->ntb_tiles = (int)tiles.size();
+  CUDA_TRY(dev_malloc(&b->d_tb_items, sizeof(BatchTbItemDev) * (size_t)std::max(n, 1)),
+           "allocating the item table");
+  CUDA_TRY(cudaMemcpy(b->d_tb_items, items.data(), sizeof(BatchTbItemDev) * (size_t)n, cudaMemcpyHostToDevice),
+           "copying the item table");
+  CUDA_TRY(dev_malloc(&b->d_tb_tiles, sizeof(BatchTbTile) * std::max<size_t>(1, tiles.size())),
+           "allocating the tile list");
+  if (!tiles.empty())
+    CUDA_TRY(cudaMemcpy(b->d_tb_tiles, tiles.data(), sizeof(BatchTbTile) * tiles.size(), cudaMemcpyHostToDevice),
+             "copying the tile list");
+  CUDA_TRY(dev_malloc(&b->d_tb_flags, sizeof(unsigned int) * std::max<size_t>(1, tiles.size())),
+           "allocating the tile flags");
+  const int occ = batched_tb_blocks_per_sm(Tb, b->boundary);
+  if (occ < 1) return fail(STENCIL_ERR_CUDA, "the batched temporal kernel does not fit on an SM");
+  b->blocks = sm_count() * std::min(occ, 2);
+  if (b->ntb_tiles > 0 && b->ntb_tiles < b->blocks) b->blocks = b->ntb_tiles;
+  return STENCIL_OK;
+}
+
 int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boundary) {
   const int n = (int)hi.size();
   b->n = n;
@@ -597,6 +652,9 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return hi[a].T > hi[c].T; });
   if (b->cpt == 0) b->cpt = batched_default_cpt();
   b->hi = hi;
+  CUDA_TRY(dev_malloc(&b->d_ctl, 4 * sizeof(unsigned int)), "allocating the barrier words");
+  CUDA_TRY(cudaMemset(b->d_ctl, 0, 4 * sizeof(unsigned int)), "clearing the barrier words");
+  if (b->Tb > 1) return batch_init_tb(b, hi, order);
   std::vector<BatchTile> tiles;
   const int tc = batched_tile_cells(b->cpt);
   for (int i : order) {
@@ -614,8 +672,6 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
   if (!tiles.empty())
     CUDA_TRY(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice),
              "copying the tile list");
-  CUDA_TRY(dev_malloc(&b->d_ctl, 4 * sizeof(unsigned int)), "allocating the barrier words");
-  CUDA_TRY(cudaMemset(b->d_ctl, 0, 4 * sizeof(unsigned int)), "clearing the barrier words");
   const int occ = batched_blocks_per_sm(b->cpt);
   if (occ < 1) return fail(STENCIL_ERR_CUDA, "the batched kernel does not fit on an SM");
   const int per_sm = b->per_sm > 0 ? std::min(b->per_sm, occ) : std::min(occ, 4);
@@ -625,6 +681,22 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
 }
 
 int batch_enqueue(stencil_batch_s* b, cudaStream_t s) {
+  if (b->Tb > 1) {
+    if (b->ntb_tiles == 0) return STENCIL_OK;  // every item has T = 0
+    BatchTbLaunch L;
+    L.items = b->d_tb_items;
+    L.tiles = b->d_tb_tiles;
+    L.ntiles = b->ntb_tiles;
+    L.max_blocks = b->tb_max_blocks;
+    L.flags = b->d_tb_flags;
+    L.status = (int*)(b->d_ctl + 2);
+    L.spin_limit = kSpinLimitNs;
+    CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 4 * sizeof(unsigned int), s), "clearing the status word");
+    CUDA_TRY(cudaMemsetAsync(b->d_tb_flags, 0, sizeof(unsigned int) * b->ntb_tiles, s), "clearing the tile flags");
+    cudaError_t e = launch_batched_tb(L, b->blocks, b->Tb, b->boundary, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the batched temporal kernel");
+    return STENCIL_OK;
+  }
   BatchLaunch L;
   L.items = b->d_items;
   L.tiles = b->d_tiles;
@@ -1127,9 +1199,16 @@ void batch_release_lists(stencil_batch_s* b) {
   cudaFree(b->d_items);
   cudaFree(b->d_tiles);
   cudaFree(b->d_ctl);
+  cudaFree(b->d_tb_items);
+  cudaFree(b->d_tb_tiles);
+  cudaFree(b->d_tb_flags);
   b->d_items = nullptr;
   b->d_tiles = nullptr;
   b->d_ctl = nullptr;
+  b->d_tb_items = nullptr;
+  b->d_tb_tiles = nullptr;
+  b->d_tb_flags = nullptr;
+  b->ntiles = b->ntb_tiles = 0;
 }
 
 // Rebuilds the tile list for the batch's current kernel configuration.
@@ -1143,22 +1222,25 @@ int batch_rebuild(stencil_batch_s* b) {
 
 extern "C" {
 
-int stencil_batch_set_tuning(stencil_batch b, int cells_per_thread, int blocks_per_sm) {
+int stencil_batch_set_tuning(stencil_batch b, int Tb, int cells_per_thread, int blocks_per_sm) {
   g_err.clear();
   if (!b) return fail(STENCIL_ERR_ARG, "batch is NULL");
+  if (Tb != 0 && Tb != 1 && Tb != 2 && Tb != 4 && Tb != 8) return fail(STENCIL_ERR_ARG, "Tb must be 0, 1, 2, 4 or 8");
   if (cells_per_thread != 0 && cells_per_thread != 1 && cells_per_thread != 2 && cells_per_thread != 4)
     return fail(STENCIL_ERR_ARG, "cells_per_thread must be 0, 1, 2 or 4");
   if (blocks_per_sm < 0 || blocks_per_sm > 32) return fail(STENCIL_ERR_ARG, "blocks_per_sm must be in [0, 32]");
+  b->Tb = Tb == 0 ? 1 : Tb;
   b->cpt = cells_per_thread;
   b->per_sm = blocks_per_sm;
   return batch_rebuild(b);
 }
 
-int stencil_batch_get_tuning(stencil_batch b, int* cells_per_thread, int* blocks_per_sm) {
+int stencil_batch_get_tuning(stencil_batch b, int* Tb, int* cells_per_thread, int* blocks_per_sm) {
   g_err.clear();
-  if (!b || !cells_per_thread || !blocks_per_sm) return fail(STENCIL_ERR_ARG, "NULL argument");
-  *cells_per_thread = b->cpt;
-  *blocks_per_sm = b->blocks / std::max(1, sm_count());
+  if (!b || !Tb || !cells_per_thread || !blocks_per_sm) return fail(STENCIL_ERR_ARG, "NULL argument");
+  *Tb = b->Tb;
+  *cells_per_thread = b->Tb > 1 ? 0 : b->cpt;
+  *blocks_per_sm = (b->blocks + sm_count() - 1) / std::max(1, sm_count());
   return STENCIL_OK;
 }
 
@@ -1198,47 +1280,53 @@ int stencil_batch_autotune(stencil_batch b, int64_t probe_steps, void* cuda_stre
   if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
     rc = fail(STENCIL_ERR_CUDA, "creating events");
   double best = -1.0;
-  int best_cpt = batched_default_cpt(), best_per_sm = 0;
-  for (int cpt : {1, 2, 4}) {
-    const int occ = batched_blocks_per_sm(cpt);
-    for (int per_sm = 1; !rc && per_sm <= std::min(occ, 4); ++per_sm) {
-      auto* t = new (std::nothrow) stencil_batch_s();
-      if (!t) {
-        rc = fail(STENCIL_ERR_OOM, "allocating a probe batch");
-        break;
-      }
-      t->cpt = cpt;
-      t->per_sm = per_sm;
-      rc = batch_init(t, probe, b->boundary);
-      if (!rc) rc = batch_enqueue(t, s);  // warm-up
-      float best_ms = -1.f;               // the faster of two timed runs
-      for (int rep = 0; rep < 2 && !rc; ++rep) {
-        cudaEventRecord(e0, s);
-        rc = batch_enqueue(t, s);
-        cudaEventRecord(e1, s);
-        if (rc) break;
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (best_ms < 0.f || ms < best_ms) best_ms = ms;
-      }
-      if (!rc) {
-        const double rate = (double)updates / (std::max(best_ms, 1e-3f) * 1e-3) / 1e9;
-        if (rate > best) {
-          best = rate;
-          best_cpt = cpt;
-          best_per_sm = per_sm;
-        }
-      }
-      t->d_partner = nullptr;  // scratch, freed below
-      stencil_batch_destroy(t);
+  int best_Tb = 1, best_cpt = batched_default_cpt(), best_per_sm = 0;
+  struct Cand { int Tb, cpt, per_sm; };
+  std::vector<Cand> cands;
+  for (int cpt : {1, 2, 4})
+    for (int per_sm = 1; per_sm <= std::min(batched_blocks_per_sm(cpt), 4); ++per_sm) cands.push_back({1, cpt, per_sm});
+  for (int Tb : {2, 4, 8}) cands.push_back({Tb, 0, 0});
+  for (const Cand& cd : cands) {
+    if (rc) break;
+    auto* t = new (std::nothrow) stencil_batch_s();
+    if (!t) {
+      rc = fail(STENCIL_ERR_OOM, "allocating a probe batch");
+      break;
     }
+    t->Tb = cd.Tb;
+    t->cpt = cd.cpt;
+    t->per_sm = cd.per_sm;
+    rc = batch_init(t, probe, b->boundary);
+    if (!rc) rc = batch_enqueue(t, s);  // warm-up
+    float best_ms = -1.f;               // the fastest of three timed runs
+    for (int rep = 0; rep < 3 && !rc; ++rep) {
+      cudaEventRecord(e0, s);
+      rc = batch_enqueue(t, s);
+      cudaEventRecord(e1, s);
+      if (rc) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best_ms < 0.f || ms < best_ms) best_ms = ms;
+    }
+    if (!rc) {
+      const double rate = (double)updates / (std::max(best_ms, 1e-3f) * 1e-3) / 1e9;
+      if (rate > best) {
+        best = rate;
+        best_Tb = cd.Tb;
+        best_cpt = cd.cpt;
+        best_per_sm = cd.per_sm;
+      }
+    }
+    t->d_partner = nullptr;  // scratch, freed below
+    stencil_batch_destroy(t);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(scratch);
   if (rc) return rc;
   if (best < 0) return fail(STENCIL_ERR_CUDA, "no batch configuration ran");
+  b->Tb = best_Tb;
   b->cpt = best_cpt;
   b->per_sm = best_per_sm;
   rc = batch_rebuild(b);
@@ -1256,6 +1344,9 @@ void stencil_batch_destroy(stencil_batch b) {
   cudaFree(b->d_tiles);
   cudaFree(b->d_partner);
   cudaFree(b->d_ctl);
+  cudaFree(b->d_tb_items);
+  cudaFree(b->d_tb_tiles);
+  cudaFree(b->d_tb_flags);
   delete b;
 }
 

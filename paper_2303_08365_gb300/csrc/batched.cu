@@ -184,21 +184,23 @@ __device__ __forceinline__ double ptb_cell(const RegWeights<NT>& W, const double
 // published at least `target` finished blocks.  The wait is bounded by wall
 // time and gives up at once when another CTA has reported an error; returns
 // false (for every thread of the CTA) when it gave up.
+// (flags: the grid's tiles_y x tiles_x flag words, row-major.)
 template <bool PERIODIC>
-__device__ bool wait_reach(const PersistTbLaunch& L, int ty, int tx, unsigned int target) {
-  const int wy = 2 * L.reach_y + 1, wx = 2 * L.reach_x + 1;
+__device__ bool wait_tiles(const unsigned int* flags, int tiles_y, int tiles_x, int reach_y, int reach_x,
+                           int ty, int tx, unsigned int target, int* status, long long spin_limit) {
+  const int wy = 2 * reach_y + 1, wx = 2 * reach_x + 1;
   int ok = 1;
   for (int i = threadIdx.x; i < wy * wx; i += blockDim.x) {
-    int yy = ty + i / wx - L.reach_y, xx = tx + i % wx - L.reach_x;
+    int yy = ty + i / wx - reach_y, xx = tx + i % wx - reach_x;
     if (PERIODIC) {
-      yy %= L.tiles_y;
-      yy += yy < 0 ? L.tiles_y : 0;
-      xx %= L.tiles_x;
-      xx += xx < 0 ? L.tiles_x : 0;
-    } else if ((unsigned)yy >= (unsigned)L.tiles_y || (unsigned)xx >= (unsigned)L.tiles_x) {
+      yy %= tiles_y;
+      yy += yy < 0 ? tiles_y : 0;
+      xx %= tiles_x;
+      xx += xx < 0 ? tiles_x : 0;
+    } else if ((unsigned)yy >= (unsigned)tiles_y || (unsigned)xx >= (unsigned)tiles_x) {
       continue;
     }
-    const unsigned int* f = L.flags + yy * L.tiles_x + xx;
+    const unsigned int* f = flags + yy * tiles_x + xx;
     unsigned int v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
     if (v >= target) continue;
@@ -207,12 +209,12 @@ __device__ bool wait_reach(const PersistTbLaunch& L, int ty, int tx, unsigned in
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
       if (v >= target) break;
       if ((spin & 31) == 31) {
-        if (*(volatile int*)L.status != 0) {
+        if (*(volatile int*)status != 0) {
           ok = 0;
           break;
         }
-        if ((long long)(global_ns() - t0) > L.spin_limit) {
-          atomicCAS(L.status, 0, (int)-5 /* STENCIL_ERR_TIMEOUT */);
+        if ((long long)(global_ns() - t0) > spin_limit) {
+          atomicCAS(status, 0, (int)-5 /* STENCIL_ERR_TIMEOUT */);
           ok = 0;
           break;
         }
@@ -221,6 +223,12 @@ __device__ bool wait_reach(const PersistTbLaunch& L, int ty, int tx, unsigned in
     if (!ok) break;
   }
   return __syncthreads_and(ok) != 0;
+}
+
+template <bool PERIODIC>
+__device__ bool wait_reach(const PersistTbLaunch& L, int ty, int tx, unsigned int target) {
+  return wait_tiles<PERIODIC>(L.flags, L.tiles_y, L.tiles_x, L.reach_y, L.reach_x, ty, tx, target, L.status,
+                              L.spin_limit);
 }
 
 // Rows [y0, y1) of tile row ty when ny rows are cut into `tiles` near-equal parts.
@@ -342,6 +350,136 @@ __global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched temporal blocking: the persistent temporal kernel over the tiles of
+// many 2D 5-point grids at once (each grid its own weights and T).  A tile of
+// an item whose blocks are done sits out; a tile waits only on the tiles of
+// its own item that its halo reaches, so items never wait on each other.
+static_assert(kBatchTbTileH == kPTH && kBatchTbTileW == kPTW, "tile bounds of the batched temporal kernel");
+
+template <bool PERIODIC, int TB>
+__global__ void __launch_bounds__(kPThreads, 2) k_batched_tb(BatchTbLaunch L) {
+  constexpr int RW = kPTW + 2 * TB;
+  constexpr int RH = kPTH + 2 * TB;
+  __shared__ double buf[2][RH * RW];
+  const int G = gridDim.x;
+  for (int blk = 0; blk < L.max_blocks; ++blk) {
+    for (int j = blockIdx.x; j < L.ntiles; j += G) {
+      const BatchTbTile tl = L.tiles[j];
+      const BatchTbItemDev& it = L.items[tl.item];
+      const int ny = it.ny, nx = it.nx, T = it.T;
+      if (blk >= (T + TB - 1) / TB) continue;  // this item is done
+      const int tb = T - blk * TB < TB ? T - blk * TB : TB;
+      const double* src = (blk & 1) ? it.b : it.a;
+      double* dst = (blk & 1) ? it.a : it.b;
+      const int ty = tl.ty, tx = tl.tx;
+      const int y0 = cut(ty, ny, it.tiles_y), x0 = cut(tx, nx, it.tiles_x);
+      const int th = cut(ty + 1, ny, it.tiles_y) - y0, tw = cut(tx + 1, nx, it.tiles_x) - x0;
+      unsigned int* flags = L.flags + it.tile_base;
+      if (blk > 0 && !wait_tiles<PERIODIC>(flags, it.tiles_y, it.tiles_x, it.reach_y, it.reach_x, ty, tx,
+                                           (unsigned int)blk, L.status, L.spin_limit))
+        return;
+      const double w0 = it.w[0], w1 = it.w[1], w2 = it.w[2], w3 = it.w[3], w4 = it.w[4], zero = it.zero;
+      // the tile with a halo of tb cells (region offset TB - tb inside the buffer)
+      const int off = TB - tb;
+      const int lh = th + 2 * tb, lw = tw + 2 * tb;
+      FlatWalk lwk(threadIdx.x, kPThreads, lw);
+      for (int c = threadIdx.x; c < lh * lw; c += kPThreads, lwk.next()) {
+        int y = y0 - tb + lwk.r, x = x0 - tb + lwk.c;
+        double v = 0.0;
+        if (PERIODIC) {
+          y = wrap_into(y, ny);
+          x = wrap_into(x, nx);
+          v = __ldcg(src + (int64_t)y * nx + x);
+        } else if ((unsigned)y < (unsigned)ny && (unsigned)x < (unsigned)nx) {
+          v = __ldcg(src + (int64_t)y * nx + x);
+        }
+        buf[0][(off + lwk.r) * RW + off + lwk.c] = v;
+      }
+      __syncthreads();
+      int cur = 0;
+      for (int s = 1; s <= tb; ++s) {
+        const int m = tb - s;
+        const int h = th + 2 * m, w = tw + 2 * m;
+        const double* in = buf[cur];
+        double* out = buf[cur ^ 1];
+        FlatWalk wk(threadIdx.x, kPThreads, w);
+        for (int c = threadIdx.x; c < h * w; c += kPThreads, wk.next()) {
+          const int ry = TB - m + wk.r, rx = TB - m + wk.c;
+          const int y = y0 - TB + ry, x = x0 - TB + rx;
+          double acc = 0.0;  // Dirichlet ghosts stay zero at every time level
+          if (PERIODIC || ((unsigned)y < (unsigned)ny && (unsigned)x < (unsigned)nx)) {
+            const double* p = in + ry * RW + rx;
+            acc = fma(w0, p[-RW], zero);  // north
+            acc = fma(w1, p[-1], acc);    // west
+            acc = fma(w2, p[0], acc);     // centre
+            acc = fma(w3, p[1], acc);     // east
+            acc = fma(w4, p[RW], acc);    // south
+          }
+          out[ry * RW + rx] = acc;
+        }
+        __syncthreads();
+        cur ^= 1;
+      }
+      FlatWalk swk(threadIdx.x, kPThreads, tw);
+      for (int c = threadIdx.x; c < th * tw; c += kPThreads, swk.next())
+        dst[(int64_t)(y0 + swk.r) * nx + x0 + swk.c] = buf[cur][(TB + swk.r) * RW + TB + swk.c];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(L.flags + j), "r"((unsigned int)(blk + 1))
+                     : "memory");
+      }
+    }
+  }
+  // items with an odd number of blocks hold their result in the partner
+  // buffer: copy each tile back once the tiles that read it are done
+  for (int j = blockIdx.x; j < L.ntiles; j += G) {
+    const BatchTbTile tl = L.tiles[j];
+    const BatchTbItemDev& it = L.items[tl.item];
+    const int nblk = (it.T + TB - 1) / TB;
+    if ((nblk & 1) == 0) continue;
+    const int ty = tl.ty, tx = tl.tx;
+    const int y0 = cut(ty, it.ny, it.tiles_y), x0 = cut(tx, it.nx, it.tiles_x);
+    const int th = cut(ty + 1, it.ny, it.tiles_y) - y0, tw = cut(tx + 1, it.nx, it.tiles_x) - x0;
+    if (!wait_tiles<PERIODIC>(L.flags + it.tile_base, it.tiles_y, it.tiles_x, it.reach_y, it.reach_x, ty, tx,
+                              (unsigned int)nblk, L.status, L.spin_limit))
+      return;
+    for (int c = threadIdx.x; c < th * tw; c += kPThreads) {
+      const int64_t k = (int64_t)(y0 + c / tw) * it.nx + x0 + c % tw;
+      it.a[k] = __ldcg(it.b + k);
+    }
+  }
+}
+
+template <bool PERIODIC, int TB>
+cudaError_t launch_btb(const BatchTbLaunch& L, int grid_blocks, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_blocks, 1, 1);
+  cfg.blockDim = dim3(kPThreads, 1, 1);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_batched_tb<PERIODIC, TB>, L);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+template <bool PERIODIC, int TB>
+int btb_occupancy() {
+  static std::atomic<int> cache[kMaxDeviceOrdinals];
+  return cached_per_device(cache, [] {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched_tb<PERIODIC, TB>, kPThreads, 0) !=
+        cudaSuccess)
+      n = 0;
+    return n;
+  });
+}
+
 template <int NT, bool BOX, bool PERIODIC, int TB>
 cudaError_t launch_ptb(const PersistTbLaunch& L, int sms, cudaStream_t stream) {
   auto kern = k_persist_tb<NT, BOX, PERIODIC, TB>;
@@ -415,6 +553,27 @@ cudaError_t launch_persist_tb(Shape shape, int boundary, int Tb, const PersistTb
   if (shape == Shape::kBox)
     return per ? ptb_by_tb<9, true, true>(Tb, L, sms, stream) : ptb_by_tb<9, true, false>(Tb, L, sms, stream);
   return per ? ptb_by_tb<5, false, true>(Tb, L, sms, stream) : ptb_by_tb<5, false, false>(Tb, L, sms, stream);
+}
+
+cudaError_t launch_batched_tb(const BatchTbLaunch& L, int grid_blocks, int Tb, int boundary,
+                              cudaStream_t stream) {
+  const bool per = boundary == kPeriodic;
+  switch (Tb) {
+    case 2: return per ? launch_btb<true, 2>(L, grid_blocks, stream) : launch_btb<false, 2>(L, grid_blocks, stream);
+    case 4: return per ? launch_btb<true, 4>(L, grid_blocks, stream) : launch_btb<false, 4>(L, grid_blocks, stream);
+    case 8: return per ? launch_btb<true, 8>(L, grid_blocks, stream) : launch_btb<false, 8>(L, grid_blocks, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int batched_tb_blocks_per_sm(int Tb, int boundary) {
+  const bool per = boundary == kPeriodic;
+  switch (Tb) {
+    case 2: return per ? btb_occupancy<true, 2>() : btb_occupancy<false, 2>();
+    case 4: return per ? btb_occupancy<true, 4>() : btb_occupancy<false, 4>();
+    case 8: return per ? btb_occupancy<true, 8>() : btb_occupancy<false, 8>();
+    default: return 0;
+  }
 }
 
 int batched_block_size() { return kThreads; }

@@ -178,6 +178,37 @@ struct PersistTbLaunch {
   int* status;
   long long spin_limit;  // ns
 };
+// Batched temporal blocking: many 2D 5-point heat grids advanced Tb steps in
+// shared memory per exchange, one launch, tiles synchronised by per-tile
+// flags (each item cut into tiles of at most 16 x 32 cells).
+struct BatchTbItemDev {
+  double* a;              // the caller's grid
+  double* b;              // partner buffer
+  int ny, nx, T;
+  int tiles_y, tiles_x;   // near-equal cut of the item
+  int reach_y, reach_x;   // tiles a Tb-cell halo can reach on each side
+  int tile_base;          // the item's first tile (its flag words start there)
+  double w[5];            // north, west, centre, east, south (lexicographic taps)
+  double zero;            // 0.0, the addend of each chain's first FMA
+};
+struct BatchTbTile {
+  int item, ty, tx;       // tile (ty, tx) of item `item`
+};
+struct BatchTbLaunch {
+  const BatchTbItemDev* items;
+  const BatchTbTile* tiles;
+  int ntiles;
+  int max_blocks;         // the largest ceil(T / Tb) over the items
+  unsigned int* flags;    // ntiles words, zero before the launch
+  int* status;
+  long long spin_limit;   // ns
+};
+cudaError_t launch_batched_tb(const BatchTbLaunch& L, int grid_blocks, int Tb, int boundary,
+                              cudaStream_t stream);
+int batched_tb_blocks_per_sm(int Tb, int boundary);
+// Largest tile of the batched temporal kernel.
+constexpr int kBatchTbTileH = 16, kBatchTbTileW = 32;
+
 // Picks the cut of an ny x nx grid into tiles of at most 16 x 32 cells that
 // minimises the FP64 work of the busiest SM for Tb steps per block, and the
 // reach of a Tb-cell halo in tiles.

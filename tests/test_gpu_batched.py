@@ -135,21 +135,50 @@ def test_autotuner_leaves_grids_alone_and_every_configuration_agrees(st):
     assert rate > 0
     for g0, d in zip(grids, dev):
         assert np.array_equal(d.cpu().numpy(), g0)      # untouched by the probes
-    cpt, per_sm = b.get_tuning()
-    assert cpt in (1, 2, 4) and per_sm >= 1
+    tb, cpt, per_sm = b.get_tuning()
+    assert tb in (1, 2, 4, 8) and per_sm >= 1 and (cpt in (1, 2, 4) if tb == 1 else cpt == 0)
     b.run()
     assert b.status() == 0
     for d, r in zip(dev, refs):
         assert np.array_equal(d.cpu().numpy(), r)
-    for cpt in (1, 2, 4):
-        for per_sm in (1, 3):
-            for g0, d in zip(grids, dev):
-                d.copy_(torch.from_numpy(g0))
-            b.set_tuning(cpt, per_sm)
-            b.run()
-            assert b.status() == 0
-            for d, r in zip(dev, refs):
-                assert np.array_equal(d.cpu().numpy(), r), (cpt, per_sm)
+    configs = [(1, cpt, per_sm) for cpt in (1, 2, 4) for per_sm in (1, 3)] + [(2, 0, 0), (4, 0, 0), (8, 0, 0)]
+    for tb, cpt, per_sm in configs:
+        for g0, d in zip(grids, dev):
+            d.copy_(torch.from_numpy(g0))
+        b.set_tuning(tb, cpt, per_sm)
+        assert b.get_tuning()[0] == tb
+        b.run()
+        assert b.status() == 0
+        for d, r in zip(dev, refs):
+            assert np.array_equal(d.cpu().numpy(), r), (tb, cpt, per_sm)
     with pytest.raises(st.StencilError):
-        b.set_tuning(3, 0)
+        b.set_tuning(1, 3, 0)
+    with pytest.raises(st.StencilError):
+        b.set_tuning(3, 0, 0)
+    b.close()
+
+
+@pytest.mark.parametrize("boundary", [DIRICHLET, PERIODIC])
+@pytest.mark.parametrize("Tb", [2, 4, 8])
+def test_batched_temporal_blocking_matches_single_grids(st, boundary, Tb):
+    """Tb steps per exchange over many grids at once (each grid its own alpha
+    and T, odd block counts, T = 0, a single cell, grids smaller than the
+    halo): bitwise equal to single-grid runs and within 1e-12 of the oracle."""
+    import torch
+    items = [(37, 91, 0.11, 13), (128, 64, 0.2, 6), (5, 3, 0.05, 9), (200, 130, 0.24, 0), (1, 1, 0.1, 4),
+             (70, 250, 0.15, 21), (16, 32, 0.19, 8), (33, 2, 0.07, 17)]
+    grids = [synth.uniform(110 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
+    dev = [torch.from_numpy(g.copy()).cuda() for g in grids]
+    b = st.Batch(dev, [x[2] for x in items], [x[3] for x in items], boundary)
+    b.set_tuning(Tb)
+    b.run()
+    assert b.status() == 0
+    for g0, d, (ny, nx, a, T) in zip(grids, dev, items):
+        got = d.cpu().numpy()
+        assert np.array_equal(got, single(st, g0, a, T, boundary)), (ny, nx, T)
+        assert normwise_rel(got, oracle.run(g0, synth.heat_weights(2, a), 1, boundary, T)) <= TOL
+    b.run()                                  # replay: T more steps each
+    assert b.status() == 0
+    for g0, d, (ny, nx, a, T) in zip(grids, dev, items):
+        assert np.array_equal(d.cpu().numpy(), single(st, g0, a, 2 * T, boundary)), (ny, nx, T)
     b.close()

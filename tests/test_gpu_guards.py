@@ -110,11 +110,13 @@ def test_sweep_writes_stay_inside_the_grid(st, shape, radius, kind, boundary, Tb
     p.close()
 
 
-def test_batched_writes_stay_inside_each_grid(st):
+@pytest.mark.parametrize("Tb", [1, 4])
+def test_batched_writes_stay_inside_each_grid(st, Tb):
     items = [(37, 91, 0.11, 13), (128, 64, 0.2, 6), (5, 3, 0.05, 9), (1, 1, 0.1, 4), (70, 250, 0.15, 21)]
     grids = [synth.uniform(60 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
     gs = [Guarded(x) for x in grids]
     b = st.Batch([g.view for g in gs], [a for _, _, a, _ in items], [T for *_, T in items])
+    b.set_tuning(Tb)
     b.run()
     assert b.status() == 0
     for x, g, (_, _, a, T) in zip(grids, gs, items):
