@@ -410,7 +410,7 @@ def form_batched(st, stream, peak, rank=0, world=1):
     b = st.Batch(dev, alphas, steps)
     # the batch autotuner picks the kernel configuration (on scratch copies)
     tuned_rate = b.autotune(probe_steps=50, stream=stream)
-    cpt, per_sm = b.get_tuning()
+    tb, cpt, per_sm = b.get_tuning()
     b.run(stream)
     assert b.status() == 0
     l0 = st.stencil_launch_count()
@@ -437,7 +437,7 @@ def form_batched(st, stream, peak, rank=0, world=1):
     return {"workload": f"batched 96 x heat2d-5pt, sides log-uniform [128,4096], T in [50,500], "
                         f"{updates:.3e} updates" + (f", sharded over {world} ranks" if world > 1 else ""),
             "gstencil_per_s": round(rate, 3), "ms": round(ms, 3), "launches": launches,
-            "autotuned": {"cells_per_thread": cpt, "blocks_per_sm": per_sm,
+            "autotuned": {"Tb": tb, "cells_per_thread": cpt, "blocks_per_sm": per_sm,
                           "probe_gstencil_per_s": round(tuned_rate, 3)},
             "plain_sweep_ms": round(ms_plain, 3),
             "plain_sweep_gstencil_per_s": round(updates / (ms_plain * 1e-3) / 1e9, 3),
