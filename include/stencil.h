@@ -303,6 +303,14 @@ int64_t stencil_launch_count(void);
  * bytes of device memory. */
 int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream);
 
+/* The same for the tile-flag waits of the temporal persistent kernels:
+ * launches the batched temporal kernel on a 32 x 64 grid cut into 2 x 2
+ * tiles with one tile left out of the work list, so the flag that tile would
+ * set is never set and its neighbours' waits can only end by their
+ * wall-time limit.  Returns STENCIL_ERR_TIMEOUT when they gave up as
+ * designed. */
+int stencil_selftest_flag_timeout(double limit_ms, void* cuda_stream);
+
 /* Host-side fault injection for tests: after `after` more device allocations
  * by this library succeed, every later one fails as if the device were out
  * of memory, without calling the driver, until the injection is turned off

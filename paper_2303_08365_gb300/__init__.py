@@ -77,6 +77,7 @@ SIGNATURES = [
     ("stencil_fp64_peak", ctypes.c_int, [ctypes.c_double, _DP, _VP]),
     ("stencil_selftest_barrier_timeout", ctypes.c_int, [ctypes.c_double, _VP]),
     ("stencil_debug_fail_allocations", None, [ctypes.c_int]),
+    ("stencil_selftest_flag_timeout", ctypes.c_int, [ctypes.c_double, _VP]),
     ("stencil_run_2d_static", ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _DP, ctypes.c_int, _VP,
                                              ctypes.c_int64, _VP]),
 ]
@@ -292,6 +293,12 @@ def stencil_run_2d_static(grid, weights, boundary, T, stream=None):
         raise ValueError("weights must be a dense 3x3 array")
     _check(lib().stencil_run_2d_static(int(grid.shape[0]), int(grid.shape[1]), w.ctypes.data_as(_DP),
                                        int(boundary), _dev_ptr(grid, "grid"), int(T), _stream(stream)))
+
+
+def stencil_selftest_flag_timeout(limit_ms=20.0, stream=None):
+    """Runs the tile-flag wait's failure path on the GPU; returns the status
+    code (ERR_TIMEOUT when it behaved)."""
+    return lib().stencil_selftest_flag_timeout(float(limit_ms), _stream(stream))
 
 
 def stencil_debug_fail_allocations(after):

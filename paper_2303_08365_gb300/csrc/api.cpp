@@ -1423,6 +1423,75 @@ int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream) {
   return st;
 }
 
+int stencil_selftest_flag_timeout(double limit_ms, void* cuda_stream) {
+  g_err.clear();
+  if (!(limit_ms > 0.0) || limit_ms > 2000.0) return fail(STENCIL_ERR_ARG, "limit_ms must be in (0, 2000]");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // one 32 x 64 grid cut into 2 x 2 tiles of the batched temporal kernel
+  // (Tb = 2, T = 4), launched with only three of the four tiles: the fourth
+  // tile's flag is never set, so the second block's waits can only end by
+  // their wall-time limit
+  double* grid = nullptr;
+  unsigned int* ctl = nullptr;
+  unsigned int* flags = nullptr;
+  BatchTbItemDev* d_item = nullptr;
+  BatchTbTile* d_tiles = nullptr;
+  int rc = STENCIL_OK;
+  auto cleanup = [&]() {
+    cudaFree(grid);
+    cudaFree(ctl);
+    cudaFree(flags);
+    cudaFree(d_item);
+    cudaFree(d_tiles);
+  };
+  const int ny = 32, nx = 64, n = ny * nx;
+  if (dev_malloc(&grid, 2 * n * sizeof(double)) != cudaSuccess ||
+      dev_malloc(&ctl, 4 * sizeof(unsigned int)) != cudaSuccess ||
+      dev_malloc(&flags, 4 * sizeof(unsigned int)) != cudaSuccess ||
+      dev_malloc(&d_item, sizeof(BatchTbItemDev)) != cudaSuccess ||
+      dev_malloc(&d_tiles, 3 * sizeof(BatchTbTile)) != cudaSuccess) {
+    cleanup();
+    return fail(STENCIL_ERR_OOM, "allocating the self-test buffers");
+  }
+  BatchTbItemDev it{};
+  it.a = grid;
+  it.b = grid + n;
+  it.ny = ny;
+  it.nx = nx;
+  it.T = 4;
+  it.tiles_y = 2;
+  it.tiles_x = 2;
+  it.reach_y = 1;
+  it.reach_x = 1;
+  it.tile_base = 0;
+  it.w[2] = 1.0;
+  it.zero = 0.0;
+  const BatchTbTile tl[3] = {{0, 0, 0}, {0, 0, 1}, {0, 1, 0}};  // tile (1, 1) left out
+  cudaMemsetAsync(grid, 0, 2 * n * sizeof(double), s);
+  cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned int), s);
+  cudaMemsetAsync(flags, 0, 4 * sizeof(unsigned int), s);
+  cudaMemcpyAsync(d_item, &it, sizeof(it), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(d_tiles, tl, sizeof(tl), cudaMemcpyHostToDevice, s);
+  BatchTbLaunch L;
+  L.items = d_item;
+  L.tiles = d_tiles;
+  L.ntiles = 3;
+  L.max_blocks = 2;
+  L.flags = flags;
+  L.status = reinterpret_cast<int*>(ctl + 2);
+  L.spin_limit = (long long)(limit_ms * 1e6);
+  cudaError_t e = launch_batched_tb(L, 3, 2, STENCIL_DIRICHLET_ZERO, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, ctl + 2, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) rc = cuda_fail(e, "running the self-test");
+  cleanup();
+  if (rc) return rc;
+  if (st != STENCIL_ERR_TIMEOUT)
+    return fail(STENCIL_ERR_CUDA, "the bounded wait did not report a timeout (status %d)", st);
+  return st;
+}
+
 // ------------------------------------------------------------ measurement
 
 int stencil_fp64_peak(double millis, double* dfma_per_s, void* cuda_stream) {

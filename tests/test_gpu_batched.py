@@ -182,3 +182,20 @@ def test_batched_temporal_blocking_matches_single_grids(st, boundary, Tb):
     for g0, d, (ny, nx, a, T) in zip(grids, dev, items):
         assert np.array_equal(d.cpu().numpy(), single(st, g0, a, 2 * T, boundary)), (ny, nx, T)
     b.close()
+
+
+def test_tile_flag_wait_reports_timeout_and_context_survives(st):
+    """Failure detection without a GPU fault, for the tile-flag waits: a flag
+    that nothing sets makes the neighbouring tiles give up after their 20 ms
+    limit with STENCIL_ERR_TIMEOUT, and the next batch runs normally."""
+    import torch
+    assert st.stencil_selftest_flag_timeout(20.0) == st.ERR_TIMEOUT
+    g0 = synth.uniform(32, (40, 70))
+    d = torch.from_numpy(g0.copy()).cuda()
+    b = st.Batch([d], [0.1], [9])
+    b.set_tuning(4)
+    b.run()
+    assert b.status() == 0
+    ref = oracle.run(g0, synth.heat_weights(2, 0.1), 1, DIRICHLET, 9)
+    assert normwise_rel(d.cpu().numpy(), ref) <= TOL
+    b.close()
