@@ -79,6 +79,23 @@ def test_constant_weight_run_reports_oom_and_recovers(st, shape, radius, w_kind,
     p2.close()
 
 
+def test_batch_retuning_reports_oom_and_recovers(st):
+    """Switching a batch to Tb = 4 rebuilds its work list; allocation failures
+    there are reported, and a later successful switch runs correctly."""
+    import torch
+    grids = [synth.uniform(42, (40, 70)), synth.uniform(43, (33, 20))]
+    alphas, Ts = [0.1, 0.2], [9, 4]
+    dev = [torch.from_numpy(x.copy()).cuda() for x in grids]
+    b = st.Batch(dev, alphas, Ts)
+    first_success(st, lambda: b.set_tuning(4))
+    assert b.get_tuning()[0] == 4
+    b.run()
+    assert b.status() == 0
+    for x, d, a, T in zip(grids, dev, alphas, Ts):
+        assert normwise_rel(d.cpu().numpy(), oracle.run(x, synth.heat_weights(2, a), 1, DIRICHLET, T)) <= TOL
+    b.close()
+
+
 def test_batch_create_reports_oom_and_a_new_batch_runs(st):
     import torch
     grids = [synth.uniform(40, (40, 70)), synth.uniform(41, (33, 20))]
