@@ -174,6 +174,7 @@ struct stencil_batch_s {
   int ntb_tiles = 0;
   int tb_max_blocks = 0;
   std::vector<BatchItemDev> hi;  // the item descriptors, kept to rebuild the tile list
+  bool ready = false;      // the work list is complete (the last build succeeded)
 };
 
 namespace {
@@ -618,7 +619,7 @@ int batch_init_tb(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, const
     for (int ty = 0; ty < d.tiles_y; ++ty)
       for (int tx = 0; tx < d.tiles_x; ++tx) tiles.push_back(BatchTbTile{i, ty, tx});
   }
-  b->ntb_tiles = (int)tiles.size();
+  b->ntb_tiles = 0;  // set once every list below exists
   CUDA_TRY(dev_malloc(&b->d_tb_items, sizeof(BatchTbItemDev) * (size_t)std::max(n, 1)),
            "allocating the item table");
   CUDA_TRY(cudaMemcpy(b->d_tb_items, items.data(), sizeof(BatchTbItemDev) * (size_t)n, cudaMemcpyHostToDevice),
@@ -632,12 +633,15 @@ int batch_init_tb(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, const
            "allocating the tile flags");
   const int occ = batched_tb_blocks_per_sm(Tb, b->boundary);
   if (occ < 1) return fail(STENCIL_ERR_CUDA, "the batched temporal kernel does not fit on an SM");
+  b->ntb_tiles = (int)tiles.size();
   b->blocks = sm_count() * std::min(occ, 2);
   if (b->ntb_tiles > 0 && b->ntb_tiles < b->blocks) b->blocks = b->ntb_tiles;
+  b->ready = true;
   return STENCIL_OK;
 }
 
 int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boundary) {
+  b->ready = false;
   const int n = (int)hi.size();
   b->n = n;
   b->boundary = boundary;
@@ -663,7 +667,7 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
     for (int64_t k0 = 0; k0 < cells; k0 += tc)
       tiles.push_back(BatchTile{i, (int)k0, (int)std::min<int64_t>(tc, cells - k0)});
   }
-  b->ntiles = (int)tiles.size();
+  b->ntiles = 0;  // set once every list below exists
   CUDA_TRY(dev_malloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n), "allocating the item table");
   CUDA_TRY(cudaMemcpy(b->d_items, hi.data(), sizeof(BatchItemDev) * (size_t)n, cudaMemcpyHostToDevice),
            "copying the item table");
@@ -674,13 +678,17 @@ int batch_init(stencil_batch_s* b, const std::vector<BatchItemDev>& hi, int boun
              "copying the tile list");
   const int occ = batched_blocks_per_sm(b->cpt);
   if (occ < 1) return fail(STENCIL_ERR_CUDA, "the batched kernel does not fit on an SM");
+  b->ntiles = (int)tiles.size();
   const int per_sm = b->per_sm > 0 ? std::min(b->per_sm, occ) : std::min(occ, 4);
   b->blocks = sm_count() * per_sm;
   if (b->ntiles > 0 && b->ntiles < b->blocks) b->blocks = b->ntiles;
+  b->ready = true;
   return STENCIL_OK;
 }
 
 int batch_enqueue(stencil_batch_s* b, cudaStream_t s) {
+  // a batch whose last (re)build failed part-way has no complete work list
+  if (!b->ready) return fail(STENCIL_ERR_ARG, "the batch has no complete work list (an earlier call failed)");
   if (b->Tb > 1) {
     if (b->ntb_tiles == 0) return STENCIL_OK;  // every item has T = 0
     BatchTbLaunch L;
@@ -1209,6 +1217,7 @@ void batch_release_lists(stencil_batch_s* b) {
   b->d_tb_tiles = nullptr;
   b->d_tb_flags = nullptr;
   b->ntiles = b->ntb_tiles = 0;
+  b->ready = false;
 }
 
 // Rebuilds the tile list for the batch's current kernel configuration.

@@ -87,6 +87,13 @@ def test_batch_retuning_reports_oom_and_recovers(st):
     alphas, Ts = [0.1, 0.2], [9, 4]
     dev = [torch.from_numpy(x.copy()).cuda() for x in grids]
     b = st.Batch(dev, alphas, Ts)
+    # a rebuild that fails part-way leaves no work list: running it is refused
+    st.stencil_debug_fail_allocations(1)
+    with pytest.raises(st.StencilError):
+        b.set_tuning(2)
+    st.stencil_debug_fail_allocations(-1)
+    with pytest.raises(st.StencilError):
+        b.run()
     first_success(st, lambda: b.set_tuning(4))
     assert b.get_tuning()[0] == 4
     b.run()
