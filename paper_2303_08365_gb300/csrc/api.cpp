@@ -371,15 +371,24 @@ int ensure_weights(stencil_plan_s* p) {
   for (int k = 0; k < p->taps.n; ++k) h[k] = p->taps.w[k];
   for (int k = 0; k < kOneSlots; ++k) h[p->taps.n + kZeroSlots + k] = 1.0;
   CUDA_TRY(dev_malloc(&p->d_w, h.size() * sizeof(double)), "allocating the weight array");
-  CUDA_TRY(cudaMemcpy(p->d_w, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice),
-           "copying the weights");
+  cudaError_t e = cudaMemcpy(p->d_w, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {  // leave no half-initialised array behind
+    cudaFree(p->d_w);
+    p->d_w = nullptr;
+    return cuda_fail(e, "copying the weights");
+  }
   return STENCIL_OK;
 }
 
 int ensure_status(stencil_plan_s* p) {
   if (p->d_status) return STENCIL_OK;
   CUDA_TRY(dev_malloc(&p->d_status, sizeof(int)), "allocating the status word");
-  CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(int)), "clearing the status word");
+  cudaError_t e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(p->d_status);
+    p->d_status = nullptr;
+    return cuda_fail(e, "clearing the status word");
+  }
   return STENCIL_OK;
 }
 
