@@ -13,7 +13,7 @@
 // library-owned partner; grids with odd T get their result copied back after
 // the last barrier.  The per-cell arithmetic is the tap order of the generic
 // sweep (lexicographic offsets: north, west, centre, east, south; the first
-// product is a plain multiply), so a batched grid is bitwise equal to the
+// product is an FMA onto 0.0), so a batched grid is bitwise equal to the
 // same grid advanced by stencil_run.
 #include "internal.h"
 #include "taps.cuh"

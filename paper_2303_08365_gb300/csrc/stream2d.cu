@@ -1,5 +1,6 @@
-// stream2d.cu -- 2D radius-1 sweep (5-point star or 9-point box) that streams
-// along y through a TMA-fed ring of row blocks in shared memory.
+// stream2d.cu -- 2D sweep (radius 1: 5-point star or 9-point box; radius 2:
+// 9-point star or 25-point box) that streams along y through a TMA-fed ring
+// of row blocks in shared memory.
 //
 // One step of u'(x) = sum_o w_o u~(x+o) (paper Sec. 2.1, Listing 1; Eq. 3 for
 // the heat weights).  A CTA owns a 64-column strip and walks down it in blocks
@@ -15,7 +16,8 @@
 //
 // Two arithmetic forms:
 //   - general weights: the taps in the direct kernel's lexicographic order
-//     (first product a multiply, then FMAs), bitwise equal to it;
+//     (the first an FMA onto a register holding 0.0, then FMAs), bitwise
+//     equal to it;
 //   - equal box weights w (e.g. 1/9): u' = w * sum of the 9 values, with the
 //     sums shared between neighbouring cells -- each warp owns two adjacent
 //     rows, so the column sums of 3 rows share their middle pair, and the two
