@@ -1,0 +1,59 @@
+"""Host-side logic of bench.py (no GPU): the roofline arithmetic, the DRAM
+traffic record and the measured-peak lookup."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_roofline_arithmetic():
+    # 512^3 cells, 1000 steps in 1548 ms at a 1.256 TFLOP/s FP64 peak
+    cells, T, ms, peak = 512 ** 3, 1000, 1548.0, 1.256
+    r = bench.roofline("heat3d-7pt", cells, T, ms, T, peak, "stream3d")
+    rate = cells * T / (ms * 1e-3) / 1e9
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(13 * rate / 1e3, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak, rel=1e-3)
+    assert r["fp64_ceiling_gstencil_per_s"] == pytest.approx(peak * 1e3 / 13, rel=1e-3)
+    assert r["hbm_ceiling_gstencil_per_s"] == pytest.approx(bench.HBM_GBS / 16, rel=1e-3)
+    # the FP64 term binds, so the stated-roofline fraction equals frac
+    assert r["frac_of_stated_roofline"] == pytest.approx(r["frac"], rel=1e-3)
+    assert r["fp64_pipe_frac"] == pytest.approx(7 * rate / (peak * 1e3 / 2), rel=1e-3)
+    assert r["algorithmic_bytes_per_launch"] == 16 * cells
+    # temporal blocking raises the HBM ceiling by Tb
+    r4 = bench.roofline("heat3d-7pt", cells, T, ms, T // 4, peak, "temporal", Tb=4)
+    assert r4["hbm_ceiling_gstencil_per_s"] == pytest.approx(4 * bench.HBM_GBS / 16, rel=1e-3)
+    assert r4["algorithmic_bytes_per_launch"] == 16 * cells  # one read + one write per 4 steps
+
+
+def test_instruction_override_and_bytes_per_cell():
+    r = bench.roofline("box2d-9pt", 10 ** 8, 10, 100.0, 10, 1.25, "stream2d", instr=9)
+    assert r["fp64_instr_per_cell"] == 9
+    a = bench.roofline("adjoint-7pt", 256 ** 3, 1000, 660.0, 2000, 1.25, "adjoint", bytes_per_cell=152)
+    assert a["hbm_ceiling_gstencil_per_s"] == pytest.approx(bench.HBM_GBS / 152, rel=1e-3)
+
+
+def test_traffic_record_matches_current_sources():
+    """The committed DRAM traffic applies to the streaming kernels as they are
+    now (their source hash matches), and a changed hash reads as unknown."""
+    for kernel, workload in [("stream3d", "heat3d-7pt"), ("stream3d", "box3d-27pt"), ("stream2d", "box2d-9pt")]:
+        t = bench.recorded_traffic(kernel, workload)
+        assert t is not None and t > 0, (kernel, workload)
+    assert bench.recorded_traffic("stream3d", "no-such-workload") is None
+    assert bench.recorded_traffic("direct", "heat3d-7pt") is None
+
+
+def test_measured_hbm_peak_is_read_from_the_file():
+    path = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        assert bench.HBM_GBS == pytest.approx(float(json.load(open(path))["hbm_gbs"]))
+    assert 1000.0 < bench.HBM_GBS < 20000.0
+
+
+def test_variant_kernel_names():
+    assert bench.variant_kernel("stream", 3) == "stream3d"
+    assert bench.variant_kernel("stream", 2) == "stream2d"
+    assert bench.variant_kernel("persistent", 2) == "batched"
+    assert bench.variant_kernel("temporal", 3) == "temporal"
