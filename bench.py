@@ -277,15 +277,19 @@ def headline(st, steps, warmup, world, stream):
     plan.run_host(host, T, stream=stream)
     torch.cuda.synchronize()
     barrier(world)
+    e2e_sampler = ClockSampler(uuid)
+    e2e_sampler.start()
     t0 = time.perf_counter()
     for _ in range(steps):
         plan.run_host(host, T, stream=stream)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+    e2e_clocks = e2e_sampler.stop()
     e2e_ms = barrier_max(world, e2e_ms)
     plan.close()
     del grid
     torch.cuda.empty_cache()
-    return dict(ms=ms / steps, launches=launches, clocks=clocks, e2e_ms=e2e_ms, h2d=h2d, d2h=h2d,
+    return dict(ms=ms / steps, launches=launches, clocks=clocks, e2e_ms=e2e_ms, e2e_clocks=e2e_clocks,
+                h2d=h2d, d2h=h2d,
                 Tb=tb, variant=st.stencil_variant_name(variant), u0=u0, checks=checks)
 
 
@@ -771,7 +775,8 @@ def main():
                              peak_tflops, variant_kernel(h["variant"], 3), Tb=h["Tb"]),
         "fp64_peak_tflops_measured": round(peak_tflops, 4),
         "e2e": {"value": round(e2e_value, 4), "unit": "GStencil/s",
-                "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"]},
+                "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"],
+                "clocks": h["e2e_clocks"]},
         "gpu_launches": int(h["launches"]),
         "clocks": h["clocks"],
         "result_checks": h["checks"],
