@@ -302,12 +302,18 @@ def time_plan(st, plan, grid, T, reps, stream, warm=1):
 
 
 def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, reps=2,
-               tb_sweep=None):
-    """One constant-weight workload with the plan's own choice of kernel and Tb;
-    `tb_sweep` ([(Tb, variant), ...]) also times each listed Tb (GStencil/s)."""
+               tb_sweep=None, autotune_steps=0):
+    """One constant-weight workload with the plan's own choice of kernel and Tb
+    (or, with `autotune_steps`, the plan autotuner's choice, timed on a scratch
+    copy first); `tb_sweep` ([(Tb, variant), ...]) also times each listed Tb
+    (GStencil/s)."""
     import torch
     grid = torch.from_numpy(u0).cuda()
     plan = st.Plan(shape, radius, weights, boundary)
+    if autotune_steps:
+        scratch = grid.clone()
+        plan.autotune(scratch, autotune_steps, stream=stream)
+        del scratch
     ms, launches = time_plan(st, plan, grid, T, reps, stream)
     cells = int(np.prod(shape))
     tb, v = plan.get_tuning()
@@ -329,7 +335,8 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
     out = {"workload": f"{name} {'x'.join(map(str, shape))} T={T} "
                        f"{'periodic' if boundary else 'dirichlet0'}",
            "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
-           "Tb": tb, "variant": st.stencil_variant_name(v), "launches": launches,
+           "Tb": tb, "variant": st.stencil_variant_name(v), "autotuned": bool(autotune_steps),
+           "launches": launches,
            "roofline": roofline(name, cells, T, ms, launches, peak,
                                 variant_kernel(st.stencil_variant_name(v), len(shape)), Tb=tb)}
     if sweep is not None:
@@ -810,7 +817,7 @@ def main():
             r = form_const(st, "heat3d-7pt", shp, 1, synth.heat_weights(3, HEADLINE["alpha"]), 1, 100, u0,
                            stream, peak_tflops, reps=1,
                            tb_sweep=[(1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
-                                     (4, st.VARIANT_TEMPORAL)])
+                                     (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL)])
             forms["heat3d_tb_sweep"] = {"workload": r["workload"],
                                         "tb_sweep_gstencil_per_s": r["tb_sweep_gstencil_per_s"]}
         if "box2d" in want:
@@ -846,11 +853,13 @@ def main():
                                            peak_tflops)
         if "box3d" in want:
             shp = (384, 384, 384)
-            # every Tb the 3D kernels offer (the temporal kernel covers Tb 2 and 4 in 3D)
+            # Tb picked by the plan autotuner among {1, 2, 4, 8} (and the Tb = 1
+            # kernels), then every Tb timed for the record
             forms["box3d"] = form_const(st, "box3d-27pt", shp, 1, synth.box_weights(3, seed=synth.SEED_BOX3D),
                                         0, 500, synth.normal(synth.SEED_BOX3D, shp), stream, peak_tflops,
                                         tb_sweep=[(1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
-                                                  (4, st.VARIANT_TEMPORAL)])
+                                                  (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL)],
+                                        autotune_steps=8)
         if "adjoint" in want:
             forms["adjoint"] = form_adjoint(st, stream, peak_tflops)
         line["forms"] = forms

@@ -230,7 +230,8 @@ typedef enum {
                                      along the slowest axis (2D/3D, radius 1;
                                      2D radius 2) */
   STENCIL_VARIANT_TEMPORAL = 3,   /* Tb fused steps per launch (overlapped
-                                     tiles): Tb 2, 4 (3D), 2, 4, 8 (1D, 2D) */
+                                     tiles): Tb 2, 4 or 8 (1D; 2D and 3D
+                                     radius 1) */
   STENCIL_VARIANT_PERSISTENT = 4  /* one launch for all T steps (2D radius 1):
                                      Tb = 1 with a device-wide barrier per step
                                      (5-point star), Tb > 1 with Tb steps in

@@ -554,7 +554,7 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   if (variant == kVariantTemporal && !temporal_supported(p->ndim, p->radius, Tb)) {
     if (forced)
       return fail(STENCIL_ERR_UNSUPPORTED,
-                  "temporal blocking covers radius-1 plans with Tb in {2, 4} (3D) or {2, 4, 8} (2D), "
+                  "temporal blocking covers 2D and 3D radius-1 plans with Tb in {2, 4, 8}, "
                   "and 1D plans of radius 1 or 2 with Tb in {2, 4, 8}");
     variant = default_variant(p) == kVariantStream && stream_ok ? kVariantStream : kVariantDirect;
   }

@@ -90,9 +90,8 @@ cudaError_t launch_stream2d(Shape shape, int radius, int boundary, bool equal, c
                             const HostTaps& taps, const double* wdev, const double* src, double* dst,
                             int* status, int sms, cudaStream_t stream);
 
-// Temporal blocking: Tb fused steps per launch (3D: Tb in {2, 4}; 2D: Tb in
-// {2, 4, 8}; radius 1, any shape and boundary; 1D: radius 1 or 2, Tb in
-// {2, 4, 8}).
+// Temporal blocking: Tb fused steps per launch (2D and 3D: radius 1, any
+// shape and boundary; 1D: radius 1 or 2; Tb in {2, 4, 8}).
 bool temporal_supported(int ndim, int radius, int Tb);
 cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int Tb, const Geom& g,
                             const double* wdev, const double* src, double* dst, int sms,

@@ -6,21 +6,25 @@
 // kernel does the same with overlapped tiles, streamed along the slowest axis:
 //
 //   - a CTA owns an output tile of the "plane" orthogonal to the streaming
-//     axis (3D: 64 x 16 cells of an (y, x) plane, streamed along z; 2D: 256
-//     cells of a row, streamed along y) and loads it with a halo of Tb cells;
+//     axis (3D: a square of the (y, x) plane, streamed along z; 2D: 256 cells
+//     of a row, streamed along y) and loads it with a halo of Tb cells;
 //   - stage s = 1 .. Tb holds the tile at time t+s on a region that shrinks by
 //     one cell per side per stage (the halo cells are recomputed by the
 //     neighbouring tiles: the overlapped-tile redundancy);
-//   - along the streaming axis nothing is recomputed: stage s produces plane
-//     i - s when input plane i arrives, from its own ring of 3 planes of stage
-//     s-1 output, so each input plane is read once from HBM and each output
-//     plane written once;
+//   - along the streaming axis nothing is recomputed: each stage keeps a ring
+//     of planes of its own output, so each input plane is read once from HBM
+//     and each output plane written once;
+//   - the stages are skewed by two planes (stage s produces plane k - 2s while
+//     input plane k lands), so that within one iteration no stage reads what
+//     another writes: one barrier per input plane covers all Tb stages, and
+//     the iteration's cells of every stage form one flat list of jobs (pairs
+//     of x-neighbours) spread over all warps, with no partial warp per stage;
 //   - input planes arrive by cp.async (8-byte copies with zero fill for
 //     Dirichlet ghosts and wrapped addresses for periodic grids; a periodic
 //     halo of width Tb does not fit the TMA box model at the grid edges);
 //   - each cell applies its taps in the direct kernel's lexicographic order
 //     with register-resident weights, so a Tb-fused sweep is bitwise equal to
-//     Tb single steps.
+//     Tb single steps; the last stage stores its pairs as 16-byte stores.
 // Dirichlet ghost cells (outside the grid, at every time level) stay zero.
 #include "internal.h"
 #include "taps.cuh"
@@ -28,30 +32,48 @@
 namespace gbst {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;  // 1D kernel
 
-// Threads of the 2D/3D temporal kernel: deep blocks (Tb >= 4) take a CTA per
-// SM and need 16 warps to keep the FP64 pipe busy (measured: 3D 7-point Tb 4
-// 58.6 vs 56.1 GStencil/s, 2D 9-point Tb 8 59.0 vs 54.4); Tb = 2 runs two
-// CTAs of 8 warps (77.0 vs 73.7).
-template <int TB>
-constexpr int temporal_threads() { return TB >= 4 ? 512 : 256; }
-
-template <int NDIM>
+// Output tile (y, x) of the 2D/3D kernel.  3D: the square with the shortest
+// perimeter per cell, hence the least halo recompute, whose stage rings fit
+// in shared memory (Tb = 2: 32 x 32, 1.06x the single-step work; Tb = 4:
+// 32 x 32, 1.20x; Tb = 8: 16 x 16, 2.15x).  2D: 256 cells of a row (1.003x to
+// 1.03x).
+template <int NDIM, int TB>
 struct Geo {
-  static constexpr int TX = NDIM == 3 ? 64 : 256;  // output tile width (x)
-  static constexpr int TY = NDIM == 3 ? 16 : 1;    // output tile height (y); 2D: the plane is a row
+  static constexpr int TX = NDIM == 3 ? (TB >= 8 ? 16 : 32) : 256;
+  static constexpr int TY = NDIM == 3 ? TX : 1;
 };
 
+// 16 warps (one CTA per SM) where the stage rings fill shared memory (3D,
+// Tb >= 4), else 8 warps with two or more CTAs per SM.
 template <int NDIM, int TB>
-struct PlaneDims {
-  static constexpr int PX = Geo<NDIM>::TX + 2 * TB;
-  static constexpr int PY = NDIM == 3 ? Geo<NDIM>::TY + 2 * TB : 1;
-  static constexpr int P = PX * PY;  // doubles per plane
-  static constexpr int kIn = 4;      // input ring slots
-  static constexpr int kStageRing = 3;
-  static constexpr int planes = kIn + kStageRing * (TB - 1);
-  static constexpr size_t bytes = (size_t)planes * P * sizeof(double);
+constexpr int temporal_threads() { return NDIM == 3 && TB >= 4 ? 512 : 256; }
+template <int NDIM, int TB>
+constexpr int temporal_min_blocks() { return temporal_threads<NDIM, TB>() == 512 ? 1 : 2; }
+
+// Shared-memory layout.  Plane coordinates (py, px) cover the tile and a halo
+// of Tb cells per side.  Stage q = 0 .. Tb-1 (q = 0: the input) keeps a ring
+// of 4 planes over its region [q, PX-q) x [q, PY-q) (2D: the row [q, PX-q)),
+// stored compactly with row stride W(q): three planes that stage q+1 reads
+// and the one stage q is writing (or, for the input, landing).
+template <int NDIM, int TB>
+struct Lay {
+  static constexpr int PX = Geo<NDIM, TB>::TX + 2 * TB;
+  static constexpr int PY = NDIM == 3 ? Geo<NDIM, TB>::TY + 2 * TB : 1;
+  static constexpr int P = PX * PY;
+  static constexpr int kRing = 4;
+  __host__ __device__ static constexpr int W(int q) { return PX - 2 * q; }
+  __host__ __device__ static constexpr int H(int q) { return NDIM == 3 ? PY - 2 * q : 1; }
+  __host__ __device__ static constexpr int N(int q) { return W(q) * H(q); }
+  // first double of stage q's ring: 4 * (N(0) + ... + N(q-1)), in closed form
+  __host__ __device__ static constexpr int off(int q) {
+    return NDIM == 3 ? kRing * (q * PX * PY - (PX + PY) * q * (q - 1) + 2 * (q - 1) * q * (2 * q - 1) / 3)
+                     : kRing * (q * PX - q * (q - 1));
+  }
+  static constexpr size_t bytes = (size_t)off(TB) * sizeof(double);
+  // jobs (pairs of x-neighbours; W(q) is even, so a pair never straddles a row)
+  __host__ __device__ static constexpr int pairs(int q) { return N(q) / 2; }
 };
 
 struct TParams {
@@ -74,20 +96,19 @@ __device__ __forceinline__ void cp_async8(double* dst, const double* src, bool v
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(sz) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Issues the copies of input plane w (global streaming coordinate) of the tile
 // whose output origin is (y0, x0) into `slot`.
 template <int NDIM, int TB, bool PERIODIC>
 __device__ __forceinline__ void load_plane(double* slot, const TParams& P, int w, int y0, int x0) {
-  using D = PlaneDims<NDIM, TB>;
+  using L = Lay<NDIM, TB>;
   bool win = true;
   int ww = w;
   if (PERIODIC) ww = wrapn(w, P.nw);
   else win = (unsigned)w < (unsigned)P.nw;
-  for (int c = threadIdx.x; c < D::P; c += temporal_threads<TB>()) {
-    const int px = c % D::PX, py = c / D::PX;
+  for (int c = threadIdx.x; c < L::P; c += temporal_threads<NDIM, TB>()) {
+    const int px = c % L::PX, py = c / L::PX;
     int x = x0 - TB + px;
     int y = NDIM == 3 ? y0 - TB + py : 0;
     bool in = win;
@@ -116,13 +137,14 @@ __device__ __forceinline__ constexpr int tidx(int dw, int dv, int du) {
   return dw < 0 ? 0 : dw > 0 ? 4 : 2 + du;
 }
 
-// One cell of a stage: taps over planes (pm, p0, pp) of the previous stage at
-// in-plane position (py, px).
-template <int NDIM, int NT, bool BOX, int PX>
-__device__ __forceinline__ double cell_update(const RegWeights<NT>& W, const double* pm,
-                                              const double* p0, const double* pp, int py, int px) {
+// Two x-neighbouring cells of a stage: taps over planes (pm, p0, pp) of the
+// previous stage (row stride sw) around the cells at (ly, lx) and (ly, lx+1)
+// of that stage's region.  Two independent chains, each in tap order.
+template <int NDIM, int NT, bool BOX>
+__device__ __forceinline__ void pair_update(const RegWeights<NT>& W, const double* pm, const double* p0,
+                                            const double* pp, int sw, int ly, int lx, double& a0,
+                                            double& a1) {
   const double* pl[3] = {pm, p0, pp};
-  double acc = 0.0;
 #pragma unroll
   for (int dw = -1; dw <= 1; ++dw) {
 #pragma unroll
@@ -130,24 +152,23 @@ __device__ __forceinline__ double cell_update(const RegWeights<NT>& W, const dou
       if (NDIM == 2 && dv != 0) continue;
 #pragma unroll
       for (int du = -1; du <= 1; ++du) {
-        const int nz_axes = (dw != 0) + (dv != 0) + (du != 0);
-        if (!BOX && nz_axes > 1) continue;
-        const double v = pl[dw + 1][(py + dv) * PX + px + du];
-        W.tap(acc, tidx<NDIM, BOX>(dw, dv, du), v, 0);
+        if (!BOX && (dw != 0) + (dv != 0) + (du != 0) > 1) continue;
+        const double* q = pl[dw + 1] + (ly + dv) * sw + lx + du;
+        const int t = tidx<NDIM, BOX>(dw, dv, du);
+        W.tap(a0, t, q[0], 0);
+        W.tap(a1, t, q[1], 1);
       }
     }
   }
-  return acc;
 }
 
 template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
-__global__ void __launch_bounds__(temporal_threads<TB>(), 1) k_temporal(const TParams P) {
-  using D = PlaneDims<NDIM, TB>;
-  constexpr int PX = D::PX, PY = D::PY;
-  constexpr int TX = Geo<NDIM>::TX, TY = Geo<NDIM>::TY;
+__global__ void __launch_bounds__(temporal_threads<NDIM, TB>(), temporal_min_blocks<NDIM, TB>())
+    k_temporal(const TParams P) {
+  using L = Lay<NDIM, TB>;
+  constexpr int NTH = temporal_threads<NDIM, TB>();
+  constexpr int TX = Geo<NDIM, TB>::TX, TY = Geo<NDIM, TB>::TY;
   extern __shared__ __align__(16) double sm[];
-  double* in_ring = sm;                       // kIn planes
-  double* st_ring = sm + D::kIn * D::P;       // (TB-1) stages x 3 planes
   RegWeights<NT> W;
   W.load(P.wdev);
 
@@ -162,62 +183,62 @@ __global__ void __launch_bounds__(temporal_threads<TB>(), 1) k_temporal(const TP
     f += wb - wa;
     const int x0 = (tile % P.tiles_x) * TX;
     const int y0 = (tile / P.tiles_x) * TY;
-    const int nin = (wb - wa) + 2 * TB;  // input planes wa-TB .. wb+TB-1
-    // prologue: planes 0 and 1 in flight
-    load_plane<NDIM, TB, PERIODIC>(in_ring + 0 * D::P, P, wa - TB, y0, x0);
+    // input planes i = 0 .. nin-1 are streaming coordinates wa-TB .. wb+TB-1;
+    // stage s produces its planes i in [s, nin-s), plane i in iteration i + 2s
+    const int nin = (wb - wa) + 2 * TB;
+    load_plane<NDIM, TB, PERIODIC>(sm, P, wa - TB, y0, x0);
     cp_async_commit();
-    load_plane<NDIM, TB, PERIODIC>(in_ring + 1 * D::P, P, wa - TB + 1, y0, x0);
-    cp_async_commit();
-    for (int k = 0; k < nin; ++k) {
-      cp_async_wait<1>();  // plane k has landed (plane k+1 may still be in flight)
-      __syncthreads();
-#pragma unroll
-      for (int s = 1; s <= TB; ++s) {
-        const int i = k - s;  // plane index this stage produces now
-        if (i < s || i >= nin - s) continue;
-        const double *pm, *p0, *pp;
-        if (s == 1) {
-          pm = in_ring + ((i - 1) & 3) * D::P;
-          p0 = in_ring + (i & 3) * D::P;
-          pp = in_ring + ((i + 1) & 3) * D::P;
-        } else {
-          const double* r = st_ring + (s - 2) * 3 * D::P;
-          pm = r + ((i - 1) % 3) * D::P;
-          p0 = r + (i % 3) * D::P;
-          pp = r + ((i + 1) % 3) * D::P;
-        }
-        const int w = wa - TB + i;  // streaming coordinate of the produced plane
-        const bool wghost = !PERIODIC && (unsigned)w >= (unsigned)P.nw;
-        const int sy = NDIM == 3 ? s : 0;
-        const int cw = PX - 2 * s, ch = PY - 2 * sy;
-        if (s < TB) {
-          double* out = st_ring + (s - 1) * 3 * D::P + (i % 3) * D::P;
-          for (int c = threadIdx.x; c < cw * ch; c += temporal_threads<TB>()) {
-            const int px = s + c % cw, py = sy + c / cw;
-            const int x = x0 - TB + px, y = NDIM == 3 ? y0 - TB + py : 0;
-            const bool ghost = !PERIODIC && (wghost || (unsigned)x >= (unsigned)P.nx ||
-                                             (NDIM == 3 && (unsigned)y >= (unsigned)P.ny));
-            out[py * PX + px] = ghost ? 0.0 : cell_update<NDIM, NT, BOX, PX>(W, pm, p0, pp, py, px);
-          }
-        } else {
-          // last stage: the tile itself, straight to global memory
-          for (int c = threadIdx.x; c < cw * ch; c += temporal_threads<TB>()) {
-            const int px = s + c % cw, py = sy + c / cw;
-            const int x = x0 - TB + px, y = NDIM == 3 ? y0 - TB + py : 0;
-            if (x >= P.nx || (NDIM == 3 && y >= P.ny)) continue;
-            const double v = cell_update<NDIM, NT, BOX, PX>(W, pm, p0, pp, py, px);
-            if (NDIM == 3) P.dst[((int64_t)w * P.ny + y) * P.nx + x] = v;
-            else P.dst[(int64_t)w * P.nx + x] = v;
-          }
-        }
-        __syncthreads();
-      }
-      // input plane k+2 goes into the slot of plane k-2 (no stage reads it any more)
-      if (k + 2 < nin) load_plane<NDIM, TB, PERIODIC>(in_ring + ((k + 2) & 3) * D::P, P, wa - TB + k + 2, y0, x0);
+    for (int k = 1; k < nin + TB; ++k) {
+      cp_async_wait_all();  // input plane k-1 has landed
+      __syncthreads();      // ... for every thread, and iteration k-1's stage planes are written
+      if (k < nin) load_plane<NDIM, TB, PERIODIC>(sm + (k & 3) * L::P, P, wa - TB + k, y0, x0);
       cp_async_commit();
+      // the flat job list of this iteration: stage s contributes its pairs
+      // when its plane k - 2s is in range, i.e. for s_lo <= s <= s_hi
+      const int s_lo = max(1, k - nin + 1), s_hi = min(TB, k / 3);
+      int njobs = 0;
+      for (int s = s_lo; s <= s_hi; ++s) njobs += L::pairs(s);
+      for (int j = threadIdx.x; j < njobs; j += NTH) {
+        int s = s_lo, c = j;
+        while (c >= L::pairs(s)) {
+          c -= L::pairs(s);
+          ++s;
+        }
+        const int i = k - 2 * s;
+        const int cw = L::W(s) / 2;          // pairs per row of stage s
+        const int qy = NDIM == 3 ? c / cw : 0;
+        const int qx = 2 * (c - qy * cw);    // offset of the pair in stage s's region
+        const int sn = L::N(s - 1);
+        const double* src = sm + L::off(s - 1);
+        const double* pm = src + ((i - 1) & 3) * sn;
+        const double* p0 = src + (i & 3) * sn;
+        const double* pp = src + ((i + 1) & 3) * sn;
+        double a0, a1;
+        pair_update<NDIM, NT, BOX>(W, pm, p0, pp, L::W(s - 1), NDIM == 3 ? qy + 1 : 0, qx + 1, a0, a1);
+        const int w = wa - TB + i;
+        const int x = x0 - TB + s + qx;
+        const int y = NDIM == 3 ? y0 - TB + s + qy : 0;
+        if (s < TB) {
+          if (!PERIODIC) {
+            const bool rowg = (unsigned)w >= (unsigned)P.nw || (NDIM == 3 && (unsigned)y >= (unsigned)P.ny);
+            if (rowg || (unsigned)x >= (unsigned)P.nx) a0 = 0.0;
+            if (rowg || (unsigned)(x + 1) >= (unsigned)P.nx) a1 = 0.0;
+          }
+          double* out = sm + L::off(s) + (i & 3) * L::N(s) + qy * L::W(s) + qx;  // 16-byte aligned
+          *reinterpret_cast<double2*>(out) = make_double2(a0, a1);
+        } else if (NDIM == 2 || y < P.ny) {
+          // the tile itself (x >= 0, y >= 0, w in range): straight to global memory
+          double* g = P.dst + (NDIM == 3 ? ((int64_t)w * P.ny + y) * P.nx : (int64_t)w * P.nx) + x;
+          if (x + 1 < P.nx && (reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+            *reinterpret_cast<double2*>(g) = make_double2(a0, a1);
+          } else {
+            if (x < P.nx) g[0] = a0;
+            if (x + 1 < P.nx) g[1] = a1;
+          }
+        }
+      }
     }
-    cp_async_wait<0>();
-    __syncthreads();
+    __syncthreads();  // the next tile's first plane reuses input slot 0
   }
   (void)TY;
 }
@@ -225,13 +246,15 @@ __global__ void __launch_bounds__(temporal_threads<TB>(), 1) k_temporal(const TP
 template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
 cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, double* dst, int sms,
                       cudaStream_t stream) {
-  using D = PlaneDims<NDIM, TB>;
+  using L = Lay<NDIM, TB>;
+  constexpr int NTH = temporal_threads<NDIM, TB>();
+  static_assert(L::bytes <= 227 * 1024, "stage rings exceed shared memory");
   auto kern = k_temporal<NDIM, NT, BOX, PERIODIC, TB>;
   static std::atomic<int> cache[kMaxDeviceOrdinals];
   const int occ = cached_per_device(cache, [kern] {
     int n = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D::bytes) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, temporal_threads<TB>(), D::bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NTH, L::bytes) != cudaSuccess)
       n = 0;
     return n;
   });
@@ -242,13 +265,13 @@ cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, doub
   P.nw = NDIM == 3 ? g.nz : g.ny;
   P.ny = g.ny;
   P.nx = g.nx;
-  P.tiles_x = (g.nx + Geo<NDIM>::TX - 1) / Geo<NDIM>::TX;
-  P.tiles_y = NDIM == 3 ? (g.ny + Geo<NDIM>::TY - 1) / Geo<NDIM>::TY : 1;
+  P.tiles_x = (g.nx + Geo<NDIM, TB>::TX - 1) / Geo<NDIM, TB>::TX;
+  P.tiles_y = NDIM == 3 ? (g.ny + Geo<NDIM, TB>::TY - 1) / Geo<NDIM, TB>::TY : 1;
   P.work = (long long)P.tiles_x * P.tiles_y * P.nw;
   P.wdev = wdev;
   long long grid = (long long)sms * occ;
   if (grid > P.work) grid = P.work;
-  kern<<<(unsigned)grid, temporal_threads<TB>(), D::bytes, stream>>>(P);
+  kern<<<(unsigned)grid, NTH, L::bytes, stream>>>(P);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
@@ -259,9 +282,7 @@ cudaError_t by_tb(int Tb, const Geom& g, const double* wdev, const double* src, 
   switch (Tb) {
     case 2: return launch_tb<NDIM, NT, BOX, PERIODIC, 2>(g, wdev, src, dst, sms, stream);
     case 4: return launch_tb<NDIM, NT, BOX, PERIODIC, 4>(g, wdev, src, dst, sms, stream);
-    case 8:
-      if (NDIM == 2) return launch_tb<NDIM, NT, BOX, PERIODIC, (NDIM == 2 ? 8 : 4)>(g, wdev, src, dst, sms, stream);
-      return cudaErrorInvalidValue;
+    case 8: return launch_tb<NDIM, NT, BOX, PERIODIC, 8>(g, wdev, src, dst, sms, stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -340,9 +361,7 @@ cudaError_t launch_1d(int Tb, const Geom& g, const double* wdev, const double* s
 bool temporal_supported(int ndim, int radius, int Tb) {
   if (ndim == 1) return (radius == 1 || radius == 2) && (Tb == 2 || Tb == 4 || Tb == 8);
   if (radius != 1) return false;
-  if (ndim == 3) return Tb == 2 || Tb == 4;
-  if (ndim == 2) return Tb == 2 || Tb == 4 || Tb == 8;
-  return false;
+  return (ndim == 2 || ndim == 3) && (Tb == 2 || Tb == 4 || Tb == 8);
 }
 
 cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int Tb, const Geom& g,

@@ -320,6 +320,11 @@ TEMPORAL_CASES = [
     ((50, 300), DIRICHLET, "box_rand", 4, 12),
     ((33, 61), DIRICHLET, "star_rand", 2, 3),
     ((7, 5), PERIODIC, "box_eq", 8, 16),
+    ((11, 37, 70), PERIODIC, "heat", 8, 19),       # 3D Tb = 8: 16 x 16 tiles, ragged edges
+    ((9, 20, 33), DIRICHLET, "box_rand", 8, 11),
+    ((4, 3, 5), PERIODIC, "heat", 8, 9),           # every axis shorter than the halo
+    ((6, 70, 100), DIRICHLET, "heat", 4, 4),       # several 32 x 32 tiles, ragged in y and x
+    ((40, 530), DIRICHLET, "star_rand", 8, 8),     # 2D: three 256-cell tiles, ragged
 ]
 
 
@@ -341,8 +346,10 @@ def test_temporal_blocking_matches_single_steps_bitwise(st, shape, boundary, kin
 
 def test_temporal_unsupported_tb_is_rejected(st):
     import torch
-    p = st.Plan((8, 8, 8), 1, synth.heat_weights(3, 0.1), PERIODIC)
-    p.set_tuning(8, st.VARIANT_TEMPORAL)   # 3D supports Tb 2 and 4
+    w = np.zeros((5, 5, 5))
+    w[2, 2, 2] = 1.0
+    p = st.Plan((8, 8, 8), 2, w, PERIODIC)
+    p.set_tuning(4, st.VARIANT_TEMPORAL)   # 2D/3D temporal blocking covers radius 1
     g = torch.from_numpy(synth.uniform(1, (8, 8, 8))).cuda()
     with pytest.raises(st.StencilError) as ei:
         p.run(g, 8)
@@ -360,7 +367,7 @@ def test_autotune_picks_a_candidate_and_keeps_results(st):
     assert rate > 0
     tb, v = p.get_tuning()
     assert (tb, v) in [(1, st.VARIANT_DIRECT), (1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
-                       (4, st.VARIANT_TEMPORAL)]
+                       (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL)]
     u0 = synth.uniform(4, shape)
     g = torch.from_numpy(u0.copy()).cuda()
     p.run(g, 10)
