@@ -775,7 +775,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "Tb": h["Tb"], "variant": h["variant"],
                    "tile": {"stream": "64 x 32 cells of (x, y), streamed along z, 4-plane TMA ring",
-                            "temporal": "64 x 16 cells of (x, y) plus a Tb halo, streamed along z",
+                            "temporal": "64 x 32 (Tb 2), 32 x 32 (Tb 4) or 16 x 16 (Tb 8) cells of (x, y) "
+                                        "plus a Tb halo, streamed along z",
                             "direct": "one cell per thread, 32 x 8 threads"}.get(h["variant"], h["variant"]),
                    "l2_flush": "none needed: each launch streams 2 GiB > 129 MB L2"},
         "roofline": roofline("heat3d-7pt", cells, T, h["ms"], h["launches"] // args.steps,

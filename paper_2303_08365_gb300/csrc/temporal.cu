@@ -34,23 +34,28 @@ namespace {
 
 constexpr int kThreads = 256;  // 1D kernel
 
-// Output tile (y, x) of the 2D/3D kernel.  3D: the square with the shortest
-// perimeter per cell, hence the least halo recompute, whose stage rings fit
-// in shared memory (Tb = 2: 32 x 32, 1.06x the single-step work; Tb = 4:
-// 32 x 32, 1.20x; Tb = 8: 16 x 16, 2.15x).  2D: 256 cells of a row (1.003x to
-// 1.03x).
+// Output tile (y, x) of the 2D/3D kernel.  3D: the tile with the shortest
+// perimeter per cell, hence the least halo recompute, whose stage rings fit in
+// shared memory (Tb = 2: 32 x 64, 1.05x the single-step work; Tb = 4: 32 x 32,
+// 1.20x; Tb = 8: 16 x 16, 2.15x).  2D: a row segment of about 256 cells, cut
+// so that one iteration's jobs (Tb stages of pairs) fill just under Tb whole
+// rounds of 8 warps (Tb = 2: 254 cells, 255 pairs; 4: 252, 510; 8: 248, 1020):
+// a round with a few pairs left over would cost a whole warp instruction per
+// FP64 operation for them.
 template <int NDIM, int TB>
 struct Geo {
-  static constexpr int TX = NDIM == 3 ? (TB >= 8 ? 16 : 32) : 256;
-  static constexpr int TY = NDIM == 3 ? TX : 1;
+  static constexpr int TX = NDIM == 3 ? (TB == 2 ? 64 : TB == 4 ? 32 : 16)
+                                      : 2 * ((128 * TB - TB * (TB - 1) / 2) / TB);
+  static constexpr int TY = NDIM == 3 ? (TB == 2 ? 32 : TX) : 1;
 };
 
-// 16 warps (one CTA per SM) where the stage rings fill shared memory (3D,
-// Tb >= 4), else 8 warps with two or more CTAs per SM.
-template <int NDIM, int TB>
-constexpr int temporal_threads() { return NDIM == 3 && TB >= 4 ? 512 : 256; }
-template <int NDIM, int TB>
-constexpr int temporal_min_blocks() { return temporal_threads<NDIM, TB>() == 512 ? 1 : 2; }
+// One CTA per SM in 3D (the stage rings take 147-172 KB of shared memory)
+// with 24 warps, or 16 for the 27-point box, whose 27 weights stay in
+// registers; 8 warps in 2D, with several CTAs per SM.
+template <int NDIM, bool BOX>
+constexpr int temporal_threads() { return NDIM == 3 ? (BOX ? 512 : 768) : 256; }
+template <int NDIM, bool BOX>
+constexpr int temporal_min_blocks() { return NDIM == 3 ? 1 : 2; }
 
 // Shared-memory layout.  Plane coordinates (py, px) cover the tile and a halo
 // of Tb cells per side.  Stage q = 0 .. Tb-1 (q = 0: the input) keeps a ring
@@ -72,7 +77,9 @@ struct Lay {
                      : kRing * (q * PX - q * (q - 1));
   }
   static constexpr size_t bytes = (size_t)off(TB) * sizeof(double);
-  // jobs (pairs of x-neighbours; W(q) is even, so a pair never straddles a row)
+  // jobs: pairs of y-neighbours in 3D (H(q) is even: a pair never leaves the
+  // region, and a warp reads 32 consecutive doubles of a row per load), pairs
+  // of x-neighbours in 2D (W(q) is even)
   __host__ __device__ static constexpr int pairs(int q) { return N(q) / 2; }
 };
 
@@ -100,14 +107,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Issues the copies of input plane w (global streaming coordinate) of the tile
 // whose output origin is (y0, x0) into `slot`.
-template <int NDIM, int TB, bool PERIODIC>
+template <int NDIM, int TB, bool PERIODIC, int NTH>
 __device__ __forceinline__ void load_plane(double* slot, const TParams& P, int w, int y0, int x0) {
   using L = Lay<NDIM, TB>;
   bool win = true;
   int ww = w;
   if (PERIODIC) ww = wrapn(w, P.nw);
   else win = (unsigned)w < (unsigned)P.nw;
-  for (int c = threadIdx.x; c < L::P; c += temporal_threads<NDIM, TB>()) {
+  for (int c = threadIdx.x; c < L::P; c += NTH) {
     const int px = c % L::PX, py = c / L::PX;
     int x = x0 - TB + px;
     int y = NDIM == 3 ? y0 - TB + py : 0;
@@ -137,14 +144,16 @@ __device__ __forceinline__ constexpr int tidx(int dw, int dv, int du) {
   return dw < 0 ? 0 : dw > 0 ? 4 : 2 + du;
 }
 
-// Two x-neighbouring cells of a stage: taps over planes (pm, p0, pp) of the
-// previous stage (row stride sw) around the cells at (ly, lx) and (ly, lx+1)
-// of that stage's region.  Two independent chains, each in tap order.
+// Two neighbouring cells of a stage (3D: along y; 2D: along x): taps over
+// planes (pm, p0, pp) of the previous stage (row stride sw) around the cells
+// at (ly, lx) and (ly + 1, lx) (2D: (0, lx) and (0, lx + 1)) of that stage's
+// region.  Two independent chains, each in tap order.
 template <int NDIM, int NT, bool BOX>
 __device__ __forceinline__ void pair_update(const RegWeights<NT>& W, const double* pm, const double* p0,
                                             const double* pp, int sw, int ly, int lx, double& a0,
                                             double& a1) {
   const double* pl[3] = {pm, p0, pp};
+  const int de = NDIM == 3 ? sw : 1;  // the second cell
 #pragma unroll
   for (int dw = -1; dw <= 1; ++dw) {
 #pragma unroll
@@ -156,17 +165,17 @@ __device__ __forceinline__ void pair_update(const RegWeights<NT>& W, const doubl
         const double* q = pl[dw + 1] + (ly + dv) * sw + lx + du;
         const int t = tidx<NDIM, BOX>(dw, dv, du);
         W.tap(a0, t, q[0], 0);
-        W.tap(a1, t, q[1], 1);
+        W.tap(a1, t, q[de], 1);
       }
     }
   }
 }
 
 template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
-__global__ void __launch_bounds__(temporal_threads<NDIM, TB>(), temporal_min_blocks<NDIM, TB>())
+__global__ void __launch_bounds__(temporal_threads<NDIM, BOX>(), temporal_min_blocks<NDIM, BOX>())
     k_temporal(const TParams P) {
   using L = Lay<NDIM, TB>;
-  constexpr int NTH = temporal_threads<NDIM, TB>();
+  constexpr int NTH = temporal_threads<NDIM, BOX>();
   constexpr int TX = Geo<NDIM, TB>::TX, TY = Geo<NDIM, TB>::TY;
   extern __shared__ __align__(16) double sm[];
   RegWeights<NT> W;
@@ -186,12 +195,12 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, TB>(), temporal_min_blo
     // input planes i = 0 .. nin-1 are streaming coordinates wa-TB .. wb+TB-1;
     // stage s produces its planes i in [s, nin-s), plane i in iteration i + 2s
     const int nin = (wb - wa) + 2 * TB;
-    load_plane<NDIM, TB, PERIODIC>(sm, P, wa - TB, y0, x0);
+    load_plane<NDIM, TB, PERIODIC, NTH>(sm, P, wa - TB, y0, x0);
     cp_async_commit();
     for (int k = 1; k < nin + TB; ++k) {
       cp_async_wait_all();  // input plane k-1 has landed
       __syncthreads();      // ... for every thread, and iteration k-1's stage planes are written
-      if (k < nin) load_plane<NDIM, TB, PERIODIC>(sm + (k & 3) * L::P, P, wa - TB + k, y0, x0);
+      if (k < nin) load_plane<NDIM, TB, PERIODIC, NTH>(sm + (k & 3) * L::P, P, wa - TB + k, y0, x0);
       cp_async_commit();
       // the flat job list of this iteration: stage s contributes its pairs
       // when its plane k - 2s is in range, i.e. for s_lo <= s <= s_hi
@@ -205,9 +214,16 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, TB>(), temporal_min_blo
           ++s;
         }
         const int i = k - 2 * s;
-        const int cw = L::W(s) / 2;          // pairs per row of stage s
-        const int qy = NDIM == 3 ? c / cw : 0;
-        const int qx = 2 * (c - qy * cw);    // offset of the pair in stage s's region
+        const int ws = L::W(s);
+        int qy, qx;  // the pair's first cell, as an offset in stage s's region
+        if (NDIM == 3) {
+          qy = c / ws;
+          qx = c - qy * ws;
+          qy *= 2;
+        } else {
+          qy = 0;
+          qx = 2 * c;
+        }
         const int sn = L::N(s - 1);
         const double* src = sm + L::off(s - 1);
         const double* pm = src + ((i - 1) & 3) * sn;
@@ -219,16 +235,32 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, TB>(), temporal_min_blo
         const int x = x0 - TB + s + qx;
         const int y = NDIM == 3 ? y0 - TB + s + qy : 0;
         if (s < TB) {
-          if (!PERIODIC) {
-            const bool rowg = (unsigned)w >= (unsigned)P.nw || (NDIM == 3 && (unsigned)y >= (unsigned)P.ny);
-            if (rowg || (unsigned)x >= (unsigned)P.nx) a0 = 0.0;
-            if (rowg || (unsigned)(x + 1) >= (unsigned)P.nx) a1 = 0.0;
+          double* out = sm + L::off(s) + (i & 3) * L::N(s) + qy * ws + qx;
+          if (NDIM == 3) {
+            if (!PERIODIC) {
+              const bool g = (unsigned)w >= (unsigned)P.nw || (unsigned)x >= (unsigned)P.nx;
+              if (g || (unsigned)y >= (unsigned)P.ny) a0 = 0.0;
+              if (g || (unsigned)(y + 1) >= (unsigned)P.ny) a1 = 0.0;
+            }
+            out[0] = a0;
+            out[ws] = a1;
+          } else {
+            if (!PERIODIC) {
+              const bool g = (unsigned)w >= (unsigned)P.nw;
+              if (g || (unsigned)x >= (unsigned)P.nx) a0 = 0.0;
+              if (g || (unsigned)(x + 1) >= (unsigned)P.nx) a1 = 0.0;
+            }
+            *reinterpret_cast<double2*>(out) = make_double2(a0, a1);  // 16-byte aligned
           }
-          double* out = sm + L::off(s) + (i & 3) * L::N(s) + qy * L::W(s) + qx;  // 16-byte aligned
-          *reinterpret_cast<double2*>(out) = make_double2(a0, a1);
-        } else if (NDIM == 2 || y < P.ny) {
+        } else if (NDIM == 3) {
           // the tile itself (x >= 0, y >= 0, w in range): straight to global memory
-          double* g = P.dst + (NDIM == 3 ? ((int64_t)w * P.ny + y) * P.nx : (int64_t)w * P.nx) + x;
+          if (x < P.nx) {
+            double* g = P.dst + ((int64_t)w * P.ny + y) * P.nx + x;
+            if (y < P.ny) g[0] = a0;
+            if (y + 1 < P.ny) g[P.nx] = a1;
+          }
+        } else {
+          double* g = P.dst + (int64_t)w * P.nx + x;
           if (x + 1 < P.nx && (reinterpret_cast<uintptr_t>(g) & 15) == 0) {
             *reinterpret_cast<double2*>(g) = make_double2(a0, a1);
           } else {
@@ -240,14 +272,13 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, TB>(), temporal_min_blo
     }
     __syncthreads();  // the next tile's first plane reuses input slot 0
   }
-  (void)TY;
 }
 
 template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
 cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, double* dst, int sms,
                       cudaStream_t stream) {
   using L = Lay<NDIM, TB>;
-  constexpr int NTH = temporal_threads<NDIM, TB>();
+  constexpr int NTH = temporal_threads<NDIM, BOX>();
   static_assert(L::bytes <= 227 * 1024, "stage rings exceed shared memory");
   auto kern = k_temporal<NDIM, NT, BOX, PERIODIC, TB>;
   static std::atomic<int> cache[kMaxDeviceOrdinals];
