@@ -34,48 +34,67 @@ namespace {
 
 constexpr int kThreads = 256;  // 1D kernel
 
-// Output tile (y, x) of the 2D/3D kernel.  3D: the tile with the shortest
-// perimeter per cell, hence the least halo recompute, whose stage rings fit in
-// shared memory (Tb = 2: 32 x 64, 1.05x the single-step work; Tb = 4: 32 x 32,
-// 1.20x; Tb = 8: 16 x 16, 2.15x).  2D: a row segment of about 256 cells, cut
-// so that one iteration's jobs (Tb stages of pairs) fill just under Tb whole
-// rounds of 8 warps (Tb = 2: 254 cells, 255 pairs; 4: 252, 510; 8: 248, 1020):
-// a round with a few pairs left over would cost a whole warp instruction per
-// FP64 operation for them.
+// Output tile (y, x) of the 2D/3D kernel.  3D: Tb = 2: 16 x 64 (1.08x the
+// single-step work in halo recompute); Tb = 4: 32 x 32 (1.20x), the tile with
+// the shortest perimeter per cell whose stage rings fit in shared memory;
+// Tb = 8: 16 x 16 (2.15x).  2D: a row segment of about 256 cells, cut so that
+// one iteration's jobs (Tb stages of pairs) fill just under Tb whole rounds of
+// 8 warps (Tb = 2: 254 cells, 255 pairs; 4: 252, 510; 8: 248, 1020): a round
+// with a few pairs left over would cost a whole warp instruction per FP64
+// operation for them.
 template <int NDIM, int TB>
 struct Geo {
   static constexpr int TX = NDIM == 3 ? (TB == 2 ? 64 : TB == 4 ? 32 : 16)
                                       : 2 * ((128 * TB - TB * (TB - 1) / 2) / TB);
-  static constexpr int TY = NDIM == 3 ? (TB == 2 ? 32 : TX) : 1;
+  static constexpr int TY = NDIM == 3 ? (TB == 2 ? 16 : TX) : 1;
 };
 
-// One CTA per SM in 3D (the stage rings take 147-172 KB of shared memory)
-// with 24 warps, or 16 for the 27-point box, whose 27 weights stay in
-// registers; 8 warps in 2D, with several CTAs per SM.
-template <int NDIM, bool BOX>
-constexpr int temporal_threads() { return NDIM == 3 ? (BOX ? 512 : 768) : 256; }
-template <int NDIM, bool BOX>
-constexpr int temporal_min_blocks() { return NDIM == 3 ? 1 : 2; }
+// Stage schedule.  LAG = 2: stage s produces plane k - 2s in iteration k, so
+// no stage reads what another writes in the same iteration and one barrier
+// per input plane covers all stages (rings of 4 planes).  LAG = 1: stage s
+// produces plane k - s - 1, reading what stage s - 1 wrote just before, with
+// a barrier between stages (rings of 3 planes).  3D Tb = 2 takes LAG = 1: its
+// 72 KB of rings let three CTAs share an SM, whose barriers then overlap
+// (measured at 512^3: 77.5 GStencil/s against 74.9 for LAG = 2 at two CTAs per
+// SM and 67.5 at one).
+template <int NDIM, int TB>
+constexpr int temporal_lag() { return NDIM == 3 && TB == 2 ? 1 : 2; }
+
+// Threads per CTA and CTAs per SM.  3D Tb = 2: 8 warps, three CTAs per SM
+// (two for the 27-point box, whose 27 weights stay in registers); 3D Tb >= 4:
+// one CTA of 16 warps (its rings take 162-172 KB); 2D: 8 warps, several CTAs.
+template <int NDIM, bool BOX, int TB>
+constexpr int temporal_threads() { return NDIM == 3 && TB > 2 ? 512 : 256; }
+template <int NDIM, bool BOX, int TB>
+constexpr int temporal_min_blocks() { return NDIM == 3 ? (TB == 2 ? (BOX ? 2 : 3) : 1) : 2; }
 
 // Shared-memory layout.  Plane coordinates (py, px) cover the tile and a halo
 // of Tb cells per side.  Stage q = 0 .. Tb-1 (q = 0: the input) keeps a ring
-// of 4 planes over its region [q, PX-q) x [q, PY-q) (2D: the row [q, PX-q)),
-// stored compactly with row stride W(q): three planes that stage q+1 reads
-// and the one stage q is writing (or, for the input, landing).
+// of planes over its region [q, PX-q) x [q, PY-q) (2D: the row [q, PX-q)),
+// stored compactly with row stride W(q): the input ring holds 4 (three that
+// stage 1 reads and one landing), the stage rings 4 (LAG = 2: three read by
+// the next stage, one being written) or 3 (LAG = 1).
 template <int NDIM, int TB>
 struct Lay {
   static constexpr int PX = Geo<NDIM, TB>::TX + 2 * TB;
   static constexpr int PY = NDIM == 3 ? Geo<NDIM, TB>::TY + 2 * TB : 1;
   static constexpr int P = PX * PY;
-  static constexpr int kRing = 4;
+  static constexpr int kIn = 4;
+  static constexpr int kRing = temporal_lag<NDIM, TB>() == 2 ? 4 : 3;
   __host__ __device__ static constexpr int W(int q) { return PX - 2 * q; }
   __host__ __device__ static constexpr int H(int q) { return NDIM == 3 ? PY - 2 * q : 1; }
   __host__ __device__ static constexpr int N(int q) { return W(q) * H(q); }
-  // first double of stage q's ring: 4 * (N(0) + ... + N(q-1)), in closed form
-  __host__ __device__ static constexpr int off(int q) {
-    return NDIM == 3 ? kRing * (q * PX * PY - (PX + PY) * q * (q - 1) + 2 * (q - 1) * q * (2 * q - 1) / 3)
-                     : kRing * (q * PX - q * (q - 1));
+  // N(0) + ... + N(q-1), in closed form
+  __host__ __device__ static constexpr int cells_before(int q) {
+    return NDIM == 3 ? q * PX * PY - (PX + PY) * q * (q - 1) + 2 * (q - 1) * q * (2 * q - 1) / 3
+                     : q * PX - q * (q - 1);
   }
+  // first double of stage q's ring
+  __host__ __device__ static constexpr int off(int q) {
+    return q == 0 ? 0 : kIn * P + kRing * (cells_before(q) - P);
+  }
+  // ring slot of plane i of stage q
+  __host__ __device__ static constexpr int slot(int q, int i) { return q == 0 || kRing == 4 ? (i & 3) : i % 3; }
   static constexpr size_t bytes = (size_t)off(TB) * sizeof(double);
   // jobs: pairs of y-neighbours in 3D (H(q) is even: a pair never leaves the
   // region, and a warp reads 32 consecutive doubles of a row per load), pairs
@@ -171,11 +190,75 @@ __device__ __forceinline__ void pair_update(const RegWeights<NT>& W, const doubl
   }
 }
 
+// Pair c of stage s's region, plane i: computed from the three planes of
+// stage s-1 around it and written to stage s's ring, or (s = Tb) to global
+// memory.
 template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
-__global__ void __launch_bounds__(temporal_threads<NDIM, BOX>(), temporal_min_blocks<NDIM, BOX>())
+__device__ __forceinline__ void stage_pair(const TParams& P, const RegWeights<NT>& W, double* sm, int s,
+                                           int c, int i, int wa, int y0, int x0) {
+  using L = Lay<NDIM, TB>;
+  const int ws = L::W(s);
+  int qy, qx;  // the pair's first cell, as an offset in stage s's region
+  if (NDIM == 3) {
+    qy = c / ws;
+    qx = c - qy * ws;
+    qy *= 2;
+  } else {
+    qy = 0;
+    qx = 2 * c;
+  }
+  const int sn = L::N(s - 1);
+  const double* src = sm + L::off(s - 1);
+  const double* pm = src + L::slot(s - 1, i - 1) * sn;
+  const double* p0 = src + L::slot(s - 1, i) * sn;
+  const double* pp = src + L::slot(s - 1, i + 1) * sn;
+  double a0, a1;
+  pair_update<NDIM, NT, BOX>(W, pm, p0, pp, L::W(s - 1), NDIM == 3 ? qy + 1 : 0, qx + 1, a0, a1);
+  const int w = wa - TB + i;
+  const int x = x0 - TB + s + qx;
+  const int y = NDIM == 3 ? y0 - TB + s + qy : 0;
+  if (s < TB) {
+    double* out = sm + L::off(s) + L::slot(s, i) * L::N(s) + qy * ws + qx;
+    if (NDIM == 3) {
+      if (!PERIODIC) {
+        const bool g = (unsigned)w >= (unsigned)P.nw || (unsigned)x >= (unsigned)P.nx;
+        if (g || (unsigned)y >= (unsigned)P.ny) a0 = 0.0;
+        if (g || (unsigned)(y + 1) >= (unsigned)P.ny) a1 = 0.0;
+      }
+      out[0] = a0;
+      out[ws] = a1;
+    } else {
+      if (!PERIODIC) {
+        const bool g = (unsigned)w >= (unsigned)P.nw;
+        if (g || (unsigned)x >= (unsigned)P.nx) a0 = 0.0;
+        if (g || (unsigned)(x + 1) >= (unsigned)P.nx) a1 = 0.0;
+      }
+      *reinterpret_cast<double2*>(out) = make_double2(a0, a1);  // 16-byte aligned
+    }
+  } else if (NDIM == 3) {
+    // the tile itself (x >= 0, y >= 0, w in range): straight to global memory
+    if (x < P.nx) {
+      double* g = P.dst + ((int64_t)w * P.ny + y) * P.nx + x;
+      if (y < P.ny) g[0] = a0;
+      if (y + 1 < P.ny) g[P.nx] = a1;
+    }
+  } else {
+    double* g = P.dst + (int64_t)w * P.nx + x;
+    if (x + 1 < P.nx && (reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+      *reinterpret_cast<double2*>(g) = make_double2(a0, a1);
+    } else {
+      if (x < P.nx) g[0] = a0;
+      if (x + 1 < P.nx) g[1] = a1;
+    }
+  }
+}
+
+template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
+__global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_min_blocks<NDIM, BOX, TB>())
     k_temporal(const TParams P) {
   using L = Lay<NDIM, TB>;
-  constexpr int NTH = temporal_threads<NDIM, BOX>();
+  constexpr int NTH = temporal_threads<NDIM, BOX, TB>();
+  constexpr int LAG = temporal_lag<NDIM, TB>();
   constexpr int TX = Geo<NDIM, TB>::TX, TY = Geo<NDIM, TB>::TY;
   extern __shared__ __align__(16) double sm[];
   RegWeights<NT> W;
@@ -193,80 +276,38 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, BOX>(), temporal_min_bl
     const int x0 = (tile % P.tiles_x) * TX;
     const int y0 = (tile / P.tiles_x) * TY;
     // input planes i = 0 .. nin-1 are streaming coordinates wa-TB .. wb+TB-1;
-    // stage s produces its planes i in [s, nin-s), plane i in iteration i + 2s
+    // stage s produces its planes i in [s, nin-s), plane i in iteration
+    // i + 2s (LAG = 2) or i + s + 1 (LAG = 1)
     const int nin = (wb - wa) + 2 * TB;
     load_plane<NDIM, TB, PERIODIC, NTH>(sm, P, wa - TB, y0, x0);
     cp_async_commit();
-    for (int k = 1; k < nin + TB; ++k) {
+    const int k_end = LAG == 2 ? nin + TB : nin + 1;
+    for (int k = 1; k < k_end; ++k) {
       cp_async_wait_all();  // input plane k-1 has landed
       __syncthreads();      // ... for every thread, and iteration k-1's stage planes are written
       if (k < nin) load_plane<NDIM, TB, PERIODIC, NTH>(sm + (k & 3) * L::P, P, wa - TB + k, y0, x0);
       cp_async_commit();
-      // the flat job list of this iteration: stage s contributes its pairs
-      // when its plane k - 2s is in range, i.e. for s_lo <= s <= s_hi
-      const int s_lo = max(1, k - nin + 1), s_hi = min(TB, k / 3);
-      int njobs = 0;
-      for (int s = s_lo; s <= s_hi; ++s) njobs += L::pairs(s);
-      for (int j = threadIdx.x; j < njobs; j += NTH) {
-        int s = s_lo, c = j;
-        while (c >= L::pairs(s)) {
-          c -= L::pairs(s);
-          ++s;
+      if (LAG == 2) {
+        // one flat job list: stage s contributes its pairs when its plane
+        // k - 2s is in range, i.e. for s_lo <= s <= s_hi
+        const int s_lo = max(1, k - nin + 1), s_hi = min(TB, k / 3);
+        int njobs = 0;
+        for (int s = s_lo; s <= s_hi; ++s) njobs += L::pairs(s);
+        for (int j = threadIdx.x; j < njobs; j += NTH) {
+          int s = s_lo, c = j;
+          while (c >= L::pairs(s)) {
+            c -= L::pairs(s);
+            ++s;
+          }
+          stage_pair<NDIM, NT, BOX, PERIODIC, TB>(P, W, sm, s, c, k - 2 * s, wa, y0, x0);
         }
-        const int i = k - 2 * s;
-        const int ws = L::W(s);
-        int qy, qx;  // the pair's first cell, as an offset in stage s's region
-        if (NDIM == 3) {
-          qy = c / ws;
-          qx = c - qy * ws;
-          qy *= 2;
-        } else {
-          qy = 0;
-          qx = 2 * c;
-        }
-        const int sn = L::N(s - 1);
-        const double* src = sm + L::off(s - 1);
-        const double* pm = src + ((i - 1) & 3) * sn;
-        const double* p0 = src + (i & 3) * sn;
-        const double* pp = src + ((i + 1) & 3) * sn;
-        double a0, a1;
-        pair_update<NDIM, NT, BOX>(W, pm, p0, pp, L::W(s - 1), NDIM == 3 ? qy + 1 : 0, qx + 1, a0, a1);
-        const int w = wa - TB + i;
-        const int x = x0 - TB + s + qx;
-        const int y = NDIM == 3 ? y0 - TB + s + qy : 0;
-        if (s < TB) {
-          double* out = sm + L::off(s) + (i & 3) * L::N(s) + qy * ws + qx;
-          if (NDIM == 3) {
-            if (!PERIODIC) {
-              const bool g = (unsigned)w >= (unsigned)P.nw || (unsigned)x >= (unsigned)P.nx;
-              if (g || (unsigned)y >= (unsigned)P.ny) a0 = 0.0;
-              if (g || (unsigned)(y + 1) >= (unsigned)P.ny) a1 = 0.0;
-            }
-            out[0] = a0;
-            out[ws] = a1;
-          } else {
-            if (!PERIODIC) {
-              const bool g = (unsigned)w >= (unsigned)P.nw;
-              if (g || (unsigned)x >= (unsigned)P.nx) a0 = 0.0;
-              if (g || (unsigned)(x + 1) >= (unsigned)P.nx) a1 = 0.0;
-            }
-            *reinterpret_cast<double2*>(out) = make_double2(a0, a1);  // 16-byte aligned
-          }
-        } else if (NDIM == 3) {
-          // the tile itself (x >= 0, y >= 0, w in range): straight to global memory
-          if (x < P.nx) {
-            double* g = P.dst + ((int64_t)w * P.ny + y) * P.nx + x;
-            if (y < P.ny) g[0] = a0;
-            if (y + 1 < P.ny) g[P.nx] = a1;
-          }
-        } else {
-          double* g = P.dst + (int64_t)w * P.nx + x;
-          if (x + 1 < P.nx && (reinterpret_cast<uintptr_t>(g) & 15) == 0) {
-            *reinterpret_cast<double2*>(g) = make_double2(a0, a1);
-          } else {
-            if (x < P.nx) g[0] = a0;
-            if (x + 1 < P.nx) g[1] = a1;
-          }
+      } else {
+        // stage by stage: plane k - s - 1 is in range for s <= (k - 1) / 2
+        const int s_hi = min(TB, (k - 1) / 2);
+        for (int s = 1; s <= s_hi; ++s) {
+          if (s > 1) __syncthreads();  // stage s-1's plane of this iteration is written
+          for (int j = threadIdx.x; j < L::pairs(s); j += NTH)
+            stage_pair<NDIM, NT, BOX, PERIODIC, TB>(P, W, sm, s, j, k - s - 1, wa, y0, x0);
         }
       }
     }
@@ -278,7 +319,7 @@ template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
 cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, double* dst, int sms,
                       cudaStream_t stream) {
   using L = Lay<NDIM, TB>;
-  constexpr int NTH = temporal_threads<NDIM, BOX>();
+  constexpr int NTH = temporal_threads<NDIM, BOX, TB>();
   static_assert(L::bytes <= 227 * 1024, "stage rings exceed shared memory");
   auto kern = k_temporal<NDIM, NT, BOX, PERIODIC, TB>;
   static std::atomic<int> cache[kMaxDeviceOrdinals];
