@@ -35,38 +35,40 @@ namespace {
 constexpr int kThreads = 256;  // 1D kernel
 
 // Output tile (y, x) of the 2D/3D kernel.  3D: Tb = 2: 16 x 64 (1.08x the
-// single-step work in halo recompute); Tb = 4: 32 x 32 (1.20x), the tile with
-// the shortest perimeter per cell whose stage rings fit in shared memory;
-// Tb = 8: 16 x 16 (2.15x).  2D: a row segment of about 256 cells, cut so that
+// single-step work in halo recompute; the 27-point box: 32 x 64, 1.05x);
+// Tb = 4: 32 x 32 (1.20x), the tile with the shortest perimeter per cell
+// whose stage rings fit in shared memory; Tb = 8: 16 x 16 (2.15x).  2D: a row segment of about 256 cells, cut so that
 // one iteration's jobs (Tb stages of pairs) fill just under Tb whole rounds of
 // 8 warps (Tb = 2: 254 cells, 255 pairs; 4: 252, 510; 8: 248, 1020): a round
 // with a few pairs left over would cost a whole warp instruction per FP64
 // operation for them.
-template <int NDIM, int TB>
+template <int NDIM, int TB, bool BOX>
 struct Geo {
   static constexpr int TX = NDIM == 3 ? (TB == 2 ? 64 : TB == 4 ? 32 : 16)
                                       : 2 * ((128 * TB - TB * (TB - 1) / 2) / TB);
-  static constexpr int TY = NDIM == 3 ? (TB == 2 ? 16 : TX) : 1;
+  static constexpr int TY = NDIM == 3 ? (TB == 2 ? (BOX ? 32 : 16) : TX) : 1;
 };
 
 // Stage schedule.  LAG = 2: stage s produces plane k - 2s in iteration k, so
 // no stage reads what another writes in the same iteration and one barrier
 // per input plane covers all stages (rings of 4 planes).  LAG = 1: stage s
 // produces plane k - s - 1, reading what stage s - 1 wrote just before, with
-// a barrier between stages (rings of 3 planes).  3D Tb = 2 takes LAG = 1: its
-// 72 KB of rings let three CTAs share an SM, whose barriers then overlap
-// (measured at 512^3: 77.5 GStencil/s against 74.9 for LAG = 2 at two CTAs per
-// SM and 67.5 at one).
-template <int NDIM, int TB>
-constexpr int temporal_lag() { return NDIM == 3 && TB == 2 ? 1 : 2; }
+// a barrier between stages (rings of 3 planes).  The 3D star at Tb = 2 takes
+// LAG = 1: its 72 KB of rings let three CTAs share an SM, whose barriers then
+// overlap (measured at 512^3: 77.2 GStencil/s against 74.9 for LAG = 2 at two
+// CTAs per SM and 67.5 at one).  The 27-point box keeps its 27 weights in
+// registers, which leaves room for one CTA of 16 warps: LAG = 2 (20.5 against
+// 19.9 GStencil/s at 384^3).
+template <int NDIM, int TB, bool BOX>
+constexpr int temporal_lag() { return NDIM == 3 && TB == 2 && !BOX ? 1 : 2; }
 
-// Threads per CTA and CTAs per SM.  3D Tb = 2: 8 warps, three CTAs per SM
-// (two for the 27-point box, whose 27 weights stay in registers); 3D Tb >= 4:
-// one CTA of 16 warps (its rings take 162-172 KB); 2D: 8 warps, several CTAs.
+// Threads per CTA and CTAs per SM.  3D star at Tb = 2: 8 warps, three CTAs per
+// SM; other 3D kernels: one CTA of 16 warps (rings of 147-172 KB); 2D: 8
+// warps, several CTAs.
 template <int NDIM, bool BOX, int TB>
-constexpr int temporal_threads() { return NDIM == 3 && TB > 2 ? 512 : 256; }
+constexpr int temporal_threads() { return NDIM == 3 && (TB > 2 || BOX) ? 512 : 256; }
 template <int NDIM, bool BOX, int TB>
-constexpr int temporal_min_blocks() { return NDIM == 3 ? (TB == 2 ? (BOX ? 2 : 3) : 1) : 2; }
+constexpr int temporal_min_blocks() { return NDIM == 3 ? (TB == 2 && !BOX ? 3 : 1) : 2; }
 
 // Shared-memory layout.  Plane coordinates (py, px) cover the tile and a halo
 // of Tb cells per side.  Stage q = 0 .. Tb-1 (q = 0: the input) keeps a ring
@@ -74,13 +76,13 @@ constexpr int temporal_min_blocks() { return NDIM == 3 ? (TB == 2 ? (BOX ? 2 : 3
 // stored compactly with row stride W(q): the input ring holds 4 (three that
 // stage 1 reads and one landing), the stage rings 4 (LAG = 2: three read by
 // the next stage, one being written) or 3 (LAG = 1).
-template <int NDIM, int TB>
+template <int NDIM, int TB, bool BOX>
 struct Lay {
-  static constexpr int PX = Geo<NDIM, TB>::TX + 2 * TB;
-  static constexpr int PY = NDIM == 3 ? Geo<NDIM, TB>::TY + 2 * TB : 1;
+  static constexpr int PX = Geo<NDIM, TB, BOX>::TX + 2 * TB;
+  static constexpr int PY = NDIM == 3 ? Geo<NDIM, TB, BOX>::TY + 2 * TB : 1;
   static constexpr int P = PX * PY;
   static constexpr int kIn = 4;
-  static constexpr int kRing = temporal_lag<NDIM, TB>() == 2 ? 4 : 3;
+  static constexpr int kRing = temporal_lag<NDIM, TB, BOX>() == 2 ? 4 : 3;
   __host__ __device__ static constexpr int W(int q) { return PX - 2 * q; }
   __host__ __device__ static constexpr int H(int q) { return NDIM == 3 ? PY - 2 * q : 1; }
   __host__ __device__ static constexpr int N(int q) { return W(q) * H(q); }
@@ -126,9 +128,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Issues the copies of input plane w (global streaming coordinate) of the tile
 // whose output origin is (y0, x0) into `slot`.
-template <int NDIM, int TB, bool PERIODIC, int NTH>
+template <int NDIM, int TB, bool BOX, bool PERIODIC, int NTH>
 __device__ __forceinline__ void load_plane(double* slot, const TParams& P, int w, int y0, int x0) {
-  using L = Lay<NDIM, TB>;
+  using L = Lay<NDIM, TB, BOX>;
   bool win = true;
   int ww = w;
   if (PERIODIC) ww = wrapn(w, P.nw);
@@ -196,7 +198,7 @@ __device__ __forceinline__ void pair_update(const RegWeights<NT>& W, const doubl
 template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
 __device__ __forceinline__ void stage_pair(const TParams& P, const RegWeights<NT>& W, double* sm, int s,
                                            int c, int i, int wa, int y0, int x0) {
-  using L = Lay<NDIM, TB>;
+  using L = Lay<NDIM, TB, BOX>;
   const int ws = L::W(s);
   int qy, qx;  // the pair's first cell, as an offset in stage s's region
   if (NDIM == 3) {
@@ -256,10 +258,10 @@ __device__ __forceinline__ void stage_pair(const TParams& P, const RegWeights<NT
 template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
 __global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_min_blocks<NDIM, BOX, TB>())
     k_temporal(const TParams P) {
-  using L = Lay<NDIM, TB>;
+  using L = Lay<NDIM, TB, BOX>;
   constexpr int NTH = temporal_threads<NDIM, BOX, TB>();
-  constexpr int LAG = temporal_lag<NDIM, TB>();
-  constexpr int TX = Geo<NDIM, TB>::TX, TY = Geo<NDIM, TB>::TY;
+  constexpr int LAG = temporal_lag<NDIM, TB, BOX>();
+  constexpr int TX = Geo<NDIM, TB, BOX>::TX, TY = Geo<NDIM, TB, BOX>::TY;
   extern __shared__ __align__(16) double sm[];
   RegWeights<NT> W;
   W.load(P.wdev);
@@ -279,13 +281,13 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_mi
     // stage s produces its planes i in [s, nin-s), plane i in iteration
     // i + 2s (LAG = 2) or i + s + 1 (LAG = 1)
     const int nin = (wb - wa) + 2 * TB;
-    load_plane<NDIM, TB, PERIODIC, NTH>(sm, P, wa - TB, y0, x0);
+    load_plane<NDIM, TB, BOX, PERIODIC, NTH>(sm, P, wa - TB, y0, x0);
     cp_async_commit();
     const int k_end = LAG == 2 ? nin + TB : nin + 1;
     for (int k = 1; k < k_end; ++k) {
       cp_async_wait_all();  // input plane k-1 has landed
       __syncthreads();      // ... for every thread, and iteration k-1's stage planes are written
-      if (k < nin) load_plane<NDIM, TB, PERIODIC, NTH>(sm + (k & 3) * L::P, P, wa - TB + k, y0, x0);
+      if (k < nin) load_plane<NDIM, TB, BOX, PERIODIC, NTH>(sm + (k & 3) * L::P, P, wa - TB + k, y0, x0);
       cp_async_commit();
       if (LAG == 2) {
         // one flat job list: stage s contributes its pairs when its plane
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_mi
 template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
 cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, double* dst, int sms,
                       cudaStream_t stream) {
-  using L = Lay<NDIM, TB>;
+  using L = Lay<NDIM, TB, BOX>;
   constexpr int NTH = temporal_threads<NDIM, BOX, TB>();
   static_assert(L::bytes <= 227 * 1024, "stage rings exceed shared memory");
   auto kern = k_temporal<NDIM, NT, BOX, PERIODIC, TB>;
@@ -337,8 +339,8 @@ cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, doub
   P.nw = NDIM == 3 ? g.nz : g.ny;
   P.ny = g.ny;
   P.nx = g.nx;
-  P.tiles_x = (g.nx + Geo<NDIM, TB>::TX - 1) / Geo<NDIM, TB>::TX;
-  P.tiles_y = NDIM == 3 ? (g.ny + Geo<NDIM, TB>::TY - 1) / Geo<NDIM, TB>::TY : 1;
+  P.tiles_x = (g.nx + Geo<NDIM, TB, BOX>::TX - 1) / Geo<NDIM, TB, BOX>::TX;
+  P.tiles_y = NDIM == 3 ? (g.ny + Geo<NDIM, TB, BOX>::TY - 1) / Geo<NDIM, TB, BOX>::TY : 1;
   P.work = (long long)P.tiles_x * P.tiles_y * P.nw;
   P.wdev = wdev;
   long long grid = (long long)sms * occ;
