@@ -86,6 +86,9 @@ CASES = [
     ((13, 37, 70), 1, "star", DIRICHLET, 1, "stream", 3),
     ((8, 32, 128), 1, "box", PERIODIC, 1, "stream", 2),
     ((13, 37, 70), 1, "box", DIRICHLET, 2, "temporal", 5),
+    ((11, 37, 70), 1, "star", DIRICHLET, 2, "temporal", 5),     # 3D star, stage by stage
+    ((9, 37, 70), 1, "star", PERIODIC, 8, "temporal", 17),
+    ((7, 20, 33), 1, "box", DIRICHLET, 4, "temporal", 9),
     ((50, 300), 1, "star", PERIODIC, 8, "temporal", 19),
     ((5001,), 2, "star", DIRICHLET, 8, "temporal", 17),
     ((37, 53), 1, "star", DIRICHLET, 1, "persistent", 5),

@@ -183,6 +183,36 @@ def test_parity_full_size_windows(st, shape, radius, boundary, kind, T, seed):
     p.close()
 
 
+# The temporal kernel at the full sizes, for every Tb the plan autotuner
+# offers: windows against the oracle after two Tb-blocks and a remainder step.
+FULL_TEMPORAL = [
+    ((512, 512, 512), PERIODIC, "heat", synth.SEED_HEAT3D),
+    ((384, 384, 384), DIRICHLET, "box_rand", synth.SEED_BOX3D),
+    ((16384, 16384), PERIODIC, "box_eq", synth.SEED_BOX2D),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape,boundary,kind,seed", FULL_TEMPORAL)
+def test_temporal_full_size_windows(st, shape, boundary, kind, seed):
+    import torch
+    w = weights_for(kind, len(shape), 1, seed)
+    u0 = synth.normal(seed, shape) if kind == "box_rand" else synth.uniform(seed, shape)
+    g = torch.empty(shape, dtype=torch.float64, device="cuda")
+    p = st.Plan(shape, 1, w, boundary)
+    for Tb in (2, 4, 8):
+        T = 2 * Tb + 1
+        p.set_tuning(Tb, st.VARIANT_TEMPORAL)
+        g.copy_(torch.from_numpy(u0))
+        p.run(g, T)
+        torch.cuda.synchronize()
+        for lo, hi in window_boxes(shape):
+            ref = oracle.run_window(u0, w, 1, boundary, T, lo, hi)
+            sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+            assert normwise_rel(g[sl].cpu().numpy(), ref) <= TOL, (Tb, lo, hi)
+    p.close()
+
+
 @pytest.mark.slow
 def test_full_size_512_cube_sine_mode_closed_form(st):
     """512^3 periodic heat, T=1000: by linearity run(r + m) - run(r) = lam^T m
