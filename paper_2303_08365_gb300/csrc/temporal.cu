@@ -72,70 +72,36 @@ constexpr int temporal_min_blocks() { return NDIM == 3 ? (TB == 2 && !BOX ? 3 : 
 
 // Shared-memory layout.  Plane coordinates (py, px) cover the tile and a halo
 // of Tb cells per side.  Stage q = 0 .. Tb-1 (q = 0: the input) keeps a ring
-// of planes over its region [q, PX-q) x [q, PY-q) (2D: the row [q, PX-q)):
-// the input ring holds 4 (three that stage 1 reads and one landing), the
-// stage rings 4 (LAG = 2: three read by the next stage, one being written) or
-// 3 (LAG = 1).  With LAG = 2 a 3D plane is stored with row stride S(q) >=
-// W(q), padded so that 2 S(q) - W(q+1) is a multiple of 16 doubles: the 32
-// pair jobs of a warp of stage q+1 that run past the end of a row pair into
-// the next one then still read 32 different banks (16 for 8 bytes per lane
-// per wavefront).  LAG = 1 (16 x 64 tiles: few warps straddle a row) keeps
-// S(q) = W(q), so that three CTAs still fit an SM.  Offsets and strides are packed into 64-bit constants, so that
-// a job finds its stage's layout with shifts instead of loads.
+// of planes over its region [q, PX-q) x [q, PY-q) (2D: the row [q, PX-q)),
+// stored compactly with row stride W(q): the input ring holds 4 (three that
+// stage 1 reads and one landing), the stage rings 4 (LAG = 2: three read by
+// the next stage, one being written) or 3 (LAG = 1).
 template <int NDIM, int TB, bool BOX>
 struct Lay {
   static constexpr int PX = Geo<NDIM, TB, BOX>::TX + 2 * TB;
   static constexpr int PY = NDIM == 3 ? Geo<NDIM, TB, BOX>::TY + 2 * TB : 1;
+  static constexpr int P = PX * PY;
   static constexpr int kIn = 4;
   static constexpr int kRing = temporal_lag<NDIM, TB, BOX>() == 2 ? 4 : 3;
   __host__ __device__ static constexpr int W(int q) { return PX - 2 * q; }
   __host__ __device__ static constexpr int H(int q) { return NDIM == 3 ? PY - 2 * q : 1; }
-  // row stride of stage q's stored planes
-  __host__ __device__ static constexpr int S(int q) {
-    int st = W(q);
-    if (NDIM == 3 && kRing == 4 && q < TB)
-      while ((2 * st - W(q + 1)) % 16 != 0) ++st;
-    return st;
+  __host__ __device__ static constexpr int N(int q) { return W(q) * H(q); }
+  // N(0) + ... + N(q-1), in closed form
+  __host__ __device__ static constexpr int cells_before(int q) {
+    return NDIM == 3 ? q * PX * PY - (PX + PY) * q * (q - 1) + 2 * (q - 1) * q * (2 * q - 1) / 3
+                     : q * PX - q * (q - 1);
   }
-  __host__ __device__ static constexpr int NS(int q) { return S(q) * H(q); }  // doubles per stored plane
   // first double of stage q's ring
   __host__ __device__ static constexpr int off(int q) {
-    int o = 0;
-    for (int r = 0; r < q; ++r) o += (r == 0 ? kIn : kRing) * NS(r);
-    return o;
-  }
-  static constexpr size_t bytes = (size_t)off(TB) * sizeof(double);
-  static_assert(off(TB) < 65536 && (NDIM == 2 || S(0) < 256), "layout does not fit the packed tables");
-  __host__ __device__ static constexpr unsigned long long pack16(int q0) {
-    unsigned long long v = 0;
-    for (int r = 0; r < 4; ++r)
-      if (q0 + r <= TB) v |= (unsigned long long)off(q0 + r) << (16 * r);
-    return v;
-  }
-  __host__ __device__ static constexpr unsigned long long pack8() {
-    unsigned long long v = 0;
-    for (int r = 0; r < 8 && r <= TB; ++r) v |= (unsigned long long)(NDIM == 3 ? S(r) : 0) << (8 * r);
-    return v;
-  }
-  static constexpr unsigned long long kOffLo = pack16(0), kOffHi = pack16(4), kStride = pack8();
-  // the same, for a stage index known only at run time (q <= min(Tb, 7))
-  __host__ __device__ static constexpr int off_rt(int q) {
-    return (int)(((q < 4 ? kOffLo : kOffHi) >> (16 * (q & 3))) & 0xFFFF);
-  }
-  __host__ __device__ static constexpr int stride_rt(int q) {
-    return NDIM == 3 ? (int)((kStride >> (8 * q)) & 0xFF) : W(q);
-  }
-  __host__ __device__ static constexpr bool tables_ok() {
-    for (int q = 0; q <= TB && q < 8; ++q)
-      if (off_rt(q) != off(q) || stride_rt(q) != S(q)) return false;
-    return true;
+    return q == 0 ? 0 : kIn * P + kRing * (cells_before(q) - P);
   }
   // ring slot of plane i of stage q
   __host__ __device__ static constexpr int slot(int q, int i) { return q == 0 || kRing == 4 ? (i & 3) : i % 3; }
+  static constexpr size_t bytes = (size_t)off(TB) * sizeof(double);
   // jobs: pairs of y-neighbours in 3D (H(q) is even: a pair never leaves the
   // region, and a warp reads 32 consecutive doubles of a row per load), pairs
   // of x-neighbours in 2D (W(q) is even)
-  __host__ __device__ static constexpr int pairs(int q) { return W(q) * H(q) / 2; }
+  __host__ __device__ static constexpr int pairs(int q) { return N(q) / 2; }
 };
 
 struct TParams {
@@ -169,7 +135,7 @@ __device__ __forceinline__ void load_plane(double* slot, const TParams& P, int w
   int ww = w;
   if (PERIODIC) ww = wrapn(w, P.nw);
   else win = (unsigned)w < (unsigned)P.nw;
-  for (int c = threadIdx.x; c < L::PX * L::PY; c += NTH) {
+  for (int c = threadIdx.x; c < L::P; c += NTH) {
     const int px = c % L::PX, py = c / L::PX;
     int x = x0 - TB + px;
     int y = NDIM == 3 ? y0 - TB + py : 0;
@@ -183,7 +149,7 @@ __device__ __forceinline__ void load_plane(double* slot, const TParams& P, int w
     int64_t gi;
     if (NDIM == 3) gi = ((int64_t)(in ? ww : 0) * P.ny + (in ? y : 0)) * P.nx + (in ? x : 0);
     else gi = (int64_t)(in ? ww : 0) * P.nx + (in ? x : 0);
-    cp_async8(slot + py * L::S(0) + px, P.src + gi, in);
+    cp_async8(slot + c, P.src + gi, in);
   }
 }
 
@@ -243,20 +209,18 @@ __device__ __forceinline__ void stage_pair(const TParams& P, const RegWeights<NT
     qy = 0;
     qx = 2 * c;
   }
-  const int sw = L::stride_rt(s - 1);
-  const int sn = sw * L::H(s - 1);
-  const double* src = sm + L::off_rt(s - 1);
+  const int sn = L::N(s - 1);
+  const double* src = sm + L::off(s - 1);
   const double* pm = src + L::slot(s - 1, i - 1) * sn;
   const double* p0 = src + L::slot(s - 1, i) * sn;
   const double* pp = src + L::slot(s - 1, i + 1) * sn;
   double a0, a1;
-  pair_update<NDIM, NT, BOX>(W, pm, p0, pp, sw, NDIM == 3 ? qy + 1 : 0, qx + 1, a0, a1);
+  pair_update<NDIM, NT, BOX>(W, pm, p0, pp, L::W(s - 1), NDIM == 3 ? qy + 1 : 0, qx + 1, a0, a1);
   const int w = wa - TB + i;
   const int x = x0 - TB + s + qx;
   const int y = NDIM == 3 ? y0 - TB + s + qy : 0;
   if (s < TB) {
-    const int so = L::stride_rt(s);
-    double* out = sm + L::off_rt(s) + L::slot(s, i) * so * L::H(s) + qy * so + qx;
+    double* out = sm + L::off(s) + L::slot(s, i) * L::N(s) + qy * ws + qx;
     if (NDIM == 3) {
       if (!PERIODIC) {
         const bool g = (unsigned)w >= (unsigned)P.nw || (unsigned)x >= (unsigned)P.nx;
@@ -264,7 +228,7 @@ __device__ __forceinline__ void stage_pair(const TParams& P, const RegWeights<NT
         if (g || (unsigned)(y + 1) >= (unsigned)P.ny) a1 = 0.0;
       }
       out[0] = a0;
-      out[so] = a1;
+      out[ws] = a1;
     } else {
       if (!PERIODIC) {
         const bool g = (unsigned)w >= (unsigned)P.nw;
@@ -323,7 +287,7 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_mi
     for (int k = 1; k < k_end; ++k) {
       cp_async_wait_all();  // input plane k-1 has landed
       __syncthreads();      // ... for every thread, and iteration k-1's stage planes are written
-      if (k < nin) load_plane<NDIM, TB, BOX, PERIODIC, NTH>(sm + (k & 3) * L::NS(0), P, wa - TB + k, y0, x0);
+      if (k < nin) load_plane<NDIM, TB, BOX, PERIODIC, NTH>(sm + (k & 3) * L::P, P, wa - TB + k, y0, x0);
       cp_async_commit();
       if (LAG == 2) {
         // one flat job list: stage s contributes its pairs when its plane
@@ -359,7 +323,6 @@ cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, doub
   using L = Lay<NDIM, TB, BOX>;
   constexpr int NTH = temporal_threads<NDIM, BOX, TB>();
   static_assert(L::bytes <= 227 * 1024, "stage rings exceed shared memory");
-  static_assert(L::tables_ok(), "packed layout tables disagree with the layout");
   auto kern = k_temporal<NDIM, NT, BOX, PERIODIC, TB>;
   static std::atomic<int> cache[kMaxDeviceOrdinals];
   const int occ = cached_per_device(cache, [kern] {
