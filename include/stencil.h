@@ -125,9 +125,11 @@ int stencil_run_f32(stencil_plan p, float* d_grid, float* d_work, int64_t T, voi
  * sqrt(T); the last segment's states are kept by the forward sweep and never
  * recomputed.  ckpt_every = 1 keeps every state (no recompute, T + 10 grids
  * of scratch: 126 GiB for 256^3 and T = 1000, which an HBM3e part of 288 GB
- * holds).  ckpt_every = 0 chooses: every state when those T + 10 grids fit
- * in half of the free device memory, else about sqrt(T).  The results do not
- * depend on the interval (bitwise).
+ * holds).  ckpt_every = 0 takes round(sqrt(T)).  The results do not depend on
+ * the interval (bitwise).  The plan keeps its adjoint scratch for the next
+ * call; a call that needs less than half of it, or stencil_destroy, frees it,
+ * and stencil_adjoint (which waits for the stream) frees a scratch more than
+ * twice the size the sqrt(T) interval would take before it returns.
  * d_grad_u0 and d_grad_kappa (device, caller-owned, same shape) are
  * overwritten; *h_loss (host) receives L and the call waits for the stream. */
 int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,
@@ -282,9 +284,28 @@ const char* stencil_variant_name(int variant);
  *   - The first call on a device looks up the array's device address and the
  *     kernel's occupancy with that device current; make that first call before
  *     any stream capture begins.
- * Asynchronous on cuda_stream; errors are reported by stencil_last_error. */
+ * Asynchronous on cuda_stream.  Argument and launch errors are returned at
+ * once (message in stencil_last_error).  The kernel's device-wide barrier is a
+ * bounded wait (2 s): if it gives up, the grid is left part-advanced and the
+ * kernel records STENCIL_ERR_TIMEOUT in a status word inside the array, which
+ * stencil_static_status returns. */
 int stencil_run_2d_static(int64_t ny, int64_t nx, const double* weights, int boundary,
                           double* d_grid, int64_t T, void* cuda_stream);
+
+/* Waits for cuda_stream and returns the status word of the last
+ * stencil_run_2d_static launch on the current device: STENCIL_OK, or
+ * STENCIL_ERR_TIMEOUT when its bounded barrier wait gave up (the word is then
+ * cleared).  Copies 4 bytes to the host; allocates nothing. */
+int stencil_static_status(void* cuda_stream);
+
+/* Failure-path self-test of the allocation-free entry: launches its kernel on
+ * a 1 x 64 grid held inside the static array with a device-wide barrier that
+ * waits for one block more than the launch has, so the wait can only end by
+ * its wall-time limit (limit_ms, at most 2000), then reads the status word.
+ * Returns STENCIL_ERR_TIMEOUT when the kernel gave up and reported it as
+ * designed.  Synchronous; allocates nothing; overwrites the array like any
+ * other call (serialise it with them). */
+int stencil_selftest_static_timeout(double limit_ms, void* cuda_stream);
 
 /* ---------------------------------------------------------- diagnostics */
 

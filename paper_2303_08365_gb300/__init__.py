@@ -80,6 +80,8 @@ SIGNATURES = [
     ("stencil_selftest_flag_timeout", ctypes.c_int, [ctypes.c_double, _VP]),
     ("stencil_run_2d_static", ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _DP, ctypes.c_int, _VP,
                                              ctypes.c_int64, _VP]),
+    ("stencil_static_status", ctypes.c_int, [_VP]),
+    ("stencil_selftest_static_timeout", ctypes.c_int, [ctypes.c_double, _VP]),
 ]
 
 _lib = None
@@ -293,6 +295,17 @@ def stencil_run_2d_static(grid, weights, boundary, T, stream=None):
         raise ValueError("weights must be a dense 3x3 array")
     _check(lib().stencil_run_2d_static(int(grid.shape[0]), int(grid.shape[1]), w.ctypes.data_as(_DP),
                                        int(boundary), _dev_ptr(grid, "grid"), int(T), _stream(stream)))
+
+
+def stencil_static_status(stream=None):
+    """Waits for the stream; the status word of the last allocation-free sweep."""
+    return lib().stencil_static_status(_stream(stream))
+
+
+def stencil_selftest_static_timeout(limit_ms=20.0, stream=None):
+    """Runs the allocation-free entry's bounded-wait failure path; returns the
+    status code (ERR_TIMEOUT when it behaved)."""
+    return lib().stencil_selftest_static_timeout(float(limit_ms), _stream(stream))
 
 
 def stencil_selftest_flag_timeout(limit_ms=20.0, stream=None):

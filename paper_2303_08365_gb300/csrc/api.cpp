@@ -881,18 +881,10 @@ int adjoint_core(stencil_plan_s* p, const double* d_u0, const double* d_kappa, d
   if (T < 0) return fail(STENCIL_ERR_ARG, "T must be >= 0");
   if (ckpt_every < 0) return fail(STENCIL_ERR_ARG, "ckpt_every must be >= 0");
   const size_t n = (size_t)p->cells();
-  int64_t c = ckpt_every;
-  if (c == 0) {
-    // automatic: keep every state (no recompute) when T + 10 grids fit in half
-    // of the free device memory -- on a 288 GB part that covers most runs --
-    // else checkpoint about every sqrt(T) steps
-    size_t free_b = 0, total_b = 0;
-    const double need = ((double)T + 10.0) * (double)n * sizeof(double);
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need <= 0.5 * (double)free_b)
-      c = 1;
-    else
-      c = std::max<int64_t>(1, (int64_t)llround(std::sqrt((double)T)));
-  }
+  // automatic interval: about sqrt(T), so the scratch grows with sqrt(T)
+  // (every state, c = 1, is an explicit choice of the caller)
+  const int64_t c_sqrt = std::max<int64_t>(1, (int64_t)llround(std::sqrt((double)T)));
+  int64_t c = ckpt_every == 0 ? c_sqrt : ckpt_every;
   if (T > 0 && c > T) c = T;
   const int64_t nck = T / c + 1;        // u at t = 0, c, 2c, ... (<= T)
   const int64_t nseg_states = c;        // u^{t0} .. u^{t0+c-1} of one segment
@@ -900,7 +892,9 @@ int adjoint_core(stencil_plan_s* p, const double* d_u0, const double* d_kappa, d
   // scratch: checkpoints, segment states, 2 lambda, 4 gradient accumulators,
   // the running state pair and the loss partials
   const size_t need = n * (size_t)(nck + nseg_states + 2 + 4 + 2) + (size_t)nblocks + 8;
-  if (p->d_adj && p->adj_cells < need) {
+  // the plan keeps its scratch between calls; one left from a call with a
+  // shorter interval (more states kept) than this one needs is given back
+  if (p->d_adj && (p->adj_cells < need || p->adj_cells > 2 * need)) {
     cudaFree(p->d_adj);
     p->d_adj = nullptr;
   }
@@ -976,6 +970,15 @@ int adjoint_core(stencil_plan_s* p, const double* d_u0, const double* d_kappa, d
     CUDA_TRY(cudaMemcpyAsync(h_loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s),
              "copying the loss");
     CUDA_TRY(cudaStreamSynchronize(s), "waiting for the adjoint");
+    // this form has waited for the stream: a scratch larger than the sqrt(T)
+    // interval's (every state kept, or nearly) is freed rather than retained
+    const int64_t nck_sqrt = T / std::min<int64_t>(std::max<int64_t>(T, 1), c_sqrt) + 1;
+    const size_t need_sqrt = n * (size_t)(nck_sqrt + c_sqrt + 2 + 4 + 2) + (size_t)nblocks + 8;
+    if (need > 2 * need_sqrt) {
+      cudaFree(p->d_adj);
+      p->d_adj = nullptr;
+      p->adj_cells = 0;
+    }
   }
   return STENCIL_OK;
 }

@@ -21,7 +21,7 @@
 namespace gbst {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = kBatchThreads;
 // A tile is a run of CPT * kThreads consecutive cells of one grid in row-major
 // order (CPT cells per thread, kThreads apart), so every warp is full except
 // at a grid's last tile: the FP64 unit charges a warp instruction the same

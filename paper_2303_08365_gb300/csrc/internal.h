@@ -156,6 +156,10 @@ struct BatchLaunch {
   long long spin_limit;   // bounded waits: wall-time limit in ns
   int barrier_blocks;     // arrivals a device-wide barrier waits for (0: the grid size)
 };
+// Threads per block of the batched kernel; a tile is cpt * kBatchThreads
+// consecutive cells, so the smallest tile (cpt = 1) holds kBatchThreads cells.
+constexpr int kBatchThreads = 256;
+constexpr int kBatchMinTileCells = kBatchThreads;
 // cpt: cells per thread of the kernel (1, 2 or 4); a tile holds cpt * 256 cells.
 cudaError_t launch_batched(const BatchLaunch& L, int grid_blocks, int cpt, cudaStream_t stream);
 int batched_block_size();

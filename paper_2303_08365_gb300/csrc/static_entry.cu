@@ -19,7 +19,10 @@
 //     without ordering) race on the array and must be serialised by the caller;
 //   - the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress) and the kernel's occupancy with that device
-//     current; make that first call before any stream capture begins.
+//     current; make that first call before any stream capture begins;
+//   - the kernel's device-wide barrier is a bounded wait: if it gives up it
+//     writes STENCIL_ERR_TIMEOUT into a status word inside the array, which
+//     stencil_static_status reads back (no allocation either).
 #include "../../include/stencil.h"
 #include "internal.h"
 
@@ -36,9 +39,10 @@ using namespace gbst;
 namespace {
 
 constexpr int64_t kMaxCells = STENCIL_STATIC_MAX_CELLS;
-// Tiles of the persistent kernel are runs of 512 consecutive cells: a grid of
-// at most kMaxCells cells has at most kMaxCells / 512 + 1 of them.
-constexpr int64_t kMaxTiles = kMaxCells / 512 + 1;
+// Tiles of the persistent kernel are runs of cpt * kBatchThreads consecutive
+// cells; sized for the smallest tile (cpt = 1), the list holds the tiles of
+// any grid within the limit whatever the kernel's cells per thread.
+constexpr int64_t kMaxTiles = kMaxCells / kBatchMinTileCells + 1;
 constexpr size_t kPartnerBytes = (size_t)kMaxCells * sizeof(double);
 constexpr size_t kItemOff = kPartnerBytes;
 constexpr size_t kTileOff = kItemOff + 256;
@@ -47,7 +51,8 @@ constexpr size_t kScratchBytes = kCtlOff + 256;
 
 static_assert(sizeof(BatchItemDev) <= 256, "item descriptor slot");
 
-// The reserved scratch: partner grid | item descriptor | tile list | barrier words.
+// The reserved scratch: partner grid | item descriptor | tile list | barrier
+// words ([0] arrivals, [1] generation, [2] status word of the last launch).
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
 struct DeviceSetup {
@@ -60,6 +65,14 @@ DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mu;
 
 int sfail(int code, const char* msg) { return set_error(code, msg); }
+
+// The persistent launch over the static scratch: fills the item descriptor and
+// tile list for a grid of `cells` cells, clears the barrier words on the
+// stream and launches `blocks` (at most the cooperative grid) blocks whose
+// device-wide barrier waits for `barrier_blocks` arrivals (0: the launch's own
+// block count) for at most `spin_limit_ns`.
+int static_launch(const DeviceSetup& s, const BatchItemDev& item, int64_t cells, int boundary,
+                  int barrier_blocks, long long spin_limit_ns, cudaStream_t stream);
 
 // Writes the item descriptor and the tile list (runs of `tc` consecutive
 // cells -- the persistent kernel's tile) into the static scratch on the device.
@@ -87,6 +100,41 @@ int setup_device(int dev, DeviceSetup& out) {
     s.ready = true;
   }
   out = s;
+  return STENCIL_OK;
+}
+
+int static_launch(const DeviceSetup& s, const BatchItemDev& item, int64_t cells, int boundary,
+                  int barrier_blocks, long long spin_limit_ns, cudaStream_t stream) {
+  // the tile list is a pure function of the shape: runs of tc consecutive cells
+  const int tc = batched_tile_cells(batched_default_cpt());
+  const int64_t ntiles = (cells + tc - 1) / tc;
+  if (ntiles > kMaxTiles) return sfail(STENCIL_ERR_UNSUPPORTED, "tile list exceeds the static scratch");
+  BatchTile* d_tiles = reinterpret_cast<BatchTile*>(s.base + kTileOff);
+  BatchItemDev* d_item = reinterpret_cast<BatchItemDev*>(s.base + kItemOff);
+  unsigned int* d_ctl = reinterpret_cast<unsigned int*>(s.base + kCtlOff);
+  {
+    const int fill_blocks = (int)((ntiles + 255) / 256 < 1024 ? (ntiles + 255) / 256 : 1024);
+    k_fill_static<<<fill_blocks, 256, 0, stream>>>(item, d_item, d_tiles, (int)ntiles, (int)cells, tc);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (cudaGetLastError() != cudaSuccess)
+      return sfail(STENCIL_ERR_CUDA, "launching the static scratch fill failed");
+  }
+  if (cudaMemsetAsync(d_ctl, 0, 4 * sizeof(unsigned int), stream) != cudaSuccess)
+    return sfail(STENCIL_ERR_CUDA, "clearing the barrier words failed");
+  BatchLaunch L;
+  L.items = d_item;
+  L.tiles = d_tiles;
+  L.ntiles = (int)ntiles;
+  L.max_T = item.T;
+  L.boundary = boundary;
+  L.barrier = d_ctl;
+  L.status = reinterpret_cast<int*>(d_ctl + 2);
+  L.spin_limit = spin_limit_ns;
+  L.barrier_blocks = barrier_blocks;
+  int blocks = s.blocks;
+  if (ntiles < blocks) blocks = (int)ntiles;
+  if (launch_batched(L, blocks, batched_default_cpt(), stream) != cudaSuccess)
+    return sfail(STENCIL_ERR_CUDA, "launching the persistent kernel failed");
   return STENCIL_OK;
 }
 
@@ -134,37 +182,62 @@ int stencil_run_2d_static(int64_t ny, int64_t nx, const double* weights, int bou
   item.w[2] = weights[4];  // centre
   item.w[3] = weights[5];  // east (x+1)
   item.w[4] = weights[7];  // south (y+1)
-  // the tile list is a pure function of the shape: runs of tc consecutive cells
-  const int tc = batched_tile_cells(batched_default_cpt());
-  const int64_t ntiles = (ny * nx + tc - 1) / tc;
-  if (ntiles > kMaxTiles) return sfail(STENCIL_ERR_UNSUPPORTED, "tile list exceeds the static scratch");
-  BatchTile* d_tiles = reinterpret_cast<BatchTile*>(s.base + kTileOff);
-  BatchItemDev* d_item = reinterpret_cast<BatchItemDev*>(s.base + kItemOff);
-  unsigned int* d_ctl = reinterpret_cast<unsigned int*>(s.base + kCtlOff);
-  {
-    const int fill_blocks = (int)((ntiles + 255) / 256 < 1024 ? (ntiles + 255) / 256 : 1024);
-    k_fill_static<<<fill_blocks, 256, 0, stream>>>(item, d_item, d_tiles, (int)ntiles, (int)(ny * nx), tc);
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (cudaGetLastError() != cudaSuccess)
-      return sfail(STENCIL_ERR_CUDA, "launching the static scratch fill failed");
-  }
-  if (cudaMemsetAsync(d_ctl, 0, 4 * sizeof(unsigned int), stream) != cudaSuccess)
-    return sfail(STENCIL_ERR_CUDA, "clearing the barrier words failed");
-  BatchLaunch L;
-  L.items = d_item;
-  L.tiles = d_tiles;
-  L.ntiles = (int)ntiles;
-  L.max_T = (int)T;
-  L.boundary = boundary;
-  L.barrier = d_ctl;
-  L.status = reinterpret_cast<int*>(d_ctl + 2);
-  L.spin_limit = kSpinLimitNs;
-  L.barrier_blocks = 0;
-  int blocks = s.blocks;
-  if (ntiles < blocks) blocks = (int)ntiles;
-  if (launch_batched(L, blocks, batched_default_cpt(), stream) != cudaSuccess)
-    return sfail(STENCIL_ERR_CUDA, "launching the persistent kernel failed");
-  return STENCIL_OK;
+  return static_launch(s, item, ny * nx, boundary, 0, kSpinLimitNs, stream);
+}
+
+int stencil_static_status(void* cuda_stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return sfail(STENCIL_ERR_CUDA, "no current CUDA device");
+  DeviceSetup s;
+  int rc = setup_device(dev, s);
+  if (rc) return rc;
+  if (cudaStreamSynchronize((cudaStream_t)cuda_stream) != cudaSuccess)
+    return sfail(STENCIL_ERR_CUDA, "waiting for the stream failed");
+  int* word = reinterpret_cast<int*>(s.base + kCtlOff) + 2;
+  int st = 0;
+  // a device-to-host copy into a stack variable: no allocation
+  if (cudaMemcpy(&st, word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return sfail(STENCIL_ERR_CUDA, "reading the static status word failed");
+  if (st == 0) return STENCIL_OK;
+  if (cudaMemset(word, 0, sizeof(int)) != cudaSuccess)
+    return sfail(STENCIL_ERR_CUDA, "clearing the static status word failed");
+  char buf[128];
+  snprintf(buf, sizeof(buf), "the static-scratch sweep reported status %d (a bounded wait gave up)", st);
+  return sfail(st, buf);
+}
+
+int stencil_selftest_static_timeout(double limit_ms, void* cuda_stream) {
+  if (!(limit_ms > 0.0) || limit_ms > 2000.0) return sfail(STENCIL_ERR_ARG, "limit_ms must be in (0, 2000]");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return sfail(STENCIL_ERR_CUDA, "no current CUDA device");
+  DeviceSetup s;
+  int rc = setup_device(dev, s);
+  if (rc) return rc;
+  // a 1 x 64 grid inside the static partner region (cells 64 .. 127; the
+  // kernel's partner is cells 0 .. 63), advanced by one block whose barrier
+  // counts on one block more than the launch has
+  double* partner = reinterpret_cast<double*>(s.base);
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  if (cudaMemsetAsync(partner, 0, 128 * sizeof(double), stream) != cudaSuccess)
+    return sfail(STENCIL_ERR_CUDA, "clearing the self-test grid failed");
+  BatchItemDev item;
+  memset(&item, 0, sizeof(item));
+  item.a = partner + 64;
+  item.b = partner;
+  item.ny = 1;
+  item.nx = 64;
+  item.T = 2;
+  item.w[2] = 1.0;
+  DeviceSetup one = s;
+  one.blocks = 1;
+  rc = static_launch(one, item, 64, STENCIL_DIRICHLET_ZERO, 2, (long long)(limit_ms * 1e6), stream);
+  if (rc) return rc;
+  rc = stencil_static_status(cuda_stream);
+  if (rc == STENCIL_ERR_TIMEOUT) return rc;
+  if (rc == STENCIL_OK) return sfail(STENCIL_ERR_CUDA, "the bounded wait did not report a timeout");
+  return rc;
 }
 
 }  // extern "C"

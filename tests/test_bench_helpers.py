@@ -57,3 +57,22 @@ def test_variant_kernel_names():
     assert bench.variant_kernel("stream", 2) == "stream2d"
     assert bench.variant_kernel("persistent", 2) == "batched"
     assert bench.variant_kernel("temporal", 3) == "temporal"
+
+
+def test_frac_basis_for_shared_partial_sums_and_hbm_bound():
+    """The equal-weight 9-point box issues 4.25 FP64 instructions per cell
+    while F = 17 credits 9: `frac` is then the executed-instruction fraction
+    (never above 1 for a kernel under the FP64 peak), with the basis named."""
+    peak = 1.256
+    cells, T = 16384 ** 2, 1000
+    rate = 140.0  # GStencil/s, as measured
+    ms = cells * T / (rate * 1e9) * 1e3
+    r = bench.roofline("box2d-9pt", cells, T, ms, T, peak, "stream2d")
+    assert r["bound"] == "alu"
+    assert r["frac"] == pytest.approx(r["fp64_pipe_frac"], rel=1e-6)
+    assert r["frac"] < 1.0 and "shares partial sums" in r["frac_basis"]
+    assert r["frac_of_stated_roofline"] <= 1.0 and "stated_roofline_note" in r
+    # a hypothetical workload where the HBM term binds is labelled "hbm"
+    h = bench.roofline("heat1d-3pt", 10 ** 7, 1, 1.0, 1, 1000.0, "temporal", bytes_per_cell=16)
+    assert h["bound"] == "hbm" and h["unit"] == "GB/s"
+    assert h["frac"] == pytest.approx(16 * 10 ** 7 / 1e-3 / 1e9 / bench.HBM_GBS, rel=1e-3)

@@ -65,8 +65,9 @@ def test_replay_advances_again(st):
 
 @pytest.mark.slow
 def test_full_96_item_batch(st):
-    """The 96-grid workload: every item bitwise equal to its single-grid run;
-    a few small items against the oracle."""
+    """The 96-grid workload: items bitwise equal to their single-grid runs,
+    the smallest against the whole-grid oracle and the two largest on oracle
+    windows at their full T."""
     import torch
     items = synth.batch_items(synth.SEED_BATCH)
     grids = [synth.uniform(synth.SEED_BATCH + 1000 + i, (ny, nx)) for i, (ny, nx, _, _) in enumerate(items)]
@@ -82,6 +83,16 @@ def test_full_96_item_batch(st):
         ny, nx, a, T = items[i]
         ref = oracle.run(grids[i], synth.heat_weights(2, a), 1, DIRICHLET, T, nthreads=0)
         assert normwise_rel(dev[i].cpu().numpy(), ref) <= TOL
+    # the two largest items at their full T: windows from the oracle's light
+    # cone at a corner (ghost cells on two sides), on an edge and inside
+    for i in order[-2:]:
+        ny, nx, a, T = items[i]
+        got = dev[i].cpu().numpy()
+        w = synth.heat_weights(2, a)
+        for lo in ((0, 0), (0, nx // 2), (ny // 3, nx // 5), (ny - 6, nx - 10)):
+            hi = (min(ny, lo[0] + 6), min(nx, lo[1] + 10))
+            ref = oracle.run_window(grids[i], w, 1, DIRICHLET, T, lo, hi)
+            assert normwise_rel(got[lo[0]:hi[0], lo[1]:hi[1]], ref) <= TOL, (i, lo)
     b.close()
 
 

@@ -87,6 +87,39 @@ def test_checkpoint_interval_is_bitwise_neutral(st):
 
 
 @pytest.mark.slow
+def test_forward_parity_at_config_size(st):
+    """The 256^3 periodic var-coef workload, in the launch configuration the
+    benchmark times: three steps of the GPU sweep against the oracle element by
+    element over all 16.8 million cells."""
+    shape = (256, 256, 256)
+    u0, kappa, _, dt = inputs(shape, synth.SEED_ADJOINT)
+    T = 3
+    ref = oracle.varcoef_run(u0, kappa, dt, PERIODIC, T, nthreads=0)
+    p = st.Plan.varcoef(shape, PERIODIC)
+    g = cuda(u0)
+    p.run(g, T, cuda(kappa), dt)
+    assert normwise_rel(g.cpu().numpy(), ref) <= TOL
+    p.close()
+
+
+@pytest.mark.slow
+def test_adjoint_parity_at_config_size(st):
+    """The 256^3 periodic adjoint workload (checkpoint interval 32 as in the
+    benchmark; T = 2 keeps the oracle's reverse sweep to seconds): loss and
+    both gradients against the oracle's adjoint over every cell."""
+    shape = (256, 256, 256)
+    u0, kappa, target, dt = inputs(shape, synth.SEED_ADJOINT)
+    T = 2
+    rl, rgu, rgk = oracle.varcoef_adjoint(u0, kappa, dt, target, PERIODIC, T, nthreads=0)
+    p = st.Plan.varcoef(shape, PERIODIC)
+    loss, gu, gk = p.adjoint(cuda(u0), cuda(kappa), dt, cuda(target), T, ckpt_every=32)
+    assert abs(loss - rl) <= TOL * abs(rl)
+    assert normwise_rel(gu.cpu().numpy(), rgu) <= TOL
+    assert normwise_rel(gk.cpu().numpy(), rgk) <= TOL
+    p.close()
+
+
+@pytest.mark.slow
 def test_full_size_finite_differences(st):
     """256^3, T=1000, checkpoints every 32: directional derivatives of the
     loss along random directions match the adjoint gradient."""
