@@ -234,10 +234,22 @@ typedef enum {
   STENCIL_VARIANT_TEMPORAL = 3,   /* Tb fused steps per launch (overlapped
                                      tiles): Tb 2, 4 or 8 (1D; 2D and 3D
                                      radius 1) */
-  STENCIL_VARIANT_PERSISTENT = 4  /* one launch for all T steps (2D radius 1):
+  STENCIL_VARIANT_PERSISTENT = 4, /* one launch for all T steps (2D radius 1):
                                      Tb = 1 with a device-wide barrier per step
                                      (5-point star), Tb > 1 with Tb steps in
                                      shared memory per exchange */
+  STENCIL_VARIANT_EXCHANGE = 5    /* Tb fused steps per launch with no
+                                     recomputed halo (3D radius 1, Tb 2, 4 or
+                                     8): the space-time tiles of Sec. 4.1
+                                     computed "without redundant computation",
+                                     one co-resident CTA per 64-column tile,
+                                     intermediate time levels handed between
+                                     tiles through an L2-resident ring of
+                                     (Tb-1) x 5 grid planes (plan-owned).
+                                     Needs nx a multiple of 64, at most one
+                                     tile column per SM and tiles of at most
+                                     32 rows (a y-x plane of up to about
+                                     32 x 64 cells per SM) */
 } stencil_variant;
 
 /* Fixes the fused step count Tb (1, 2, 4 or 8) and kernel variant (a

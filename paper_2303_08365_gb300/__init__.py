@@ -33,6 +33,7 @@ VARIANT_DIRECT = 1
 VARIANT_STREAM = 2
 VARIANT_TEMPORAL = 3
 VARIANT_PERSISTENT = 4
+VARIANT_EXCHANGE = 5
 
 # (name, restype, argtypes) of every entry point of include/stencil.h
 _VP = ctypes.c_void_p

@@ -128,6 +128,10 @@ struct stencil_plan_s {
   int* d_status = nullptr;     // device status word (bounded waits that gave up)
   unsigned int* d_flags = nullptr;  // per-tile flags of the persistent temporal kernel
   int flags_cap = 0;
+  double* d_ring = nullptr;         // exchange kernel: ring of intermediate time levels
+  size_t ring_cells = 0;
+  unsigned int* d_xcnt = nullptr;   // exchange kernel: per-CTA progress counters
+  int xcnt_cap = 0;
   double* d_w = nullptr;       // weights in tap order, then kZeroSlots zeros and kOneSlots ones
   // one-item batches of the one-step persistent path, one per (grid, T) the
   // plan has run recently (least recently used evicted beyond kPersistCache):
@@ -475,9 +479,54 @@ int run_persistent_step(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream
   return batch_enqueue(hit, s);
 }
 
-// One launch per step (direct or streaming) or per Tb steps (temporal, with
-// single steps for the remainder), ping-ponging with the plan's buffer; the
-// result ends in d_grid.
+// The exchange kernel's ring and progress counters for Tb (grown on demand).
+int ensure_exchange(stencil_plan_s* p, int Tb, int ntiles) {
+  const size_t cells = exchange_ring_cells(p->g, Tb);
+  if (p->ring_cells < cells) {
+    cudaFree(p->d_ring);
+    p->d_ring = nullptr;
+    p->ring_cells = 0;
+    CUDA_TRY(dev_malloc(&p->d_ring, cells * sizeof(double)), "allocating the exchange ring");
+    p->ring_cells = cells;
+  }
+  const int words = exchange_counter_words(ntiles);
+  if (p->xcnt_cap < words) {
+    cudaFree(p->d_xcnt);
+    p->d_xcnt = nullptr;
+    p->xcnt_cap = 0;
+    CUDA_TRY(dev_malloc(&p->d_xcnt, words * sizeof(unsigned int)), "allocating the exchange counters");
+    p->xcnt_cap = words;
+  }
+  return STENCIL_OK;
+}
+
+// One Tb-step launch of the exchange kernel from a to b.
+int launch_exchange_block(stencil_plan_s* p, const double* a, double* b, int Tb, cudaStream_t s) {
+  ExchangeLaunch L;
+  if (!exchange_tiling(p->ndim, p->radius, p->g, sm_count(), &L.tiles_y, &L.tiles_x))
+    return fail(STENCIL_ERR_UNSUPPORTED, "the grid does not fit the exchange kernel's tiling");
+  const int ntiles = L.tiles_y * L.tiles_x;
+  int rc = ensure_exchange(p, Tb, ntiles);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemsetAsync(p->d_xcnt, 0, exchange_counter_words(ntiles) * sizeof(unsigned int), s),
+           "clearing the exchange counters");
+  L.g = p->g;
+  L.src = a;
+  L.dst = b;
+  L.ring = p->d_ring;
+  L.counters = p->d_xcnt;
+  L.status = p->d_status;
+  L.wdev = p->d_w;
+  L.Tb = Tb;
+  L.spin_limit = kSpinLimitNs;
+  cudaError_t e = launch_exchange(p->shape, p->boundary, L, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launching the exchange kernel");
+  return STENCIL_OK;
+}
+
+// One launch per step (direct or streaming) or per Tb steps (temporal or
+// exchange, with single steps for the remainder), ping-ponging with the
+// plan's buffer; the result ends in d_grid.
 int run_steps(stencil_plan_s* p, double* d_grid, int64_t T, int Tb, int variant, bool stream_ok,
               cudaStream_t s) {
   const int sms = sm_count();
@@ -490,11 +539,16 @@ int run_steps(stencil_plan_s* p, double* d_grid, int64_t T, int Tb, int variant,
   while (t < T) {
     cudaError_t e;
     int steps = 1;
-    if (variant == kVariantTemporal && T - t >= Tb) {
+    if (variant == kVariantExchange && T - t >= Tb) {
+      const int rc = launch_exchange_block(p, a, b, Tb, s);
+      if (rc) return rc;
+      e = cudaSuccess;
+      steps = Tb;
+    } else if (variant == kVariantTemporal && T - t >= Tb) {
       e = launch_temporal(p->ndim, p->radius, p->shape, p->boundary, Tb, p->g, p->d_w, a, b, sms, s);
       steps = Tb;
     } else {
-      const int v = variant == kVariantTemporal ? single : variant;
+      const int v = variant == kVariantTemporal || variant == kVariantExchange ? single : variant;
       if (v == kVariantStream && p->ndim == 3)
         e = launch_stream3d(p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, p->d_status, sms, s);
       else if (v == kVariantStream)
@@ -558,8 +612,22 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
                   "and 1D plans of radius 1 or 2 with Tb in {2, 4, 8}");
     variant = default_variant(p) == kVariantStream && stream_ok ? kVariantStream : kVariantDirect;
   }
-  if (variant != kVariantTemporal) Tb = 1;
-  if (variant != kVariantDirect && variant != kVariantStream && variant != kVariantTemporal)
+  if (variant == kVariantExchange) {
+    int ty, tx;
+    const bool ok = Tb >= 2 && Tb <= 8 && exchange_tiling(p->ndim, p->radius, p->g, sm_count(), &ty, &tx) &&
+                    ((uintptr_t)d_grid & 15) == 0 && ((uintptr_t)p->d_tmp & 15) == 0;
+    if (!ok) {
+      if (forced)
+        return fail(STENCIL_ERR_UNSUPPORTED,
+                    "the exchange kernel covers 3D radius-1 plans with Tb in {2, 4, 8}, nx a multiple of "
+                    "64, at most %d tile columns and tiles of at most 32 rows, on 16-byte aligned buffers",
+                    sm_count());
+      variant = stream_ok ? kVariantStream : kVariantDirect;
+    }
+  }
+  if (variant != kVariantTemporal && variant != kVariantExchange) Tb = 1;
+  if (variant != kVariantDirect && variant != kVariantStream && variant != kVariantTemporal &&
+      variant != kVariantExchange)
     return fail(STENCIL_ERR_UNSUPPORTED, "variant %s is not available", stencil_variant_name(variant));
   return run_steps(p, d_grid, T, Tb, variant, stream_ok, s);
 }
@@ -748,6 +816,7 @@ const char* stencil_variant_name(int v) {
     case kVariantStream: return "stream";
     case kVariantTemporal: return "temporal";
     case kVariantPersistent: return "persistent";
+    case kVariantExchange: return "exchange";
     default: return "";
   }
 }
@@ -821,6 +890,8 @@ void stencil_destroy(stencil_plan p) {
   cudaFree(p->d_adj);
   cudaFree(p->d_status);
   cudaFree(p->d_flags);
+  cudaFree(p->d_ring);
+  cudaFree(p->d_xcnt);
   cudaFree(p->d_w);
   for (auto& e : p->persist) {
     e.batch->d_partner = nullptr;  // the plan's own ping-pong buffer
@@ -1070,7 +1141,8 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
   struct Cand { int Tb, variant; };
   std::vector<Cand> cands = {{1, kVariantDirect}, {1, kVariantStream}, {1, kVariantPersistent},
                              {2, kVariantPersistent}, {4, kVariantPersistent}, {8, kVariantPersistent},
-                             {2, kVariantTemporal}, {4, kVariantTemporal}, {8, kVariantTemporal}};
+                             {2, kVariantTemporal}, {4, kVariantTemporal}, {8, kVariantTemporal},
+                             {2, kVariantExchange}, {4, kVariantExchange}, {8, kVariantExchange}};
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0), "creating an event");
   CUDA_TRY(cudaEventCreate(&e1), "creating an event");

@@ -32,7 +32,8 @@ enum Variant : int {
   kVariantStream = 2,     // slowest-axis streaming through a TMA-fed SMEM ring
   kVariantTemporal = 3,   // Tb fused steps per HBM round trip (overlapped tiles)
   kVariantPersistent = 4, // one launch for all steps: barrier per step (Tb 1) or tile flags (Tb > 1)
-  kVariantCount = 5
+  kVariantExchange = 5,   // Tb fused steps per launch, 3D, no recompute: tiles hand over levels through L2
+  kVariantCount = 6
 };
 
 // Tap list for a launch, passed by value (kernel parameter space lives in the
@@ -96,6 +97,28 @@ bool temporal_supported(int ndim, int radius, int Tb);
 cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int Tb, const Geom& g,
                             const double* wdev, const double* src, double* dst, int sms,
                             cudaStream_t stream);
+
+// Temporal blocking without recomputation (3D radius 1, star or box, Tb >= 2):
+// one co-resident CTA per 64-column tile of the (y, x) plane, intermediate
+// time levels handed between tiles through a ring of Tb-1 x 5 grid planes.
+struct ExchangeLaunch {
+  Geom g;
+  const double* src;       // time t (16-byte aligned)
+  double* dst;             // time t + Tb (16-byte aligned, not src)
+  double* ring;            // exchange_ring_cells(g, Tb) doubles
+  unsigned int* counters;  // exchange_counter_words(tiles) words, zero before the launch
+  int* status;
+  const double* wdev;
+  int Tb;
+  int tiles_y, tiles_x;    // from exchange_tiling
+  long long spin_limit;    // ns
+};
+// The tile grid for `sms` co-resident CTAs; false when the shape does not fit
+// the kernel (not 3D radius 1, nx not a multiple of 64, tiles taller than 32).
+bool exchange_tiling(int ndim, int radius, const Geom& g, int sms, int* tiles_y, int* tiles_x);
+size_t exchange_ring_cells(const Geom& g, int Tb);
+int exchange_counter_words(int tiles);
+cudaError_t launch_exchange(Shape shape, int boundary, const ExchangeLaunch& L, cudaStream_t stream);
 
 // Variable-coefficient diffusion: coefficient preparation, one forward step,
 // one fused adjoint step, gradient finalisation and the loss reduction.

@@ -95,6 +95,8 @@ CASES = [
     ((37, 53), 1, "star", PERIODIC, 4, "persistent", 9),
     ((300, 257), 1, "box", DIRICHLET, 2, "persistent", 7),
     ((9, 10, 11), 2, "box", PERIODIC, 1, "direct", 2),
+    ((13, 37, 128), 1, "star", DIRICHLET, 4, "exchange", 9),
+    ((6, 40, 192), 1, "box", PERIODIC, 8, "exchange", 17),
 ]
 
 
@@ -106,7 +108,8 @@ def test_sweep_writes_stay_inside_the_grid(st, shape, radius, kind, boundary, Tb
     g = Guarded(u0)
     p = st.Plan(shape, radius, w, boundary)
     p.set_tuning(Tb, {"direct": st.VARIANT_DIRECT, "stream": st.VARIANT_STREAM,
-                      "temporal": st.VARIANT_TEMPORAL, "persistent": st.VARIANT_PERSISTENT}[variant])
+                      "temporal": st.VARIANT_TEMPORAL, "persistent": st.VARIANT_PERSISTENT,
+                      "exchange": st.VARIANT_EXCHANGE}[variant])
     p.run(g.view, T)
     assert g.intact()
     assert normwise_rel(g.numpy(), oracle.run(u0, w, radius, boundary, T, nthreads=0)) <= TOL

@@ -374,6 +374,74 @@ def test_temporal_blocking_matches_single_steps_bitwise(st, shape, boundary, kin
     assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
 
 
+EXCHANGE_CASES = [
+    # shape, boundary, kind, Tb, T
+    ((13, 45, 64), PERIODIC, "heat", 2, 5),
+    ((13, 45, 64), PERIODIC, "heat", 4, 9),
+    ((13, 45, 64), PERIODIC, "heat", 8, 17),
+    ((9, 30, 128), DIRICHLET, "box_rand", 4, 9),
+    ((9, 30, 128), PERIODIC, "box_rand", 8, 19),
+    ((2, 5, 64), PERIODIC, "box_rand", 8, 16),      # fewer planes than the stage skew
+    ((1, 1, 64), DIRICHLET, "heat", 2, 4),          # one row of one plane
+    ((20, 33, 192), DIRICHLET, "star_rand", 8, 8),  # one-row tiles, three tile columns
+    ((7, 150, 64), PERIODIC, "heat", 4, 4),         # 150 one-row tiles in one column
+    ((6, 400, 128), DIRICHLET, "box_rand", 2, 7),   # tiles of 5 and 6 rows
+    ((31, 64, 256), PERIODIC, "star_rand", 4, 12),
+]
+
+
+@pytest.mark.parametrize("shape,boundary,kind,Tb,T", EXCHANGE_CASES)
+def test_exchange_kernel_matches_single_steps_bitwise(st, shape, boundary, kind, Tb, T):
+    """Tb fused steps with no recomputed halo (tiles hand their intermediate
+    levels to each other through L2): the same per-cell FMA chain as single
+    steps, so bitwise equal to the direct kernel, remainder steps included,
+    and within 1e-12 of the oracle."""
+    w = weights_for(kind, 3, 1, 700 + Tb)
+    u0 = synth.normal(13, shape)
+    a = gpu_run(st, u0, w, 1, boundary, T, Tb=Tb, variant=st.VARIANT_EXCHANGE)
+    b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
+
+
+def test_exchange_kernel_rejects_shapes_it_cannot_take(st):
+    import torch
+    for shape, radius in (((9, 30, 100), 1), ((40, 128), 1), ((9, 30, 64), 2)):
+        w = np.zeros((2 * radius + 1,) * len(shape))
+        w[(radius,) * len(shape)] = 1.0
+        p = st.Plan(shape, radius, w, PERIODIC)
+        p.set_tuning(4, st.VARIANT_EXCHANGE)
+        g = torch.zeros(shape, dtype=torch.float64, device="cuda")
+        with pytest.raises(st.StencilError) as e:
+            p.run(g, 4)
+        assert e.value.code == st.ERR_UNSUPPORTED
+        p.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape,boundary,kind,seed", FULL_TEMPORAL[:2])
+def test_exchange_full_size_windows(st, shape, boundary, kind, seed):
+    """The exchange kernel at the benchmark's sizes and launch configuration,
+    for Tb = 2, 4, 8: windows against the oracle after two Tb-blocks and a
+    remainder step."""
+    import torch
+    w = weights_for(kind, len(shape), 1, seed)
+    u0 = synth.normal(seed, shape) if kind == "box_rand" else synth.uniform(seed, shape)
+    g = torch.empty(shape, dtype=torch.float64, device="cuda")
+    p = st.Plan(shape, 1, w, boundary)
+    for Tb in (2, 4, 8):
+        T = 2 * Tb + 1
+        p.set_tuning(Tb, st.VARIANT_EXCHANGE)
+        g.copy_(torch.from_numpy(u0))
+        p.run(g, T)
+        assert p.status() == 0
+        for lo, hi in window_boxes(shape):
+            ref = oracle.run_window(u0, w, 1, boundary, T, lo, hi)
+            sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+            assert normwise_rel(g[sl].cpu().numpy(), ref) <= TOL, (Tb, lo, hi)
+    p.close()
+
+
 def test_temporal_unsupported_tb_is_rejected(st):
     import torch
     w = np.zeros((5, 5, 5))
