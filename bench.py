@@ -156,6 +156,7 @@ def cuda_time(fn, stream):
 KERNEL_SOURCES = {"stream3d": ["stream.cu", "ptx.cuh", "taps.cuh"],
                   "stream2d": ["stream2d.cu", "ptx.cuh", "taps.cuh"],
                   "temporal": ["temporal.cu", "taps.cuh"],
+                  "exchange": ["exchange.cu", "ptx.cuh", "taps.cuh"],
                   "direct": ["direct.cu", "taps.cuh"],
                   "batched": ["batched.cu"],
                   "varcoef": ["varcoef.cu"],
@@ -369,6 +370,31 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
     if sweep is not None:
         out["tb_sweep_gstencil_per_s"] = sweep
     return out
+
+
+def form_forced(st, name, shape, radius, weights, boundary, T, u0, stream, peak, Tb, variant, reps=1):
+    """One constant-weight workload on a forced (Tb, variant), with its roofline:
+    FP64 instructions per cell include the periodic z-halo the exchange kernel
+    recomputes ((Tb-1)/nz of the planes)."""
+    import torch
+    grid = torch.from_numpy(u0).cuda()
+    plan = st.Plan(shape, radius, weights, boundary)
+    plan.set_tuning(Tb, variant)
+    ms, launches = time_plan(st, plan, grid, T, reps, stream)
+    assert plan.status() == 0
+    plan.close()
+    del grid
+    torch.cuda.empty_cache()
+    cells = int(np.prod(shape))
+    vname = st.stencil_variant_name(variant)
+    instr = INSTR[name]
+    if vname == "exchange" and boundary == 1:
+        instr *= 1 + (Tb - 1) / shape[0]
+    return {"workload": f"{name} {'x'.join(map(str, shape))} T={T} {'periodic' if boundary else 'dirichlet0'}",
+            "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3), "Tb": Tb,
+            "variant": vname, "launches": launches,
+            "roofline": roofline(name, cells, T, ms, launches, peak, variant_kernel(vname, len(shape)), Tb=Tb,
+                                 instr=instr)}
 
 
 # The paper's eight benchmark stencils at its own problem sizes (Table 1),
@@ -697,7 +723,7 @@ def run_case(args):
     n = args.size
     name = args.case
     if name in ("heat3d", "box3d"):
-        shape = (n, n, n)
+        shape = (args.nz or n, n, n)
         w = synth.heat_weights(3, 0.1) if name == "heat3d" else synth.box_weights(3, seed=synth.SEED_BOX3D)
         bnd = 1 if name == "heat3d" else 0
     elif name in ("heat2d", "box2d"):
@@ -758,12 +784,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="all", help="all | none | comma list of "
-                    "box2d,box3d,heat2d,batched,adjoint")
+                    "box2d,box3d,heat2d,batched,adjoint,radius2,onedim,thermal,heat3d_tb,temporal,table1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None,
                     help="profiling mode: heat3d | box3d | heat2d | box2d | varcoef | adjoint | batched | "
                          "thermal (the case study with the FP32 deviation counts)")
     ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--nz", type=int, default=0, help="3D cases: slowest-axis length (0: --size)")
     ap.add_argument("--T", type=int, default=4)
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--Tb", type=int, default=0)
@@ -804,6 +831,8 @@ def main():
                    "tile": {"stream": "64 x 32 cells of (x, y), streamed along z, 4-plane TMA ring",
                             "temporal": "64 x 32 (Tb 2), 32 x 32 (Tb 4) or 16 x 16 (Tb 8) cells of (x, y) "
                                         "plus a Tb halo, streamed along z",
+                            "exchange": "64 columns x 26-27 rows of (x, y) per co-resident CTA, streamed "
+                                        "along z, levels handed over through an L2 ring",
                             "direct": "one cell per thread, 32 x 8 threads"}.get(h["variant"], h["variant"]),
                    "l2_flush": "none needed: each launch streams 2 GiB > 129 MB L2"},
         "roofline": roofline("heat3d-7pt", cells, T, h["ms"], h["launches"] // args.steps,
@@ -827,7 +856,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline(h["u0"], gpu_run=gpu_run)
     forms = {}
     want = set(["box2d", "box3d", "heat2d", "batched", "adjoint", "radius2", "onedim", "thermal",
-                "heat3d_tb", "table1"]) \
+                "heat3d_tb", "temporal", "table1"]) \
         if args.forms == "all" else \
         set() if args.forms == "none" else set(args.forms.split(","))
     if "batched" in want:
@@ -845,9 +874,18 @@ def main():
             r = form_const(st, "heat3d-7pt", shp, 1, synth.heat_weights(3, HEADLINE["alpha"]), 1, 100, u0,
                            stream, peak_tflops, reps=1,
                            tb_sweep=[(1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
-                                     (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL)])
+                                     (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL),
+                                     (2, st.VARIANT_EXCHANGE), (4, st.VARIANT_EXCHANGE),
+                                     (8, st.VARIANT_EXCHANGE)])
             forms["heat3d_tb_sweep"] = {"workload": r["workload"],
                                         "tb_sweep_gstencil_per_s": r["tb_sweep_gstencil_per_s"]}
+        if "temporal" in want:
+            # the temporal-blocked sweep on the headline workload at full T: the
+            # exchange kernel (no recomputed halo), Tb = 4 and 8
+            for tb in (4, 8):
+                forms[f"temporal_tb{tb}"] = form_forced(st, "heat3d-7pt", HEADLINE["shape"], 1,
+                                                        synth.heat_weights(3, HEADLINE["alpha"]), 1, HEADLINE["T"],
+                                                        h["u0"], stream, peak_tflops, tb, st.VARIANT_EXCHANGE)
         if "box2d" in want:
             shp = (16384, 16384)
             forms["box2d"] = form_const(st, "box2d-9pt", shp, 1, synth.box_weights(2, 1.0 / 9.0), 1, 1000,
@@ -886,7 +924,9 @@ def main():
             forms["box3d"] = form_const(st, "box3d-27pt", shp, 1, synth.box_weights(3, seed=synth.SEED_BOX3D),
                                         0, 500, synth.normal(synth.SEED_BOX3D, shp), stream, peak_tflops,
                                         tb_sweep=[(1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
-                                                  (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL)],
+                                                  (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL),
+                                                  (2, st.VARIANT_EXCHANGE), (4, st.VARIANT_EXCHANGE),
+                                                  (8, st.VARIANT_EXCHANGE)],
                                         autotune_steps=8)
         if "adjoint" in want:
             forms["adjoint"] = form_adjoint(st, stream, peak_tflops)
