@@ -258,7 +258,7 @@ __device__ __forceinline__ bool wait_counters(const XParams& P, const int (&nb)[
 // (s == 1) or its ring slot (-1: a plane of zeros) and `st` the ring stage.
 template <bool PERIODIC>
 __device__ __forceinline__ void post_plane(const XParams& P, XSlot& sl, uint64_t* bar, int j, int ra, int rb,
-                                           int y0, int x0, int s, int z, int st) {
+                                           int y0, int x0, int s, int z, int st, uint64_t keep) {
   int seg_r[3], seg_y[3], seg_n[3], nseg = 0;
   int a = ra, b = rb;
   if (PERIODIC && y0 - 1 + a < 0) {  // the row above the grid: the last row
@@ -290,8 +290,8 @@ __device__ __forceinline__ void post_plane(const XParams& P, XSlot& sl, uint64_t
       const int which = whole ? k : 0;
       if (s == 1)
         tma_load_3d(&sl.plane[j][r + e][0], &P.map_in[which], x0, y + e, z, bar);
-      else
-        tma_load_4d(&sl.plane[j][r + e][0], &P.map_ring[which], x0, y + e, z, st, bar);
+      else  // ring lines stay in L2 until their slot is rewritten
+        tma_load_4d_hint(&sl.plane[j][r + e][0], &P.map_ring[which], x0, y + e, z, st, bar, keep);
     }
   }
 }
@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
     }
     uint32_t u = 0;
     bool failed = false;
+    const uint64_t keep = policy_evict_last();
     unsigned int ready[kMaxStages];  // lane 0: acquired minimum of the counters per stage
 #pragma unroll
     for (int k = 0; k < kMaxStages; ++k) ready[k] = 0;
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
             z = exists ? wrapi(qq, K) : -1;
           }
           const int ra = (BOX || j == 1) ? 0 : 1, rb = (BOX || j == 1) ? h + 1 : h;
-          post_plane<PERIODIC>(P, sl, &S.full[slot], j, ra, rb, y0, x0, s, z, s - 2);
+          post_plane<PERIODIC>(P, sl, &S.full[slot], j, ra, rb, y0, x0, s, z, s - 2, keep);
         }
         // x-halo pairs: box: every plane and row; star: plane q at the tile's rows
         const int hrows = BOX ? 3 * (h + 2) : h;
@@ -430,7 +431,10 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
               g = P.ring + (((int64_t)(s - 2) * K + wrapi(qq, K)) * P.ny + y) * P.nx + x;
             }
           }
-          cp_async16_cg(&sl.halo[j][r][side], g, valid);
+          if (s == 1)
+            cp_async16_cg(&sl.halo[j][r][side], g, valid);
+          else
+            cp_async16_cg_hint(&sl.halo[j][r][side], g, valid, keep);
         }
         cp_async_arrive_noinc(&S.full[slot]);
         ++u;

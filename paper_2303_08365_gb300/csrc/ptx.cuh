@@ -98,6 +98,16 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// The same with an L2 cache policy for the lines read (see policy_evict_last).
+__device__ __forceinline__ void tma_load_4d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                                 int c3, uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
 // Orders this thread's generic-proxy global accesses with its async-proxy
 // (TMA) accesses of global memory, in both directions.
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -109,6 +119,13 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 __device__ __forceinline__ void cp_async16_cg(void* dst, const void* src, bool valid) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
                "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+// The same with an L2 cache policy for the lines read.
+__device__ __forceinline__ void cp_async16_cg_hint(void* dst, const void* src, bool valid, uint64_t policy) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(smem_u32(dst)),
+               "l"(src), "r"(valid ? 16 : 0), "l"(policy)
                : "memory");
 }
 
