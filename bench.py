@@ -210,16 +210,16 @@ HBM_GBS = _measured_hbm_gbs()
 
 
 def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_cell=16,
-             instr=None):
+             instr=None, flops=None):
     """The stated roofline: min(FP64 peak / F, HBM bandwidth * Tb / bytes per
     cell) in cell updates per second; `frac` = achieved FP64 flops / peak
     (the FP64 term binds for every workload here)."""
-    flops = FLOPS[name] * cells * T
-    achieved = flops / (ms * 1e-3) / 1e12
-    per_launch = FLOPS[name] * cells * T / max(launches, 1)
+    F = FLOPS[name] if flops is None else flops
+    achieved = F * cells * T / (ms * 1e-3) / 1e12
+    per_launch = F * cells * T / max(launches, 1)
     instr = INSTR[name] if instr is None else instr
     instr_rate = instr * cells * T / (ms * 1e-3)             # FP64 instructions per second
-    fp64_ceiling = peak_tflops * 1e12 / FLOPS[name] / 1e9
+    fp64_ceiling = peak_tflops * 1e12 / F / 1e9
     hbm_ceiling = HBM_GBS * 1e9 * Tb / bytes_per_cell / 1e9
     rate = cells * T / (ms * 1e-3) / 1e9
     pipe_frac = instr_rate / (peak_tflops * 1e12 / 2)
@@ -228,17 +228,17 @@ def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_
         # per cell than the K taps the metric's F credits (shared partial sums
         # of an equal-weight box), flops / peak overstates its efficiency and
         # `frac` is the executed-instruction fraction instead
-        credited = (FLOPS[name] + 1) / 2
+        credited = (F + 1) / 2
         if instr < credited - 1e-9:
             out = {"bound": "alu", "achieved": round(instr_rate * 2 / 1e12, 4), "peak": round(peak_tflops, 4),
                    "unit": "TFLOP/s", "frac": round(pipe_frac, 4),
                    "frac_basis": f"executed FP64 instructions ({instr:g} per cell, x2 flop) / peak: the kernel "
-                                 f"shares partial sums, so the metric's F = {FLOPS[name]} flop/cell over-counts "
+                                 f"shares partial sums, so the metric's F = {F} flop/cell over-counts "
                                  f"its work (flops-credited fraction {achieved / peak_tflops:.3f})"}
         else:
             out = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tflops, 4),
                    "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                   "frac_basis": f"algorithmic flops (F = {FLOPS[name]} per cell) / measured FP64 peak"}
+                   "frac_basis": f"algorithmic flops (F = {F:g} per cell) / measured FP64 peak"}
     else:
         gbs = bytes_per_cell * cells * T / Tb / (ms * 1e-3) / 1e9
         out = {"bound": "hbm", "achieved": round(gbs, 2), "peak": round(HBM_GBS, 1), "unit": "GB/s",
@@ -560,8 +560,15 @@ def form_adjoint(st, stream, peak):
             # (48 each); the transposed step reads lambda, u, c0..cz, reads and writes the
             # three face-gradient accumulators and writes lambda' (104; periodic grids have no
             # ghost faces, so the fourth accumulator is untouched)
-            "roofline": roofline("adjoint-7pt", cells, T, ms, launches, peak, "adjoint",
-                                 bytes_per_cell=48 + 48 * recomputed / T + 104, instr=instr),
+            # F per cell-step: forward 13, transposed step 13 + 3 faces x (2 differences, a
+            # product, a sum) = 25, and the forward recompute that checkpointing every 32 steps
+            # makes part of the method (13 per recomputed step); frac_without_recompute_credit
+            # counts only the 38 of a run that stores every state
+            "roofline": dict(roofline("adjoint-7pt", cells, T, ms, launches, peak, "adjoint",
+                                      bytes_per_cell=48 + 48 * recomputed / T + 104, instr=instr,
+                                      flops=FLOPS["adjoint-7pt"] + 13 * recomputed / T),
+                             frac_without_recompute_credit=round(
+                                 FLOPS["adjoint-7pt"] * cells * T / (ms * 1e-3) / 1e12 / peak, 4)),
             "forward_roofline": roofline("varcoef-7pt", cells, T, ms_fwd, T, peak, "varcoef",
                                          bytes_per_cell=48),
             "every_state_kept": store_all}
