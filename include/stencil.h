@@ -345,6 +345,15 @@ int stencil_selftest_barrier_timeout(double limit_ms, void* cuda_stream);
  * designed. */
 int stencil_selftest_flag_timeout(double limit_ms, void* cuda_stream);
 
+/* The same for the TMA-fed streaming kernel's mbarrier waits: launches it on
+ * an 8 x 32 x 128 periodic grid with its producer warp told to post no copy
+ * (and not the arrival that announces the copy's bytes) for the second plane
+ * of every CTA, so the consumers' waits for that plane can only end by their
+ * wall-time limit (limit_ms, at most 2000).  No copy is left half-issued, so
+ * nothing can fault.  Returns STENCIL_ERR_TIMEOUT when the kernel gave up and
+ * reported it as designed.  Synchronous; allocates and frees about 0.5 MB. */
+int stencil_selftest_tma_timeout(double limit_ms, void* cuda_stream);
+
 /* Host-side fault injection for tests: after `after` more device allocations
  * by this library succeed, every later one fails as if the device were out
  * of memory, without calling the driver, until the injection is turned off

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("stencil_selftest_barrier_timeout", ctypes.c_int, [ctypes.c_double, _VP]),
     ("stencil_debug_fail_allocations", None, [ctypes.c_int]),
     ("stencil_selftest_flag_timeout", ctypes.c_int, [ctypes.c_double, _VP]),
+    ("stencil_selftest_tma_timeout", ctypes.c_int, [ctypes.c_double, _VP]),
     ("stencil_run_2d_static", ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _DP, ctypes.c_int, _VP,
                                              ctypes.c_int64, _VP]),
     ("stencil_static_status", ctypes.c_int, [_VP]),
@@ -313,6 +314,12 @@ def stencil_selftest_flag_timeout(limit_ms=20.0, stream=None):
     """Runs the tile-flag wait's failure path on the GPU; returns the status
     code (ERR_TIMEOUT when it behaved)."""
     return lib().stencil_selftest_flag_timeout(float(limit_ms), _stream(stream))
+
+
+def stencil_selftest_tma_timeout(limit_ms=20.0, stream=None):
+    """Runs the streaming kernel's starved-mbarrier failure path; returns the
+    status code (ERR_TIMEOUT when it behaved)."""
+    return lib().stencil_selftest_tma_timeout(float(limit_ms), _stream(stream))
 
 
 def stencil_debug_fail_allocations(after):

@@ -1585,6 +1585,59 @@ int stencil_selftest_flag_timeout(double limit_ms, void* cuda_stream) {
   return st;
 }
 
+int stencil_selftest_tma_timeout(double limit_ms, void* cuda_stream) {
+  g_err.clear();
+  if (!(limit_ms > 0.0) || limit_ms > 2000.0) return fail(STENCIL_ERR_ARG, "limit_ms must be in (0, 2000]");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // an 8 x 32 x 128 periodic grid on the TMA-fed streaming kernel (7-point
+  // star), whose producer warp posts no copy -- and not the arrival that
+  // announces its bytes -- for the second plane of every CTA: the consumers'
+  // mbarrier waits for that plane can only end by their wall-time limit
+  const Geom g{8, 32, 128};
+  const size_t cells = (size_t)g.cells();
+  double* a = nullptr;
+  double* b = nullptr;
+  double* w = nullptr;
+  int* status = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(w);
+    cudaFree(status);
+  };
+  if (dev_malloc(&a, cells * sizeof(double)) != cudaSuccess ||
+      dev_malloc(&b, cells * sizeof(double)) != cudaSuccess ||
+      dev_malloc(&w, (7 + kExtraSlots) * sizeof(double)) != cudaSuccess ||
+      dev_malloc(&status, sizeof(int)) != cudaSuccess) {
+    cleanup();
+    return fail(STENCIL_ERR_OOM, "allocating the self-test buffers");
+  }
+  HostTaps taps;
+  taps.n = 7;
+  for (int k = 0; k < 7; ++k) {
+    taps.w[k] = k == 3 ? 1.0 : 0.0;
+    taps.dz[k] = taps.dy[k] = taps.dx[k] = 0;
+  }
+  std::vector<double> hw(7 + kExtraSlots, 0.0);
+  hw[3] = 1.0;
+  for (int k = 0; k < kOneSlots; ++k) hw[7 + kZeroSlots + k] = 1.0;
+  cudaMemsetAsync(a, 0, cells * sizeof(double), s);
+  cudaMemsetAsync(status, 0, sizeof(int), s);
+  cudaMemcpyAsync(w, hw.data(), hw.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  int rc = STENCIL_OK;
+  cudaError_t e = launch_stream3d(Shape::kStar, kPeriodic, g, taps, w, a, b, status, sm_count(), s,
+                                  (unsigned long long)(limit_ms * 1e6), 1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int st = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) rc = cuda_fail(e, "running the self-test");
+  cleanup();
+  if (rc) return rc;
+  if (st != STENCIL_ERR_TIMEOUT)
+    return fail(STENCIL_ERR_CUDA, "the bounded mbarrier wait did not report a timeout (status %d)", st);
+  return st;
+}
+
 // ------------------------------------------------------------ measurement
 
 int stencil_fp64_peak(double millis, double* dfma_per_s, void* cuda_stream) {

@@ -76,9 +76,12 @@ bool stream3d_eligible(int ndim, int radius, Shape shape, int boundary, const Ge
                        const void* b);
 // The shape part of that rule (no buffers, no driver query).
 bool stream3d_shape_ok(int ndim, int radius, Shape shape, int boundary, const Geom& g);
+// wait_ns bounds every mbarrier wait (kSpinLimitNs in normal runs); skip_plane
+// >= 0 is the self-test's starved plane (the producer posts no copy for it).
 cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const HostTaps& taps,
                             const double* wdev, const double* src, double* dst, int* status,
-                            int sms, cudaStream_t stream);
+                            int sms, cudaStream_t stream, unsigned long long wait_ns = 2000000000ull,
+                            long long skip_plane = -1);
 
 // 2D radius-1 or radius-2 streaming sweep (TMA-fed ring of 16-row blocks).  Same
 // eligibility rules with ny % 16 == 0 for periodic grids.  `equal` selects

@@ -54,7 +54,6 @@ namespace {
 constexpr int kTX = 64;
 constexpr int kSlots = 4;
 constexpr int kThreads = 256;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
 // Tile height: the 7-point star takes 32 rows (4 per warp, 8 FMA chains per
 // thread, one barrier per 2048 cells); the 27-point box keeps 16 rows (its 27
@@ -78,6 +77,8 @@ struct StreamParams {
   long long work;  // tiles * nz plane-tiles
   int* status;
   const double* wdev;  // NT weights then kZeroSlots zeros (device)
+  unsigned long long wait_ns;  // limit of every mbarrier wait (2 s; the self-test sets less)
+  long long skip_plane;        // self-test only: the producer posts no copy for this plane (-1: none)
 };
 
 __device__ __forceinline__ int wrap_or_keep(int c, int n, bool periodic) {
@@ -197,18 +198,20 @@ __global__ void __launch_bounds__(kThreads + 32, BOX ? 2 : 3)
       for (int j = 0; j < nplanes; ++j, ++g) {
         const int slot = g % kSlots;
         if (g >= kSlots &&
-            !mbar_wait_bounded(&S.empty[slot], ((g - kSlots) / kSlots) & 1, kWaitLimitNs)) {
+            !mbar_wait_bounded(&S.empty[slot], ((g - kSlots) / kSlots) & 1, P.wait_ns)) {
           *abort_flag = 1;
           atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
         }
         if (*abort_flag) {
           // let the copies already posted land (bounded), then leave
           for (uint32_t q = g > kSlots ? g - kSlots : 0; q < g; ++q)
-            mbar_wait_bounded(&S.full[q % kSlots], (q / kSlots) & 1, kWaitLimitNs);
+            mbar_wait_bounded(&S.full[q % kSlots], (q / kSlots) & 1, P.wait_ns);
           return;
         }
         const int z = za - 1 + j;
-        if (lane == 0) {
+        // (the self-test's skipped plane gets neither its copies nor the
+        // arrival that announces them: its consumers' wait can only run out)
+        if (lane == 0 && (long long)g != P.skip_plane) {
           fence_proxy_async_smem();
           issue_plane<NT, BOX, PERIODIC>(S, P, slot, z, y0, x0);
         }
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kThreads + 32, BOX ? 2 : 3)
       const int jfirst = (k == 1) ? 0 : k + 1;
       for (int j = jfirst; j <= k + 1; ++j) {
         const uint32_t gq = base + j;
-        if (!mbar_wait_bounded(&S.full[gq % kSlots], (gq / kSlots) & 1, kWaitLimitNs)) {
+        if (!mbar_wait_bounded(&S.full[gq % kSlots], (gq / kSlots) & 1, P.wait_ns)) {
           *abort_flag = 1;
           atomicCAS(P.status, 0, -5 /* STENCIL_ERR_TIMEOUT */);
         }
@@ -315,7 +318,7 @@ int ws_occupancy() {
 
 template <int NT, bool BOX, bool PERIODIC>
 cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, double* dst, int* status,
-                     int sms, cudaStream_t stream) {
+                     int sms, cudaStream_t stream, unsigned long long wait_ns, long long skip_plane) {
   constexpr int kTY = Tile<BOX>::TY;
   StreamParams<NT> P;
   if (!encode_3d(&P.map_row, src, g.nz, g.ny, g.nx, 1) ||
@@ -331,6 +334,8 @@ cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, doubl
   P.work = (long long)P.tiles_x * P.tiles_y * g.nz;
   P.status = status;
   P.wdev = wdev;
+  P.wait_ns = wait_ns;
+  P.skip_plane = skip_plane;
   int occ = ws_occupancy<NT, BOX, PERIODIC>();
   if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)sms * occ;
@@ -358,16 +363,16 @@ bool stream3d_eligible(int ndim, int radius, Shape shape, int boundary, const Ge
 
 cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const HostTaps& taps,
                             const double* wdev, const double* src, double* dst, int* status,
-                            int sms, cudaStream_t stream) {
+                            int sms, cudaStream_t stream, unsigned long long wait_ns, long long skip_plane) {
   const bool per = boundary == kPeriodic;
   if (shape == Shape::kBox) {
     if (taps.n != 27) return cudaErrorInvalidValue;
-    return per ? launch_t<27, true, true>(g, wdev, src, dst, status, sms, stream)
-               : launch_t<27, true, false>(g, wdev, src, dst, status, sms, stream);
+    return per ? launch_t<27, true, true>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane)
+               : launch_t<27, true, false>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
   }
   if (taps.n != 7) return cudaErrorInvalidValue;
-  return per ? launch_t<7, false, true>(g, wdev, src, dst, status, sms, stream)
-             : launch_t<7, false, false>(g, wdev, src, dst, status, sms, stream);
+  return per ? launch_t<7, false, true>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane)
+             : launch_t<7, false, false>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
 }
 
 }  // namespace gbst

@@ -554,3 +554,25 @@ def test_tuning_record_is_shared_by_plans_with_the_same_key(st):
     assert b.get_tuning() == a.get_tuning()
     a.close()
     b.close()
+
+
+def test_tma_mbarrier_wait_reports_timeout_and_context_survives(st):
+    """Failure detection without a GPU fault, for the TMA-fed streaming kernel:
+    its producer posts no copy for one plane, so the consumers' mbarrier waits
+    give up after their 20 ms limit with STENCIL_ERR_TIMEOUT, and the next
+    sweep on the same kernel matches the oracle."""
+    import time
+    import torch
+    t0 = time.perf_counter()
+    assert st.stencil_selftest_tma_timeout(20.0) == st.ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    shape = (8, 32, 128)
+    u0 = synth.uniform(33, shape)
+    w = synth.heat_weights(3, 0.1)
+    g = torch.from_numpy(u0.copy()).cuda()
+    p = st.Plan(shape, 1, w, PERIODIC)
+    p.set_tuning(1, st.VARIANT_STREAM)
+    p.run(g, 5)
+    assert p.status() == 0
+    assert normwise_rel(g.cpu().numpy(), oracle.run(u0, w, 1, PERIODIC, 5)) <= TOL
+    p.close()
