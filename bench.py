@@ -251,7 +251,7 @@ def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_
             "frac_of_stated_roofline": round(min(stated, pipe_frac) if stated > 1.0 else stated, 4),
             "fp64_instr_per_cell": round(instr, 4),
             "fp64_pipe_frac": round(pipe_frac, 4),
-            "traffic": recorded_traffic(kernel, name),
+            "traffic": recorded_traffic(kernel, name if Tb == 1 else f"{name}@tb{Tb}"),
             "algorithmic_flops_per_launch": per_launch,
             "algorithmic_bytes_per_launch": bytes_per_cell * cells * T / Tb / max(launches, 1),
             "peak_source": "FP64 DFMA microbenchmark measured in this run, best of 3 (x2 flop/FMA); "
@@ -345,6 +345,7 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
     ms, launches = time_plan(st, plan, grid, T, reps, stream)
     cells = int(np.prod(shape))
     tb, v = plan.get_tuning()
+    tile = plan.get_tile()
     sweep = None
     if tb_sweep:
         sweep = {}
@@ -364,6 +365,7 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
                        f"{'periodic' if boundary else 'dirichlet0'}",
            "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3),
            "Tb": tb, "variant": st.stencil_variant_name(v), "autotuned": bool(autotune_steps),
+           "tile": list(tile) if tile[0] else None,
            "launches": launches,
            "roofline": roofline(name, cells, T, ms, launches, peak,
                                 variant_kernel(st.stencil_variant_name(v), len(shape)), Tb=tb)}

@@ -260,10 +260,29 @@ int stencil_set_tuning(stencil_plan p, int Tb, int variant);
 /* Reports the Tb and variant the next stencil_run of p will use. */
 int stencil_get_tuning(stencil_plan p, int* Tb, int* variant);
 
-/* Times the candidate (Tb, variant) pairs on d_grid (device, contents are
- * destroyed) for probe_steps steps each, after a warm-up, and keeps the
- * fastest for p.  Synchronous.  *best_gstencils (may be NULL) receives its
- * rate in 1e9 cell updates per second. */
+/* Tile shape of the 3D TMA-fed streaming kernel (STENCIL_VARIANT_STREAM,
+ * radius 1): tiles of tile_x = 64 columns (one warp's 32 lanes x 2 cells; 0
+ * also means 64) by tile_y rows, tile_y in {8, 16, 32}, or 0 for the default
+ * (32 for a star, 16 for a box).  Periodic grids need ny a multiple of
+ * tile_y (STENCIL_ERR_UNSUPPORTED at the next run otherwise).  The paper's
+ * blocking sizes are per-benchmark tuning parameters too (Table 1); results
+ * do not depend on the tile (bitwise).  The temporal kernels' tiles follow
+ * from Tb and, for STENCIL_VARIANT_EXCHANGE, from the SM count (one
+ * co-resident tile per SM), and are not set here.  stencil_autotune tries
+ * every tile height of the streaming kernel. */
+int stencil_set_tile(stencil_plan p, int tile_x, int tile_y);
+
+/* Reports the tile of the kernel the next run of p will use: (64, tile_y)
+ * for the 3D streaming kernel, (0, 0) for kernels whose tile is not a tuning
+ * choice. */
+int stencil_get_tile(stencil_plan p, int* tile_x, int* tile_y);
+
+/* Times the candidate (Tb, variant) pairs -- and, for the 3D streaming
+ * kernel, each tile height -- on d_grid (device, contents are destroyed) for
+ * probe_steps steps each, after a warm-up, and keeps the fastest for p (and
+ * in the tuning record: key Tb variant tile_y rate).  Synchronous.
+ * *best_gstencils (may be NULL) receives its rate in 1e9 cell updates per
+ * second. */
 int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* cuda_stream,
                      double* best_gstencils);
 

@@ -71,6 +71,8 @@ SIGNATURES = [
     ("stencil_plan_status", ctypes.c_int, [_VP, _VP]),
     ("stencil_set_tuning", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("stencil_get_tuning", ctypes.c_int, [_VP, _IP, _IP]),
+    ("stencil_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    ("stencil_get_tile", ctypes.c_int, [_VP, _IP, _IP]),
     ("stencil_autotune", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _DP]),
     ("stencil_variant_name", ctypes.c_char_p, [ctypes.c_int]),
     ("stencil_last_error", ctypes.c_char_p, []),
@@ -379,6 +381,15 @@ class Plan:
 
     def status(self, stream=None):
         return stencil_plan_status(self.handle, stream)
+
+    def set_tile(self, tile_x=0, tile_y=0):
+        """Tile of the 3D streaming kernel (64 x 8/16/32; 0 = default)."""
+        _check(lib().stencil_set_tile(self.handle, int(tile_x), int(tile_y)))
+
+    def get_tile(self):
+        tx, ty = ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().stencil_get_tile(self.handle, ctypes.byref(tx), ctypes.byref(ty)))
+        return tx.value, ty.value
 
     def get_tuning(self):
         return stencil_get_tuning(self.handle)

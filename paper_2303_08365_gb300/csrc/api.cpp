@@ -147,6 +147,7 @@ struct stencil_plan_s {
   // tuning
   int user_Tb = 0, user_variant = 0;
   int tuned_Tb = 0, tuned_variant = 0;
+  int user_tile_y = 0, tuned_tile_y = 0;  // streaming kernel's tile height (0: its default)
 
   int64_t cells() const { return g.cells(); }
 };
@@ -255,8 +256,11 @@ int sm_count() {
 // boundary).  STENCIL_TUNE_CACHE=<file> persists it across processes (one
 // line per key: key Tb variant rate); STENCIL_TUNE=off ignores it,
 // STENCIL_TUNE=full tunes a plan on its first run when no record exists.
+struct TuneRec {
+  int Tb, variant, tile_y;
+};
 std::mutex g_tune_mu;
-std::map<std::string, std::pair<int, int>> g_tune;
+std::map<std::string, TuneRec> g_tune;
 bool g_tune_loaded = false;
 
 // Name of the current device with blanks replaced (cached per device).
@@ -287,33 +291,39 @@ void tune_load_locked() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  char key[512];
-  int tb, v;
-  double rate;
-  while (std::fscanf(f, "%511s %d %d %lf", key, &tb, &v, &rate) == 4)
-    if (tb > 0 && v > 0 && v < kVariantCount) g_tune[key] = {tb, v};
+  // one line per key: key Tb variant tile_y rate (older records: key Tb variant rate)
+  char line[1024];
+  while (std::fgets(line, sizeof(line), f)) {
+    char key[512];
+    int tb = 0, v = 0, ty = 0;
+    double rate = 0.0;
+    const int got = std::sscanf(line, "%511s %d %d %d %lf", key, &tb, &v, &ty, &rate);
+    if (got == 4) ty = 0;  // key Tb variant rate
+    if (got >= 4 && tb > 0 && v > 0 && v < kVariantCount && ty >= 0) g_tune[key] = {tb, v, ty};
+  }
   std::fclose(f);
 }
 
-void tune_store(const std::string& key, int tb, int v, double rate) {
+void tune_store(const std::string& key, int tb, int v, int ty, double rate) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load_locked();
-  g_tune[key] = {tb, v};
+  g_tune[key] = {tb, v, ty};
   const char* path = std::getenv("STENCIL_TUNE_CACHE");
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %.3f\n", key.c_str(), tb, v, rate);
+  std::fprintf(f, "%s %d %d %d %.3f\n", key.c_str(), tb, v, ty, rate);
   std::fclose(f);
 }
 
-bool tune_lookup(const std::string& key, int& tb, int& v) {
+bool tune_lookup(const std::string& key, int& tb, int& v, int& ty) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load_locked();
   auto it = g_tune.find(key);
   if (it == g_tune.end()) return false;
-  tb = it->second.first;
-  v = it->second.second;
+  tb = it->second.Tb;
+  v = it->second.variant;
+  ty = it->second.tile_y;
   return true;
 }
 
@@ -352,8 +362,10 @@ bool persistent_eligible(const stencil_plan_s* p) {
   return p->ndim == 2 && p->radius == 1 && p->shape == Shape::kStar && p->taps.n == 5;
 }
 
-// Resolved (Tb, variant) for the next run of a constant-weight plan.
-void choose(const stencil_plan_s* p, int& Tb, int& variant) {
+// Resolved (Tb, variant, streaming tile height; 0 = the kernel's default) for
+// the next run of a constant-weight plan.
+void choose(const stencil_plan_s* p, int& Tb, int& variant, int& tile_y) {
+  tile_y = p->user_tile_y;
   if (p->user_Tb > 0 || p->user_variant > 0) {
     Tb = p->user_Tb > 0 ? p->user_Tb : 1;
     variant = p->user_variant > 0 ? p->user_variant : default_variant(p);
@@ -362,10 +374,19 @@ void choose(const stencil_plan_s* p, int& Tb, int& variant) {
   if (p->tuned_Tb > 0) {
     Tb = p->tuned_Tb;
     variant = p->tuned_variant;
+    if (!tile_y) tile_y = p->tuned_tile_y;
     return;
   }
-  if (tune_mode() != "off" && tune_lookup(plan_key(p), Tb, variant)) return;
+  int ty = 0;
+  if (tune_mode() != "off" && tune_lookup(plan_key(p), Tb, variant, ty)) {
+    if (!tile_y) tile_y = ty;
+    return;
+  }
   variant = default_variant(p, &Tb);
+}
+void choose(const stencil_plan_s* p, int& Tb, int& variant) {
+  int ty;
+  choose(p, Tb, variant, ty);
 }
 
 // Uploads the plan's weights (and the zero slots) to the device once.
@@ -400,8 +421,8 @@ int ensure_status(stencil_plan_s* p) {
 // on a scratch copy of the grid (their runs destroy it) and records the best.
 void tune_on_first_run(stencil_plan_s* p, const double* d_grid, cudaStream_t s) {
   if (tune_mode() != "full" || p->user_Tb != 0 || p->user_variant != 0 || p->tuned_Tb != 0) return;
-  int tb0, v0;
-  if (tune_lookup(plan_key(p), tb0, v0)) return;
+  int tb0, v0, ty0;
+  if (tune_lookup(plan_key(p), tb0, v0, ty0)) return;
   double* scratch = nullptr;
   if (dev_malloc(&scratch, (size_t)p->cells() * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -528,7 +549,7 @@ int launch_exchange_block(stencil_plan_s* p, const double* a, double* b, int Tb,
 // exchange, with single steps for the remainder), ping-ponging with the
 // plan's buffer; the result ends in d_grid.
 int run_steps(stencil_plan_s* p, double* d_grid, int64_t T, int Tb, int variant, bool stream_ok,
-              cudaStream_t s) {
+              int tile_y, cudaStream_t s) {
   const int sms = sm_count();
   const bool equal_box = p->shape == Shape::kBox && taps_all_equal(p->taps);
   // the single-step kernel for the steps that do not fill a whole Tb block
@@ -550,7 +571,8 @@ int run_steps(stencil_plan_s* p, double* d_grid, int64_t T, int Tb, int variant,
     } else {
       const int v = variant == kVariantTemporal || variant == kVariantExchange ? single : variant;
       if (v == kVariantStream && p->ndim == 3)
-        e = launch_stream3d(p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, p->d_status, sms, s);
+        e = launch_stream3d(p->shape, p->boundary, p->g, p->taps, p->d_w, a, b, p->d_status, sms, s,
+                            (unsigned long long)kSpinLimitNs, -1, tile_y);
       else if (v == kVariantStream)
         e = launch_stream2d(p->shape, p->radius, p->boundary, equal_box && p->radius == 1, p->g, p->taps,
                             p->d_w, a, b, p->d_status, sms, s);
@@ -572,8 +594,8 @@ int run_steps(stencil_plan_s* p, double* d_grid, int64_t T, int Tb, int variant,
 // the caller forced it) and dispatch.
 int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   tune_on_first_run(p, d_grid, s);
-  int Tb, variant;
-  choose(p, Tb, variant);
+  int Tb, variant, tile_y;
+  choose(p, Tb, variant, tile_y);
   const bool forced = p->user_Tb > 0 || p->user_variant > 0;
   int rc = ensure(&p->d_tmp, (size_t)p->cells(), "allocating the ping-pong buffer");
   if (rc) return rc;
@@ -581,9 +603,16 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   if (rc) return rc;
   rc = ensure_weights(p);
   if (rc) return rc;
+  if (p->ndim == 3 && tile_y && !stream3d_eligible(p->ndim, p->radius, p->shape, p->boundary, p->g, d_grid,
+                                                      p->d_tmp, tile_y)) {
+    if (p->user_tile_y)
+      return fail(STENCIL_ERR_UNSUPPORTED, "tile height %d does not fit this grid (periodic grids need ny a "
+                  "multiple of it)", tile_y);
+    tile_y = 0;  // a tuned tile that no longer fits: the default
+  }
   const bool stream_ok = p->ndim == 3
                              ? stream3d_eligible(p->ndim, p->radius, p->shape, p->boundary, p->g, d_grid,
-                                                 p->d_tmp)
+                                                 p->d_tmp, tile_y)
                              : stream2d_eligible(p->ndim, p->radius, p->boundary, p->g, d_grid, p->d_tmp);
   if (variant == kVariantStream && !stream_ok) {
     if (forced)
@@ -629,7 +658,7 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   if (variant != kVariantDirect && variant != kVariantStream && variant != kVariantTemporal &&
       variant != kVariantExchange)
     return fail(STENCIL_ERR_UNSUPPORTED, "variant %s is not available", stencil_variant_name(variant));
-  return run_steps(p, d_grid, T, Tb, variant, stream_ok, s);
+  return run_steps(p, d_grid, T, Tb, variant, stream_ok, tile_y, s);
 }
 
 VarcoefBufs coef_bufs(stencil_plan_s* p) {
@@ -1124,6 +1153,30 @@ int stencil_set_tuning(stencil_plan p, int Tb, int variant) {
   return STENCIL_OK;
 }
 
+int stencil_set_tile(stencil_plan p, int tile_x, int tile_y) {
+  g_err.clear();
+  if (!p) return fail(STENCIL_ERR_ARG, "plan is NULL");
+  if (tile_x != 0 && tile_x != 64) return fail(STENCIL_ERR_ARG, "tile_x must be 0 or 64 (got %d)", tile_x);
+  if (tile_y != 0 && stream3d_tile_y(p->shape, tile_y) < 0)
+    return fail(STENCIL_ERR_ARG, "tile_y must be 0, 8, 16 or 32 (got %d)", tile_y);
+  p->user_tile_y = tile_y;
+  return STENCIL_OK;
+}
+
+int stencil_get_tile(stencil_plan p, int* tile_x, int* tile_y) {
+  g_err.clear();
+  if (!p || !tile_x || !tile_y) return fail(STENCIL_ERR_ARG, "NULL argument");
+  int Tb, v, ty;
+  choose(p, Tb, v, ty);
+  *tile_x = 0;
+  *tile_y = 0;
+  if (v == kVariantStream && p->ndim == 3 && p->radius == 1) {
+    *tile_x = 64;
+    *tile_y = stream3d_tile_y(p->shape, ty);
+  }
+  return STENCIL_OK;
+}
+
 int stencil_get_tuning(stencil_plan p, int* Tb, int* variant) {
   g_err.clear();
   if (!p || !Tb || !variant) return fail(STENCIL_ERR_ARG, "NULL argument");
@@ -1138,20 +1191,24 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
   if (p->varcoef) return fail(STENCIL_ERR_UNSUPPORTED, "autotune covers constant-weight plans");
   if (probe_steps < 1) return fail(STENCIL_ERR_ARG, "probe_steps must be >= 1");
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  struct Cand { int Tb, variant; };
-  std::vector<Cand> cands = {{1, kVariantDirect}, {1, kVariantStream}, {1, kVariantPersistent},
-                             {2, kVariantPersistent}, {4, kVariantPersistent}, {8, kVariantPersistent},
-                             {2, kVariantTemporal}, {4, kVariantTemporal}, {8, kVariantTemporal},
-                             {2, kVariantExchange}, {4, kVariantExchange}, {8, kVariantExchange}};
+  struct Cand { int Tb, variant, tile_y; };
+  std::vector<Cand> cands = {{1, kVariantDirect, 0}, {1, kVariantStream, 0}, {1, kVariantPersistent, 0},
+                             {2, kVariantPersistent, 0}, {4, kVariantPersistent, 0}, {8, kVariantPersistent, 0},
+                             {2, kVariantTemporal, 0}, {4, kVariantTemporal, 0}, {8, kVariantTemporal, 0},
+                             {2, kVariantExchange, 0}, {4, kVariantExchange, 0}, {8, kVariantExchange, 0}};
+  if (p->ndim == 3 && p->radius == 1)  // the streaming kernel's tile heights
+    for (int ty : {8, 16, 32})
+      if (ty != stream3d_tile_y(p->shape, 0)) cands.push_back({1, kVariantStream, ty});
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0), "creating an event");
   CUDA_TRY(cudaEventCreate(&e1), "creating an event");
-  const int saved_Tb = p->user_Tb, saved_v = p->user_variant;
+  const int saved_Tb = p->user_Tb, saved_v = p->user_variant, saved_ty = p->user_tile_y;
   double best = -1.0;
   Cand best_c = cands[0];
   for (const Cand& c : cands) {
     p->user_Tb = c.Tb;
     p->user_variant = c.variant;
+    p->user_tile_y = c.tile_y;
     int rc = stencil_run(p, d_grid, c.Tb, nullptr, 0.0, cuda_stream);  // warm-up
     if (rc == STENCIL_ERR_UNSUPPORTED) continue;
     if (rc) break;
@@ -1170,12 +1227,14 @@ int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* 
   }
   p->user_Tb = saved_Tb;
   p->user_variant = saved_v;
+  p->user_tile_y = saved_ty;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best < 0) return g_err.empty() ? fail(STENCIL_ERR_CUDA, "no candidate ran") : STENCIL_ERR_CUDA;
   p->tuned_Tb = best_c.Tb;
   p->tuned_variant = best_c.variant;
-  tune_store(plan_key(p), best_c.Tb, best_c.variant, best);
+  p->tuned_tile_y = best_c.tile_y;
+  tune_store(plan_key(p), best_c.Tb, best_c.variant, best_c.tile_y, best);
   if (best_gstencils) *best_gstencils = best;
   return STENCIL_OK;
 }

@@ -69,19 +69,22 @@ cudaError_t launch_direct(int ndim, int radius, Shape shape, int boundary, const
 cudaError_t launch_direct_f32(int ndim, int radius, int boundary, const Geom& g, const HostTaps& taps,
                               const float* src, float* dst, cudaStream_t stream);
 
-// 3D radius-1 streaming sweep (TMA-fed shared-memory plane ring).  Eligible
-// when nx is even, both buffers are 16-byte aligned and, for periodic grids,
-// nx % 64 == 0 and ny a multiple of the tile height (32 star, 16 box).
+// 3D radius-1 streaming sweep (TMA-fed shared-memory plane ring) over tiles
+// of 64 columns by tile_y rows (8, 16 or 32; 0 = the default: 32 for the
+// star, 16 for the box).  Eligible when nx is even, both buffers are 16-byte
+// aligned and, for periodic grids, nx % 64 == 0 and ny % tile_y == 0.
 bool stream3d_eligible(int ndim, int radius, Shape shape, int boundary, const Geom& g, const void* a,
-                       const void* b);
+                       const void* b, int tile_y = 0);
 // The shape part of that rule (no buffers, no driver query).
-bool stream3d_shape_ok(int ndim, int radius, Shape shape, int boundary, const Geom& g);
+bool stream3d_shape_ok(int ndim, int radius, Shape shape, int boundary, const Geom& g, int tile_y = 0);
+// The tile height a tile_y request resolves to (-1: not a supported height).
+int stream3d_tile_y(Shape shape, int tile_y);
 // wait_ns bounds every mbarrier wait (kSpinLimitNs in normal runs); skip_plane
 // >= 0 is the self-test's starved plane (the producer posts no copy for it).
 cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const HostTaps& taps,
                             const double* wdev, const double* src, double* dst, int* status,
                             int sms, cudaStream_t stream, unsigned long long wait_ns = 2000000000ull,
-                            long long skip_plane = -1);
+                            long long skip_plane = -1, int tile_y = 0);
 
 // 2D radius-1 or radius-2 streaming sweep (TMA-fed ring of 16-row blocks).  Same
 // eligibility rules with ny % 16 == 0 for periodic grids.  `equal` selects

@@ -55,16 +55,19 @@ constexpr int kTX = 64;
 constexpr int kSlots = 4;
 constexpr int kThreads = 256;
 
-// Tile height: the 7-point star takes 32 rows (4 per warp, 8 FMA chains per
+// Tile height TY (8, 16 or 32 rows of 64 columns; a tuning choice).  The
+// default: the 7-point star takes 32 rows (4 per warp, 8 FMA chains per
 // thread, one barrier per 2048 cells); the 27-point box keeps 16 rows (its 27
-// register-resident weights leave no room for more chains).
-template <bool BOX>
+// register-resident weights leave room for fewer chains).
+template <int TY_>
 struct Tile {
-  static constexpr int TY = BOX ? 16 : 32;
+  static constexpr int TY = TY_;
   static constexpr int Rows = TY + 2;
   static constexpr int RowsPerWarp = TY / 8;
   static constexpr uint32_t PlaneBytes = Rows * kTX * sizeof(double);
 };
+template <bool BOX>
+constexpr int default_ty() { return BOX ? 16 : 32; }
 
 template <int NT>
 struct StreamParams {
@@ -86,14 +89,14 @@ __device__ __forceinline__ int wrap_or_keep(int c, int n, bool periodic) {
   return c < 0 ? c + n : (c >= n ? c - n : c);
 }
 
-template <int NT, bool BOX, bool PERIODIC, class Smem>
+template <int NT, int TY, bool PERIODIC, class Smem>
 __device__ __forceinline__ void issue_plane(Smem& S, const StreamParams<NT>& P, int slot,
                                             int z, int y0, int x0) {
-  constexpr int kRows = Tile<BOX>::Rows;
+  constexpr int kRows = Tile<TY>::Rows;
   const int zc = wrap_or_keep(z, P.nz, PERIODIC);
   const int ya = wrap_or_keep(y0 - 1, P.ny, PERIODIC);
-  const int yb = wrap_or_keep(y0 + Tile<BOX>::TY, P.ny, PERIODIC);
-  mbar_arrive_expect_tx(&S.full[slot], Tile<BOX>::PlaneBytes);
+  const int yb = wrap_or_keep(y0 + TY, P.ny, PERIODIC);
+  mbar_arrive_expect_tx(&S.full[slot], Tile<TY>::PlaneBytes);
   tma_load_3d(&S.plane[slot][0][0], &P.map_row, x0, ya, zc, &S.full[slot]);
   tma_load_3d(&S.plane[slot][1][0], &P.map_main, x0, y0, zc, &S.full[slot]);
   tma_load_3d(&S.plane[slot][kRows - 1][0], &P.map_row, x0, yb, zc, &S.full[slot]);
@@ -150,22 +153,22 @@ __device__ __forceinline__ void compute_pair(const Smem& S, const RegWeights<NT>
 //     the x-halo into shared memory and arrives on `full` (1 + 32 arrivals);
 //   - consumers: wait on `full` for the planes a step reads, compute, and
 //     release plane k-1 with one arrival per warp on `empty`.
-template <bool BOX>
+template <int TY>
 struct __align__(128) WsSmem {
-  double plane[kSlots][Tile<BOX>::Rows][kTX];
-  double halo[kSlots][2][Tile<BOX>::Rows];
+  double plane[kSlots][Tile<TY>::Rows][kTX];
+  double halo[kSlots][2][Tile<TY>::Rows];
   uint64_t full[kSlots];
   uint64_t empty[kSlots];
   int abort;
 };
 
-template <int NT, bool BOX, bool PERIODIC>
+template <int NT, bool BOX, bool PERIODIC, int TY>
 __global__ void __launch_bounds__(kThreads + 32, BOX ? 2 : 3)
     k_stream3d_ws(const __grid_constant__ StreamParams<NT> P) {
-  constexpr int kTY = Tile<BOX>::TY;
-  constexpr int kRows = Tile<BOX>::Rows;
+  constexpr int kTY = TY;
+  constexpr int kRows = Tile<TY>::Rows;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  WsSmem<BOX>& S = *reinterpret_cast<WsSmem<BOX>*>(smem_raw);
+  WsSmem<TY>& S = *reinterpret_cast<WsSmem<TY>*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kSlots; ++s) {
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(kThreads + 32, BOX ? 2 : 3)
         // arrival that announces them: its consumers' wait can only run out)
         if (lane == 0 && (long long)g != P.skip_plane) {
           fence_proxy_async_smem();
-          issue_plane<NT, BOX, PERIODIC>(S, P, slot, z, y0, x0);
+          issue_plane<NT, TY, PERIODIC>(S, P, slot, z, y0, x0);
         }
         for (int h = lane; h < 2 * kRows; h += 32) {
           const int side = h / kRows, r = h % kRows;
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(kThreads + 32, BOX ? 2 : 3)
       const int sm = (base + k - 1) % kSlots, s0 = (base + k) % kSlots, sp = (base + k + 1) % kSlots;
       const int z = za + k - 1;
 #pragma unroll
-      for (int r = 0; r < Tile<BOX>::RowsPerWarp; ++r) {
+      for (int r = 0; r < Tile<TY>::RowsPerWarp; ++r) {
         const int ry = warp + 8 * r;
         double a0 = 0.0, a1 = 0.0;
         compute_pair<NT, BOX>(S, W, sm, s0, sp, ry, lane, (2 * r) & 3, a0, a1);
@@ -296,30 +299,30 @@ bool encode_3d(CUtensorMap* map, const double* base, int nz, int ny, int nx, int
   return r == CUDA_SUCCESS;
 }
 
-template <bool BOX>
-constexpr size_t ws_smem_bytes() { return sizeof(WsSmem<BOX>); }
+template <int TY>
+constexpr size_t ws_smem_bytes() { return sizeof(WsSmem<TY>); }
 
-template <int NT, bool BOX, bool PERIODIC>
+template <int NT, bool BOX, bool PERIODIC, int TY>
 int ws_occupancy() {
   static std::atomic<int> cache[kMaxDeviceOrdinals];
   const int n = cached_per_device(cache, [] {
     int occ = 0;
-    cudaFuncSetAttribute(k_stream3d_ws<NT, BOX, PERIODIC>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
-    if (cudaFuncSetAttribute(k_stream3d_ws<NT, BOX, PERIODIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ws_smem_bytes<BOX>()) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_stream3d_ws<NT, BOX, PERIODIC>, kThreads + 32,
-                                                      ws_smem_bytes<BOX>()) != cudaSuccess)
+    auto kern = k_stream3d_ws<NT, BOX, PERIODIC, TY>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes<TY>()) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads + 32, ws_smem_bytes<TY>()) !=
+            cudaSuccess)
       occ = 0;
     return occ;
   });
   return n;
 }
 
-template <int NT, bool BOX, bool PERIODIC>
+template <int NT, bool BOX, bool PERIODIC, int TY>
 cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, double* dst, int* status,
                      int sms, cudaStream_t stream, unsigned long long wait_ns, long long skip_plane) {
-  constexpr int kTY = Tile<BOX>::TY;
+  constexpr int kTY = TY;
   StreamParams<NT> P;
   if (!encode_3d(&P.map_row, src, g.nz, g.ny, g.nx, 1) ||
       !encode_3d(&P.map_main, src, g.nz, g.ny, g.nx, kTY))
@@ -336,43 +339,64 @@ cudaError_t launch_t(const Geom& g, const double* wdev, const double* src, doubl
   P.wdev = wdev;
   P.wait_ns = wait_ns;
   P.skip_plane = skip_plane;
-  int occ = ws_occupancy<NT, BOX, PERIODIC>();
+  int occ = ws_occupancy<NT, BOX, PERIODIC, TY>();
   if (occ < 1) return cudaErrorInvalidConfiguration;
   long long grid = (long long)sms * occ;
   if (grid > P.work) grid = P.work;
-  k_stream3d_ws<NT, BOX, PERIODIC><<<(unsigned)grid, kThreads + 32, ws_smem_bytes<BOX>(), stream>>>(P);
+  k_stream3d_ws<NT, BOX, PERIODIC, TY><<<(unsigned)grid, kThreads + 32, ws_smem_bytes<TY>(), stream>>>(P);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-bool stream3d_shape_ok(int ndim, int radius, Shape shape, int boundary, const Geom& g) {
+int stream3d_tile_y(Shape shape, int tile_y) {
+  if (tile_y == 0) return shape == Shape::kBox ? default_ty<true>() : default_ty<false>();
+  return (tile_y == 8 || tile_y == 16 || tile_y == 32) ? tile_y : -1;
+}
+
+bool stream3d_shape_ok(int ndim, int radius, Shape shape, int boundary, const Geom& g, int tile_y) {
   if (ndim != 3 || radius != 1) return false;
   if (g.nx % 2 != 0) return false;  // TMA: row pitch multiple of 16 bytes
-  const int ty = shape == Shape::kBox ? Tile<true>::TY : Tile<false>::TY;
+  const int ty = stream3d_tile_y(shape, tile_y);
+  if (ty < 0) return false;
   return !(boundary == kPeriodic && (g.nx % kTX != 0 || g.ny % ty != 0));
 }
 
 bool stream3d_eligible(int ndim, int radius, Shape shape, int boundary, const Geom& g, const void* a,
-                       const void* b) {
-  if (!stream3d_shape_ok(ndim, radius, shape, boundary, g)) return false;
+                       const void* b, int tile_y) {
+  if (!stream3d_shape_ok(ndim, radius, shape, boundary, g, tile_y)) return false;
   if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return false;  // TMA base and 16-byte stores
   return tensor_map_encoder() != nullptr;
 }
 
+namespace {
+template <int NT, bool BOX, bool PERIODIC>
+cudaError_t launch_ty(int ty, const Geom& g, const double* wdev, const double* src, double* dst, int* status,
+                      int sms, cudaStream_t stream, unsigned long long wait_ns, long long skip_plane) {
+  switch (ty) {
+    case 8: return launch_t<NT, BOX, PERIODIC, 8>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
+    case 16: return launch_t<NT, BOX, PERIODIC, 16>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
+    case 32: return launch_t<NT, BOX, PERIODIC, 32>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
 cudaError_t launch_stream3d(Shape shape, int boundary, const Geom& g, const HostTaps& taps,
                             const double* wdev, const double* src, double* dst, int* status,
-                            int sms, cudaStream_t stream, unsigned long long wait_ns, long long skip_plane) {
+                            int sms, cudaStream_t stream, unsigned long long wait_ns, long long skip_plane,
+                            int tile_y) {
   const bool per = boundary == kPeriodic;
+  const int ty = stream3d_tile_y(shape, tile_y);
   if (shape == Shape::kBox) {
     if (taps.n != 27) return cudaErrorInvalidValue;
-    return per ? launch_t<27, true, true>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane)
-               : launch_t<27, true, false>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
+    return per ? launch_ty<27, true, true>(ty, g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane)
+               : launch_ty<27, true, false>(ty, g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
   }
   if (taps.n != 7) return cudaErrorInvalidValue;
-  return per ? launch_t<7, false, true>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane)
-             : launch_t<7, false, false>(g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
+  return per ? launch_ty<7, false, true>(ty, g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane)
+             : launch_ty<7, false, false>(ty, g, wdev, src, dst, status, sms, stream, wait_ns, skip_plane);
 }
 
 }  // namespace gbst

@@ -106,7 +106,7 @@ def test_tuning_record_file_is_read(tmp_path):
             "print(*st.stencil_get_tuning(h))\n")
     cache = tmp_path / "tune.txt"
     # without a GPU the device name reads 'unknown'
-    cache.write_text("unknown/d3/16x32x64/r1/boxeq/b1 2 3 12.5\n")
+    cache.write_text("unknown/d3/16x32x64/r1/boxeq/b1 2 3 0 12.5\n")
     env = dict(os.environ, STENCIL_TUNE_CACHE=str(cache), PYTHONPATH=ROOT)
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
     assert out.returncode == 0, out.stderr
@@ -142,3 +142,30 @@ def test_default_goes_direct_for_shapes_the_streaming_kernels_cannot_take(stenci
     for dims, w, boundary, want in cases:
         with stencil.Plan(dims, 1, w, boundary) as p:
             assert p.get_tuning() == (1, want), dims
+
+
+def test_tile_setting_is_checked_on_host(stencil):
+    p = stencil.Plan((8, 32, 128), 1, np.ones(27) / 27, stencil.PERIODIC)
+    for bad in ((32, 16), (64, 12), (0, 64)):
+        with pytest.raises(stencil.StencilError):
+            p.set_tile(*bad)
+    p.set_tile(64, 8)
+    p.set_tile(0, 0)
+    p.close()
+
+
+def test_old_four_field_tuning_records_are_read(tmp_path):
+    """Records written before the tile field (key Tb variant rate) still apply."""
+    import subprocess
+    import sys
+    code = ("import numpy as np, paper_2303_08365_gb300 as st\n"
+            "h = st.stencil_create((16, 32, 64), 1, np.ones(27) / 27, st.PERIODIC)\n"
+            "print(*st.stencil_get_tuning(h))\n")
+    cache = tmp_path / "tune.txt"
+    cache.write_text("unknown/d3/16x32x64/r1/boxeq/b1 4 3 9.5\n")
+    env = dict(os.environ, STENCIL_TUNE_CACHE=str(cache), PYTHONPATH=ROOT)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    if out.stdout.split() == ["1", "2"]:
+        pytest.skip("a CUDA device is visible: the key carries its name")
+    assert out.stdout.split() == ["4", "3"]

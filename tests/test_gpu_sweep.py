@@ -465,7 +465,8 @@ def test_autotune_picks_a_candidate_and_keeps_results(st):
     assert rate > 0
     tb, v = p.get_tuning()
     assert (tb, v) in [(1, st.VARIANT_DIRECT), (1, st.VARIANT_STREAM), (2, st.VARIANT_TEMPORAL),
-                       (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL)]
+                       (4, st.VARIANT_TEMPORAL), (8, st.VARIANT_TEMPORAL), (2, st.VARIANT_EXCHANGE),
+                       (4, st.VARIANT_EXCHANGE), (8, st.VARIANT_EXCHANGE)]
     u0 = synth.uniform(4, shape)
     g = torch.from_numpy(u0.copy()).cuda()
     p.run(g, 10)
@@ -575,4 +576,47 @@ def test_tma_mbarrier_wait_reports_timeout_and_context_survives(st):
     p.run(g, 5)
     assert p.status() == 0
     assert normwise_rel(g.cpu().numpy(), oracle.run(u0, w, 1, PERIODIC, 5)) <= TOL
+    p.close()
+
+
+@pytest.mark.parametrize("shape,boundary,kind", [((10, 64, 128), PERIODIC, "heat"), ((9, 48, 192), PERIODIC, "box_rand"),
+                                                 ((7, 37, 70), DIRICHLET, "heat"), ((7, 37, 70), DIRICHLET, "box_rand")])
+def test_every_stream_tile_height_matches_direct_bitwise(st, shape, boundary, kind):
+    """The 3D streaming kernel's tile heights (the tuning dimension the
+    autotuner searches): each is bitwise equal to the direct kernel and
+    within 1e-12 of the oracle."""
+    import torch
+    w = weights_for(kind, 3, 1, 800)
+    u0 = synth.normal(14, shape)
+    ref = gpu_run(st, u0, w, 1, boundary, 5, Tb=1, variant=st.VARIANT_DIRECT)
+    assert normwise_rel(ref, oracle.run(u0, w, 1, boundary, 5, nthreads=0)) <= TOL
+    for ty in (8, 16, 32):
+        g = torch.from_numpy(u0.copy()).cuda()
+        p = st.Plan(shape, 1, w, boundary)
+        p.set_tuning(1, st.VARIANT_STREAM)
+        p.set_tile(64, ty)
+        assert p.get_tile() == (64, ty)
+        p.run(g, 5)
+        assert p.status() == 0
+        assert np.array_equal(g.cpu().numpy(), ref), ty
+        p.close()
+
+
+def test_autotune_records_the_tile(st, tmp_path):
+    import torch
+    shape = (12, 64, 128)
+    w = weights_for("box_rand", 3, 1, 801)
+    p = st.Plan(shape, 1, w, PERIODIC)
+    scratch = torch.from_numpy(synth.uniform(5, shape)).cuda()
+    p.autotune(scratch, 2)
+    tb, v = p.get_tuning()
+    tx, ty = p.get_tile()
+    if v == st.VARIANT_STREAM:
+        assert tx == 64 and ty in (8, 16, 32)
+    else:
+        assert (tx, ty) == (0, 0)
+    u0 = synth.uniform(6, shape)
+    g = torch.from_numpy(u0.copy()).cuda()
+    p.run(g, 6)
+    assert normwise_rel(g.cpu().numpy(), oracle.run(u0, w, 1, PERIODIC, 6, nthreads=0)) <= TOL
     p.close()
