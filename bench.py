@@ -159,8 +159,8 @@ KERNEL_SOURCES = {"stream3d": ["stream.cu", "ptx.cuh", "taps.cuh"],
                   "exchange": ["exchange.cu", "ptx.cuh", "taps.cuh"],
                   "direct": ["direct.cu", "taps.cuh"],
                   "batched": ["batched.cu"],
-                  "varcoef": ["varcoef.cu"],
-                  "adjoint": ["varcoef.cu"]}
+                  "varcoef": ["varcoef.cu", "taps.cuh"],
+                  "adjoint": ["varcoef.cu", "taps.cuh"]}
 
 
 def kernel_source_hash(kernel):
@@ -175,6 +175,21 @@ def recorded_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the kernel's current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
+        return None
+    cur = kernel_source_hash(kernel)
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == workload:
+            if parts[3] == cur:
+                return float(parts[2])
+    return None
+
+
+def recorded_instr(kernel, workload):
+    """FP64 instructions per cell update counted by ncu (profiles/fp64_instr.txt),
+    if counted on the kernel's current sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "fp64_instr.txt")
     if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
     cur = kernel_source_hash(kernel)
@@ -217,7 +232,12 @@ def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_
     F = FLOPS[name] if flops is None else flops
     achieved = F * cells * T / (ms * 1e-3) / 1e12
     per_launch = F * cells * T / max(launches, 1)
-    instr = INSTR[name] if instr is None else instr
+    instr_source = "given by the caller"
+    if instr is None:
+        counted = recorded_instr(kernel, name)
+        instr = INSTR[name] if counted is None else counted
+        instr_source = "table (kernel changed since the ncu count)" if counted is None else \
+            "ncu count, profiles/fp64_instr.txt"
     instr_rate = instr * cells * T / (ms * 1e-3)             # FP64 instructions per second
     fp64_ceiling = peak_tflops * 1e12 / F / 1e9
     hbm_ceiling = HBM_GBS * 1e9 * Tb / bytes_per_cell / 1e9
@@ -250,6 +270,7 @@ def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_
             "hbm_ceiling_gstencil_per_s": round(hbm_ceiling, 3),
             "frac_of_stated_roofline": round(min(stated, pipe_frac) if stated > 1.0 else stated, 4),
             "fp64_instr_per_cell": round(instr, 4),
+            "fp64_instr_source": instr_source,
             "fp64_pipe_frac": round(pipe_frac, 4),
             "traffic": recorded_traffic(kernel, name if Tb == 1 else f"{name}@tb{Tb}"),
             "algorithmic_flops_per_launch": per_launch,
@@ -389,9 +410,10 @@ def form_forced(st, name, shape, radius, weights, boundary, T, u0, stream, peak,
     torch.cuda.empty_cache()
     cells = int(np.prod(shape))
     vname = st.stencil_variant_name(variant)
-    instr = INSTR[name]
+    counted = recorded_instr(variant_kernel(vname, len(shape)), name)
+    instr = INSTR[name] if counted is None else counted
     if vname == "exchange" and boundary == 1:
-        instr *= 1 + (Tb - 1) / shape[0]
+        instr *= 1 + (Tb - 1) / shape[0]  # the stage skew's extra planes
     return {"workload": f"{name} {'x'.join(map(str, shape))} T={T} {'periodic' if boundary else 'dirichlet0'}",
             "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3), "Tb": Tb,
             "variant": vname, "launches": launches,
@@ -526,7 +548,9 @@ def form_adjoint(st, stream, peak):
     # recompute of every segment but the last (the forward sweep keeps that one's states)
     nseg = -(-T // ck)
     recomputed = (nseg - 1) * (ck - 1)
-    instr = 7 + 7 * recomputed / T + 7 + 9
+    fwd = recorded_instr("varcoef", "varcoef-7pt") or 7.0     # ncu counts when current
+    adj = recorded_instr("adjoint", "adjoint-step") or 16.0
+    instr = fwd + fwd * recomputed / T + adj
     plan.adjoint(u0, kappa, dt, target, T, ckpt_every=ck, stream=stream)  # warm-up
     l0 = st.stencil_launch_count()
     ms = cuda_time(lambda: plan.adjoint(u0, kappa, dt, target, T, ckpt_every=ck, stream=stream), stream)
@@ -550,7 +574,7 @@ def form_adjoint(st, stream, peak):
                      "ratio_vs_forward": round(ms_all / ms_fwd, 3),
                      "scratch_gib": round(need / 2**30, 1),
                      "roofline": roofline("adjoint-7pt", cells, T, ms_all, 2 * T, peak, "adjoint",
-                                          bytes_per_cell=48 + 104, instr=7 + 7 + 9)}
+                                          bytes_per_cell=48 + 104, instr=fwd + adj)}
     del u0, kappa, target, grid
     torch.cuda.empty_cache()
     return {"workload": "adjoint varcoef-7pt 256^3 T=1000 periodic, checkpoints every 32",

@@ -126,10 +126,10 @@ int stencil_run_f32(stencil_plan p, float* d_grid, float* d_work, int64_t T, voi
  * recomputed.  ckpt_every = 1 keeps every state (no recompute, T + 10 grids
  * of scratch: 126 GiB for 256^3 and T = 1000, which an HBM3e part of 288 GB
  * holds).  ckpt_every = 0 takes round(sqrt(T)).  The results do not depend on
- * the interval (bitwise).  The plan keeps its adjoint scratch for the next
- * call; a call that needs less than half of it, or stencil_destroy, frees it,
- * and stencil_adjoint (which waits for the stream) frees a scratch more than
- * twice the size the sqrt(T) interval would take before it returns.
+ * the interval (bitwise).  The plan keeps its adjoint scratch (checkpoints,
+ * segment states, adjoint fields: (T/c + c + 8) grids) for the next call, so
+ * repeated calls allocate nothing; a call that needs less than half of it
+ * gives it back and allocates its own size, and stencil_destroy frees it.
  * d_grad_u0 and d_grad_kappa (device, caller-owned, same shape) are
  * overwritten; *h_loss (host) receives L and the call waits for the stream. */
 int stencil_adjoint(stencil_plan p, const double* d_u0, const double* d_kappa, double dt,

@@ -1070,15 +1070,6 @@ int adjoint_core(stencil_plan_s* p, const double* d_u0, const double* d_kappa, d
     CUDA_TRY(cudaMemcpyAsync(h_loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, s),
              "copying the loss");
     CUDA_TRY(cudaStreamSynchronize(s), "waiting for the adjoint");
-    // this form has waited for the stream: a scratch larger than the sqrt(T)
-    // interval's (every state kept, or nearly) is freed rather than retained
-    const int64_t nck_sqrt = T / std::min<int64_t>(std::max<int64_t>(T, 1), c_sqrt) + 1;
-    const size_t need_sqrt = n * (size_t)(nck_sqrt + c_sqrt + 2 + 4 + 2) + (size_t)nblocks + 8;
-    if (need > 2 * need_sqrt) {
-      cudaFree(p->d_adj);
-      p->d_adj = nullptr;
-      p->adj_cells = 0;
-    }
   }
   return STENCIL_OK;
 }

@@ -76,3 +76,17 @@ def test_frac_basis_for_shared_partial_sums_and_hbm_bound():
     h = bench.roofline("heat1d-3pt", 10 ** 7, 1, 1.0, 1, 1000.0, "temporal", bytes_per_cell=16)
     assert h["bound"] == "hbm" and h["unit"] == "GB/s"
     assert h["frac"] == pytest.approx(16 * 10 ** 7 / 1e-3 / 1e9 / bench.HBM_GBS, rel=1e-3)
+
+
+def test_fp64_instruction_record_matches_current_sources():
+    """The ncu-counted FP64 instructions per cell apply to the kernels as they
+    are now, and agree with the hand table the bench falls back to."""
+    for kernel, workload, name in [("stream3d", "heat3d-7pt", "heat3d-7pt"), ("stream3d", "box3d-27pt", "box3d-27pt"),
+                                   ("stream2d", "box2d-9pt", "box2d-9pt"), ("varcoef", "varcoef-7pt", "varcoef-7pt")]:
+        n = bench.recorded_instr(kernel, workload)
+        assert n is not None, (kernel, workload)
+        assert n == pytest.approx(bench.INSTR[name])
+    assert bench.recorded_instr("exchange", "heat3d-7pt") == pytest.approx(7.0)
+    assert bench.recorded_instr("direct", "heat3d-7pt") is None
+    r = bench.roofline("heat3d-7pt", 512 ** 3, 10, 15.5, 10, 1.256, "stream3d")
+    assert r["fp64_instr_source"].startswith("ncu count")
