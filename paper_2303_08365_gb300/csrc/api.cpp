@@ -566,7 +566,8 @@ int run_steps(stencil_plan_s* p, double* d_grid, int64_t T, int Tb, int variant,
       e = cudaSuccess;
       steps = Tb;
     } else if (variant == kVariantTemporal && T - t >= Tb) {
-      e = launch_temporal(p->ndim, p->radius, p->shape, p->boundary, Tb, p->g, p->d_w, a, b, sms, s);
+      e = launch_temporal(p->ndim, p->radius, p->shape, p->boundary, Tb, p->g, p->d_w, a, b, sms, s,
+                          equal_box && p->ndim == 2 && p->radius == 1);
       steps = Tb;
     } else {
       const int v = variant == kVariantTemporal || variant == kVariantExchange ? single : variant;

@@ -100,9 +100,11 @@ cudaError_t launch_stream2d(Shape shape, int radius, int boundary, bool equal, c
 // Temporal blocking: Tb fused steps per launch (2D and 3D: radius 1, any
 // shape and boundary; 1D: radius 1 or 2; Tb in {2, 4, 8}).
 bool temporal_supported(int ndim, int radius, int Tb);
+// equal: a 2D box whose weights are all equal takes the shared-partial-sum
+// form (within rounding of the tap-order kernels, not bitwise equal).
 cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int Tb, const Geom& g,
                             const double* wdev, const double* src, double* dst, int sms,
-                            cudaStream_t stream);
+                            cudaStream_t stream, bool equal = false);
 
 // Temporal blocking without recomputation (3D radius 1, star or box, Tb >= 2):
 // one co-resident CTA per 64-column tile of the (y, x) plane, intermediate

@@ -169,10 +169,29 @@ __device__ __forceinline__ constexpr int tidx(int dw, int dv, int du) {
 // planes (pm, p0, pp) of the previous stage (row stride sw) around the cells
 // at (ly, lx) and (ly + 1, lx) (2D: (0, lx) and (0, lx + 1)) of that stage's
 // region.  Two independent chains, each in tap order.
-template <int NDIM, int NT, bool BOX>
+// EQ (2D 9-point box whose weights are all equal, w): the pair shares partial
+// sums instead: the four column sums C(x) = u(y-1, x) + (u(y, x) + u(y+1, x))
+// it needs, then u'(x) = w C(x-1) + w (C(x) + C(x+1)) and u'(x+1) =
+// w C(x+2) + w (C(x) + C(x+1)): 12 FP64 instructions for the two cells
+// instead of 18 (additions as FMAs against a register holding 1).  The sum
+// is taken in another order than the tap list, so the result is within
+// rounding of the other kernels, not bitwise equal to them.
+template <int NDIM, int NT, bool BOX, bool EQ = false>
 __device__ __forceinline__ void pair_update(const RegWeights<NT>& W, const double* pm, const double* p0,
                                             const double* pp, int sw, int ly, int lx, double& a0,
                                             double& a1) {
+  if constexpr (NDIM == 2 && EQ) {
+    double C[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int x = lx - 1 + k;
+      C[k] = W.add(pm[x], W.add(p0[x], pp[x], k & 1), 2 + (k & 1));
+    }
+    const double wt = fma(W.w[4], W.add(C[1], C[2], 0), W.z[0]);
+    a0 = fma(W.w[0], C[0], wt);
+    a1 = fma(W.w[8], C[3], wt);
+    return;
+  }
   const double* pl[3] = {pm, p0, pp};
   const int de = NDIM == 3 ? sw : 1;  // the second cell
 #pragma unroll
@@ -195,7 +214,7 @@ __device__ __forceinline__ void pair_update(const RegWeights<NT>& W, const doubl
 // Pair c of stage s's region, plane i: computed from the three planes of
 // stage s-1 around it and written to stage s's ring, or (s = Tb) to global
 // memory.
-template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
+template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB, bool EQ = false>
 __device__ __forceinline__ void stage_pair(const TParams& P, const RegWeights<NT>& W, double* sm, int s,
                                            int c, int i, int wa, int y0, int x0) {
   using L = Lay<NDIM, TB, BOX>;
@@ -215,7 +234,7 @@ __device__ __forceinline__ void stage_pair(const TParams& P, const RegWeights<NT
   const double* p0 = src + L::slot(s - 1, i) * sn;
   const double* pp = src + L::slot(s - 1, i + 1) * sn;
   double a0, a1;
-  pair_update<NDIM, NT, BOX>(W, pm, p0, pp, L::W(s - 1), NDIM == 3 ? qy + 1 : 0, qx + 1, a0, a1);
+  pair_update<NDIM, NT, BOX, EQ>(W, pm, p0, pp, L::W(s - 1), NDIM == 3 ? qy + 1 : 0, qx + 1, a0, a1);
   const int w = wa - TB + i;
   const int x = x0 - TB + s + qx;
   const int y = NDIM == 3 ? y0 - TB + s + qy : 0;
@@ -255,7 +274,7 @@ __device__ __forceinline__ void stage_pair(const TParams& P, const RegWeights<NT
   }
 }
 
-template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
+template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB, bool EQ = false>
 __global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_min_blocks<NDIM, BOX, TB>())
     k_temporal(const TParams P) {
   using L = Lay<NDIM, TB, BOX>;
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_mi
             c -= L::pairs(s);
             ++s;
           }
-          stage_pair<NDIM, NT, BOX, PERIODIC, TB>(P, W, sm, s, c, k - 2 * s, wa, y0, x0);
+          stage_pair<NDIM, NT, BOX, PERIODIC, TB, EQ>(P, W, sm, s, c, k - 2 * s, wa, y0, x0);
         }
       } else {
         // stage by stage: plane k - s - 1 is in range for s <= (k - 1) / 2
@@ -309,7 +328,7 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_mi
         for (int s = 1; s <= s_hi; ++s) {
           if (s > 1) __syncthreads();  // stage s-1's plane of this iteration is written
           for (int j = threadIdx.x; j < L::pairs(s); j += NTH)
-            stage_pair<NDIM, NT, BOX, PERIODIC, TB>(P, W, sm, s, j, k - s - 1, wa, y0, x0);
+            stage_pair<NDIM, NT, BOX, PERIODIC, TB, EQ>(P, W, sm, s, j, k - s - 1, wa, y0, x0);
         }
       }
     }
@@ -317,13 +336,13 @@ __global__ void __launch_bounds__(temporal_threads<NDIM, BOX, TB>(), temporal_mi
   }
 }
 
-template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB>
+template <int NDIM, int NT, bool BOX, bool PERIODIC, int TB, bool EQ = false>
 cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, double* dst, int sms,
                       cudaStream_t stream) {
   using L = Lay<NDIM, TB, BOX>;
   constexpr int NTH = temporal_threads<NDIM, BOX, TB>();
   static_assert(L::bytes <= 227 * 1024, "stage rings exceed shared memory");
-  auto kern = k_temporal<NDIM, NT, BOX, PERIODIC, TB>;
+  auto kern = k_temporal<NDIM, NT, BOX, PERIODIC, TB, EQ>;
   static std::atomic<int> cache[kMaxDeviceOrdinals];
   const int occ = cached_per_device(cache, [kern] {
     int n = 0;
@@ -350,13 +369,13 @@ cudaError_t launch_tb(const Geom& g, const double* wdev, const double* src, doub
   return cudaGetLastError();
 }
 
-template <int NDIM, int NT, bool BOX, bool PERIODIC>
+template <int NDIM, int NT, bool BOX, bool PERIODIC, bool EQ = false>
 cudaError_t by_tb(int Tb, const Geom& g, const double* wdev, const double* src, double* dst, int sms,
                   cudaStream_t stream) {
   switch (Tb) {
-    case 2: return launch_tb<NDIM, NT, BOX, PERIODIC, 2>(g, wdev, src, dst, sms, stream);
-    case 4: return launch_tb<NDIM, NT, BOX, PERIODIC, 4>(g, wdev, src, dst, sms, stream);
-    case 8: return launch_tb<NDIM, NT, BOX, PERIODIC, 8>(g, wdev, src, dst, sms, stream);
+    case 2: return launch_tb<NDIM, NT, BOX, PERIODIC, 2, EQ>(g, wdev, src, dst, sms, stream);
+    case 4: return launch_tb<NDIM, NT, BOX, PERIODIC, 4, EQ>(g, wdev, src, dst, sms, stream);
+    case 8: return launch_tb<NDIM, NT, BOX, PERIODIC, 8, EQ>(g, wdev, src, dst, sms, stream);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -440,7 +459,7 @@ bool temporal_supported(int ndim, int radius, int Tb) {
 
 cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int Tb, const Geom& g,
                             const double* wdev, const double* src, double* dst, int sms,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, bool equal) {
   const bool per = boundary == kPeriodic;
   const bool box = shape == Shape::kBox;
   if (ndim == 1) {
@@ -458,6 +477,8 @@ cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int
     return per ? by_tb<3, 7, false, true>(Tb, g, wdev, src, dst, sms, stream)
                : by_tb<3, 7, false, false>(Tb, g, wdev, src, dst, sms, stream);
   }
+  if (box && equal) return per ? by_tb<2, 9, true, true, true>(Tb, g, wdev, src, dst, sms, stream)
+                               : by_tb<2, 9, true, false, true>(Tb, g, wdev, src, dst, sms, stream);
   if (box) return per ? by_tb<2, 9, true, true>(Tb, g, wdev, src, dst, sms, stream)
                       : by_tb<2, 9, true, false>(Tb, g, wdev, src, dst, sms, stream);
   return per ? by_tb<2, 5, false, true>(Tb, g, wdev, src, dst, sms, stream)

@@ -370,7 +370,8 @@ def test_temporal_blocking_matches_single_steps_bitwise(st, shape, boundary, kin
     u0 = synth.normal(12, shape)
     a = gpu_run(st, u0, w, 1, boundary, T, Tb=Tb, variant=st.VARIANT_TEMPORAL)
     b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
-    assert np.array_equal(a, b)
+    if kind != "box_eq":  # the equal-weight 2D box shares partial sums: another summation order
+        assert np.array_equal(a, b)
     assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
 
 
@@ -440,6 +441,20 @@ def test_exchange_full_size_windows(st, shape, boundary, kind, seed):
             sl = tuple(slice(a, b) for a, b in zip(lo, hi))
             assert normwise_rel(g[sl].cpu().numpy(), ref) <= TOL, (Tb, lo, hi)
     p.close()
+
+
+@pytest.mark.parametrize("shape,boundary,Tb,T", [((64, 256), PERIODIC, 2, 9), ((45, 94), DIRICHLET, 4, 13),
+                                                ((33, 600), DIRICHLET, 8, 17), ((7, 5), PERIODIC, 8, 16),
+                                                ((1, 300), PERIODIC, 4, 8)])
+def test_temporal_equal_weight_box_shares_partial_sums(st, shape, boundary, Tb, T):
+    """The 2D 9-point box with equal weights in the temporal kernel: column
+    sums shared by each pair of cells (12 FP64 instructions per pair instead
+    of 18), within 1e-12 of the oracle, ragged segments and remainder steps
+    included."""
+    w = synth.box_weights(2, 1.0 / 9.0)
+    u0 = synth.uniform(15, shape)
+    a = gpu_run(st, u0, w, 1, boundary, T, Tb=Tb, variant=st.VARIANT_TEMPORAL)
+    assert normwise_rel(a, oracle.run(u0, w, 1, boundary, T, nthreads=0)) <= TOL
 
 
 def test_temporal_unsupported_tb_is_rejected(st):
