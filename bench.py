@@ -376,8 +376,13 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
             ms_s, _ = time_plan(st, plan, grid, T, 1, stream)
             rate = cells * T / (ms_s * 1e-3) / 1e9
             ceiling = min(fp64_ceiling, HBM_GBS * tbs / 16)
-            sweep[f"Tb={tbs} {st.stencil_variant_name(vs)}"] = {
-                "gstencil_per_s": round(rate, 3), "frac_of_stated_roofline": round(rate / ceiling, 4)}
+            entry = {"gstencil_per_s": round(rate, 3), "frac_of_stated_roofline": round(rate / ceiling, 4)}
+            instr = shared_sum_instr(name, st.stencil_variant_name(vs), tbs)
+            if instr is not None and rate / ceiling > 1.0:
+                # shared partial sums: F over-counts the work, report the executed fraction
+                entry["frac_of_stated_roofline"] = round(rate * 1e9 * instr / (peak * 1e12 / 2), 4)
+                entry["frac_basis"] = f"executed FP64 instructions ({instr:.3f} per cell) / peak"
+            sweep[f"Tb={tbs} {st.stencil_variant_name(vs)}"] = entry
         plan.set_tuning(0, 0)
     plan.close()
     del grid
@@ -393,6 +398,21 @@ def form_const(st, name, shape, radius, weights, boundary, T, u0, stream, peak, 
     if sweep is not None:
         out["tb_sweep_gstencil_per_s"] = sweep
     return out
+
+
+def shared_sum_instr(name, variant, Tb):
+    """FP64 instructions per cell of the kernels that share partial sums (the
+    equal-weight 2D 9-point box; None for every other workload): the streaming
+    kernel's 4.25, and the temporal kernel's 6 per cell times its row segment's
+    halo recompute ((TX + Tb - 1) / TX, TX = 254, 252, 248 for Tb = 2, 4, 8)."""
+    if name != "box2d-9pt":
+        return None
+    if variant == "stream":
+        return recorded_instr("stream2d", name) or INSTR[name]
+    if variant == "temporal":
+        tx = {2: 254, 4: 252, 8: 248}.get(Tb)
+        return None if tx is None else 6.0 * (tx + Tb - 1) / tx
+    return None
 
 
 def form_forced(st, name, shape, radius, weights, boundary, T, u0, stream, peak, Tb, variant, reps=1):

@@ -90,3 +90,9 @@ def test_fp64_instruction_record_matches_current_sources():
     assert bench.recorded_instr("direct", "heat3d-7pt") is None
     r = bench.roofline("heat3d-7pt", 512 ** 3, 10, 15.5, 10, 1.256, "stream3d")
     assert r["fp64_instr_source"].startswith("ncu count")
+
+
+def test_shared_sum_instruction_model():
+    assert bench.shared_sum_instr("heat3d-7pt", "stream", 1) is None
+    assert bench.shared_sum_instr("box2d-9pt", "stream", 1) == pytest.approx(4.25)
+    assert bench.shared_sum_instr("box2d-9pt", "temporal", 4) == pytest.approx(6 * 255 / 252)
