@@ -37,6 +37,8 @@ CASES = [
     ((300, 257), "heat", DIRICHLET, 1, "persistent", 6),
     ((50, 300), "heat", PERIODIC, 8, "temporal", 19),
     ((37, 70), "box", DIRICHLET, 1, "direct", 5),
+    ((24, 64, 128), "heat", PERIODIC, 4, "exchange", 9),
+    ((16, 40, 64), "box", DIRICHLET, 8, "exchange", 17),
 ]
 
 
@@ -54,7 +56,8 @@ def test_captured_sweep_replays_bitwise(st, shape, kind, boundary, Tb, variant, 
     u0 = synth.uniform(55, shape)
     p = st.Plan(shape, 1, w, boundary)
     p.set_tuning(Tb, {"stream": st.VARIANT_STREAM, "persistent": st.VARIANT_PERSISTENT,
-                      "temporal": st.VARIANT_TEMPORAL, "direct": st.VARIANT_DIRECT}[variant])
+                      "temporal": st.VARIANT_TEMPORAL, "direct": st.VARIANT_DIRECT,
+                      "exchange": st.VARIANT_EXCHANGE}[variant])
     g = torch.from_numpy(u0.copy()).cuda()
     p.run(g, T)                          # first run, on the grid the graph will use: scratch set up
     eager_T = g.cpu().numpy()
@@ -104,5 +107,32 @@ def test_plans_on_two_streams_run_concurrently(st):
     assert pa.status() == 0 and pb.status() == 0
     assert normwise_rel(ga.cpu().numpy(), oracle.run(a0, wa, 1, PERIODIC, 15, nthreads=0)) <= TOL
     assert normwise_rel(gb.cpu().numpy(), oracle.run(b0, wb, 1, PERIODIC, 15, nthreads=0)) <= TOL
+    pa.close()
+    pb.close()
+
+
+def test_exchange_plans_on_two_streams(st):
+    """Two plans on the co-resident exchange kernel, each a cooperative launch
+    that needs every SM, on two streams: the launches take turns and both
+    results match the oracle."""
+    import torch
+    a0 = synth.uniform(63, (20, 64, 128))
+    b0 = synth.uniform(64, (12, 96, 192))
+    wa, wb = synth.heat_weights(3, 0.1), weights("box", 3)
+    pa = st.Plan(a0.shape, 1, wa, PERIODIC)
+    pb = st.Plan(b0.shape, 1, wb, DIRICHLET)
+    pa.set_tuning(4, st.VARIANT_EXCHANGE)
+    pb.set_tuning(2, st.VARIANT_EXCHANGE)
+    ga, gb = torch.from_numpy(a0.copy()).cuda(), torch.from_numpy(b0.copy()).cuda()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    sa.wait_stream(torch.cuda.current_stream())
+    sb.wait_stream(torch.cuda.current_stream())
+    for _ in range(3):
+        pa.run(ga, 8, stream=sa)
+        pb.run(gb, 6, stream=sb)
+    torch.cuda.synchronize()
+    assert pa.status() == 0 and pb.status() == 0
+    assert normwise_rel(ga.cpu().numpy(), oracle.run(a0, wa, 1, PERIODIC, 24, nthreads=0)) <= TOL
+    assert normwise_rel(gb.cpu().numpy(), oracle.run(b0, wb, 1, DIRICHLET, 18, nthreads=0)) <= TOL
     pa.close()
     pb.close()
