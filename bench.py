@@ -159,6 +159,7 @@ KERNEL_SOURCES = {"stream3d": ["stream.cu", "ptx.cuh", "taps.cuh"],
                   "exchange": ["exchange.cu", "ptx.cuh", "taps.cuh"],
                   "direct": ["direct.cu", "taps.cuh"],
                   "batched": ["batched.cu"],
+                  "persistent": ["batched.cu"],
                   "varcoef": ["varcoef.cu", "taps.cuh"],
                   "adjoint": ["varcoef.cu", "taps.cuh"]}
 
@@ -189,24 +190,30 @@ def recorded_traffic(kernel, workload):
 def recorded_instr(kernel, workload):
     """FP64 instructions per cell update counted by ncu (profiles/fp64_instr.txt),
     if counted on the kernel's current sources (else None)."""
+    return recorded_instr_state(kernel, workload)[0]
+
+
+def recorded_instr_state(kernel, workload):
+    """(count, state): state is "current", "stale" (counted on older sources)
+    or "none" (never counted)."""
     path = os.path.join(ROOT, "profiles", "fp64_instr.txt")
     if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
-        return None
+        return None, "none"
     cur = kernel_source_hash(kernel)
+    state = "none"
     for ln in open(path):
         parts = ln.split()
         if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == workload:
             if parts[3] == cur:
-                return float(parts[2])
-    return None
+                return float(parts[2]), "current"
+            state = "stale"
+    return None, state
 
 
 def variant_kernel(variant, ndim):
     """The kernel family a variant name runs (for the traffic record)."""
     if variant == "stream":
         return "stream3d" if ndim == 3 else "stream2d"
-    if variant == "persistent":
-        return "batched"
     return variant
 
 
@@ -225,19 +232,25 @@ HBM_GBS = _measured_hbm_gbs()
 
 
 def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_cell=16,
-             instr=None, flops=None):
+             instr=None, flops=None, traffic_key=None):
     """The stated roofline: min(FP64 peak / F, HBM bandwidth * Tb / bytes per
     cell) in cell updates per second; `frac` = achieved FP64 flops / peak
-    (the FP64 term binds for every workload here)."""
+    (the FP64 term binds for every workload here).  `traffic_key` names the
+    DRAM-traffic record when it is not the workload name (plus "@tb<Tb>")."""
     F = FLOPS[name] if flops is None else flops
     achieved = F * cells * T / (ms * 1e-3) / 1e12
     per_launch = F * cells * T / max(launches, 1)
     instr_source = "given by the caller"
     if instr is None:
-        counted = recorded_instr(kernel, name)
+        # a Tb-fused kernel's count (halo recompute included) is keyed "<name>@tb<Tb>"
+        counted, state = recorded_instr_state(kernel, f"{name}@tb{Tb}") if Tb > 1 else (None, "none")
+        if counted is None:
+            counted, state0 = recorded_instr_state(kernel, name)
+            state = state0 if state == "none" else state
         instr = INSTR[name] if counted is None else counted
-        instr_source = "table (kernel changed since the ncu count)" if counted is None else \
-            "ncu count, profiles/fp64_instr.txt"
+        instr_source = "ncu count, profiles/fp64_instr.txt" if counted is not None else \
+            "table (kernel changed since the ncu count)" if state == "stale" else \
+            "table (no ncu count recorded)"
     instr_rate = instr * cells * T / (ms * 1e-3)             # FP64 instructions per second
     fp64_ceiling = peak_tflops * 1e12 / F / 1e9
     hbm_ceiling = HBM_GBS * 1e9 * Tb / bytes_per_cell / 1e9
@@ -272,7 +285,7 @@ def roofline(name, cells, T, ms, launches, peak_tflops, kernel, Tb=1, bytes_per_
             "fp64_instr_per_cell": round(instr, 4),
             "fp64_instr_source": instr_source,
             "fp64_pipe_frac": round(pipe_frac, 4),
-            "traffic": recorded_traffic(kernel, name if Tb == 1 else f"{name}@tb{Tb}"),
+            "traffic": recorded_traffic(kernel, traffic_key or (name if Tb == 1 else f"{name}@tb{Tb}")),
             "algorithmic_flops_per_launch": per_launch,
             "algorithmic_bytes_per_launch": bytes_per_cell * cells * T / Tb / max(launches, 1),
             "peak_source": "FP64 DFMA microbenchmark measured in this run, best of 3 (x2 flop/FMA); "
@@ -474,6 +487,25 @@ def table1_weights(ndim, radius, kind, seed):
     return v / v.sum()
 
 
+def radius2_weights():
+    """The radius-2 2D workloads' weights (Star-2D9P, Box-2D25P): seeded
+    uniform weights summing to 1, the star keeping the box's centre row and
+    column."""
+    v = synth.uniform(synth.SEED_BOX2D + 10, (5, 5))
+    box25 = v / v.sum()
+    star9 = np.zeros((5, 5))
+    star9[2, :] = box25[2, :]
+    star9[:, 2] = box25[:, 2]
+    return star9 / star9.sum(), box25
+
+
+def onedim_weights():
+    """The 1D workloads' weights: Heat-1D (alpha = 0.25) and Star-1D5P
+    (seeded, summing to 1)."""
+    v5 = synth.uniform(synth.SEED_HEAT2D + 21, (5,))
+    return np.array([0.25, 0.5, 0.25]), v5 / v5.sum()
+
+
 def form_table1(st, stream, peak):
     """GStencil/s of each Table 1 stencil at Table 1's grid size.  The input
     is drawn on the device from a seeded generator (a 1024^3 grid is 8 GiB)."""
@@ -594,7 +626,8 @@ def form_adjoint(st, stream, peak):
                      "ratio_vs_forward": round(ms_all / ms_fwd, 3),
                      "scratch_gib": round(need / 2**30, 1),
                      "roofline": roofline("adjoint-7pt", cells, T, ms_all, 2 * T, peak, "adjoint",
-                                          bytes_per_cell=48 + 104, instr=fwd + adj)}
+                                          bytes_per_cell=48 + 104, instr=fwd + adj,
+                                          traffic_key="adjoint-step")}
     del u0, kappa, target, grid
     torch.cuda.empty_cache()
     return {"workload": "adjoint varcoef-7pt 256^3 T=1000 periodic, checkpoints every 32",
@@ -610,11 +643,16 @@ def form_adjoint(st, stream, peak):
             # product, a sum) = 25, and the forward recompute that checkpointing every 32 steps
             # makes part of the method (13 per recomputed step); frac_without_recompute_credit
             # counts only the 38 of a run that stores every state
+            # traffic: DRAM bytes of one k_adjoint launch (the dominant kernel), against
+            # its algorithmic 104 B per cell
             "roofline": dict(roofline("adjoint-7pt", cells, T, ms, launches, peak, "adjoint",
                                       bytes_per_cell=48 + 48 * recomputed / T + 104, instr=instr,
-                                      flops=FLOPS["adjoint-7pt"] + 13 * recomputed / T),
+                                      flops=FLOPS["adjoint-7pt"] + 13 * recomputed / T,
+                                      traffic_key="adjoint-step"),
                              frac_without_recompute_credit=round(
-                                 FLOPS["adjoint-7pt"] * cells * T / (ms * 1e-3) / 1e12 / peak, 4)),
+                                 FLOPS["adjoint-7pt"] * cells * T / (ms * 1e-3) / 1e12 / peak, 4),
+                             traffic_kernel="k_adjoint, per launch",
+                             traffic_algorithmic_bytes=104 * cells),
             "forward_roofline": roofline("varcoef-7pt", cells, T, ms_fwd, T, peak, "varcoef",
                                          bytes_per_cell=48),
             "every_state_kept": store_all}
@@ -737,7 +775,8 @@ def thermal_case(st, n, T, stream, fp32=True, peak=None):
     rate = n * n * T / (ms * 1e-3)
     if peak:
         out["roofline"] = roofline("heat2d-5pt", n * n, T, ms, T, peak,
-                                   variant_kernel(st.stencil_variant_name(v), 2), Tb=tb)
+                                   variant_kernel(st.stencil_variant_name(v), 2), Tb=tb,
+                                   traffic_key=f"heat2d-5pt-{n}sq" if tb == 1 else None)
     if n == THERMAL["n"]:
         full = THERMAL["n"] ** 2 * THERMAL["T_full"] / rate
         out["extrapolated_full_run_s"] = round(full, 1)
@@ -775,6 +814,7 @@ def run_case(args):
     stream = torch.cuda.current_stream()
     n = args.size
     name = args.case
+    radius = 2 if name in ("star2d9", "box2d25", "star1d5") else 1
     if name in ("heat3d", "box3d"):
         shape = (args.nz or n, n, n)
         w = synth.heat_weights(3, 0.1) if name == "heat3d" else synth.box_weights(3, seed=synth.SEED_BOX3D)
@@ -783,18 +823,35 @@ def run_case(args):
         shape = (n, n)
         w = synth.heat_weights(2, 0.1) if name == "heat2d" else synth.box_weights(2, 1.0 / 9.0)
         bnd = 0 if name == "heat2d" else 1
+    elif name in ("star2d9", "box2d25"):
+        # the radius-2 workloads of the benchmark line (periodic)
+        shape = (n, n)
+        w = radius2_weights()[0 if name == "star2d9" else 1]
+        bnd = 1
+    elif name in ("heat1d", "star1d5"):
+        # the 1D workloads (Heat-1D Dirichlet, Star-1D5P periodic), --size cells
+        shape = (n,)
+        w = onedim_weights()[0 if name == "heat1d" else 1]
+        bnd = 0 if name == "heat1d" else 1
     elif name in ("varcoef", "adjoint"):
         shape = (n, n, n)
     elif name == "thermal":
         print(json.dumps(thermal_case(st, n, args.T, stream)))
         return 0
     elif name == "batched":
-        # a reduced batch of the 96-grid workload's kind: sides log-uniform in [64, n]
-        items = synth.batch_items(synth.SEED_BATCH, count=24, side_lo=64, side_hi=n, t_lo=args.T,
-                                  t_hi=args.T)
+        # --size 0: the benchmark line's 96-grid workload with the kernel
+        # configuration --Tb / --cpt / --per-sm (the batch autotuner's pick);
+        # else a reduced batch of its kind: sides log-uniform in [64, n]
+        if n == 0:
+            items = synth.batch_items(synth.SEED_BATCH)
+        else:
+            items = synth.batch_items(synth.SEED_BATCH, count=24, side_lo=64, side_hi=n, t_lo=args.T,
+                                      t_hi=args.T)
         dev = [torch.from_numpy(synth.uniform(synth.SEED_BATCH + 1000 + i, (ny, nx))).cuda()
                for i, (ny, nx, _, _) in enumerate(items)]
         b = st.Batch(dev, [a for _, _, a, _ in items], [T for *_, T in items])
+        if n == 0:
+            b.set_tuning(args.Tb or 1, args.cpt, args.per_sm)
         for _ in range(args.warmup):
             b.run(stream)
         ms = cuda_time(lambda: [b.run(stream) for _ in range(args.steps)], stream) / args.steps
@@ -817,7 +874,7 @@ def run_case(args):
             fn = lambda: plan.adjoint(grid, kappa, dt, target, args.T, ckpt_every=args.ckpt,
                                       stream=stream)
     else:
-        plan = st.Plan(shape, 1, w, bnd)
+        plan = st.Plan(shape, radius, w, bnd)
         if args.variant:
             plan.set_tuning(args.Tb or 1, args.variant)
         fn = lambda: plan.run(grid, args.T, stream=stream)
@@ -840,13 +897,16 @@ def main():
                     "box2d,box3d,heat2d,batched,adjoint,radius2,onedim,thermal,heat3d_tb,temporal,table1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None,
-                    help="profiling mode: heat3d | box3d | heat2d | box2d | varcoef | adjoint | batched | "
-                         "thermal (the case study with the FP32 deviation counts)")
+                    help="profiling mode: heat3d | box3d | heat2d | box2d | star2d9 | box2d25 | heat1d | "
+                         "star1d5 | varcoef | adjoint | batched | thermal (the case study with the FP32 "
+                         "deviation counts)")
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--nz", type=int, default=0, help="3D cases: slowest-axis length (0: --size)")
     ap.add_argument("--T", type=int, default=4)
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--Tb", type=int, default=0)
+    ap.add_argument("--cpt", type=int, default=0, help="batched case: cells per thread (0 = default)")
+    ap.add_argument("--per-sm", type=int, default=0, help="batched case: blocks per SM (0 = default)")
     ap.add_argument("--ckpt", type=int, default=0, help="adjoint case: checkpoint interval "
                     "(0 = about sqrt(T), 1 = keep every state)")
     args = ap.parse_args()
@@ -948,12 +1008,7 @@ def main():
         if "radius2" in want:
             # Table 1's radius-2 shapes (Star-2D9P, Box-2D25P), seeded random weights summing to 1
             shp = (8192, 8192)
-            v = synth.uniform(synth.SEED_BOX2D + 10, (5, 5))
-            box25 = v / v.sum()
-            star9 = np.zeros((5, 5))
-            star9[2, :] = box25[2, :]
-            star9[:, 2] = box25[:, 2]
-            star9 /= star9.sum()
+            star9, box25 = radius2_weights()
             u0 = synth.uniform(synth.SEED_BOX2D + 11, shp)
             forms["star2d9p"] = form_const(st, "star2d-9pt", shp, 2, star9, 1, 100, u0, stream, peak_tflops)
             forms["box2d25p"] = form_const(st, "box2d-25pt", shp, 2, box25, 1, 100, u0, stream, peak_tflops)
@@ -965,10 +1020,9 @@ def main():
             # Table 1's 1D shapes: Heat-1D (alpha = 0.25) and Star-1D5P, 10^7 cells
             n1 = 10_000_000
             u1 = synth.uniform(synth.SEED_HEAT2D + 20, (n1,))
-            forms["heat1d"] = form_const(st, "heat1d-3pt", (n1,), 1, np.array([0.25, 0.5, 0.25]), 0, 1000,
-                                         u1, stream, peak_tflops)
-            v5 = synth.uniform(synth.SEED_HEAT2D + 21, (5,))
-            forms["star1d5p"] = form_const(st, "star1d-5pt", (n1,), 2, v5 / v5.sum(), 1, 1000, u1, stream,
+            heat3, star5 = onedim_weights()
+            forms["heat1d"] = form_const(st, "heat1d-3pt", (n1,), 1, heat3, 0, 1000, u1, stream, peak_tflops)
+            forms["star1d5p"] = form_const(st, "star1d-5pt", (n1,), 2, star5, 1, 1000, u1, stream,
                                            peak_tflops)
         if "box3d" in want:
             shp = (384, 384, 384)

@@ -55,7 +55,7 @@ def test_measured_hbm_peak_is_read_from_the_file():
 def test_variant_kernel_names():
     assert bench.variant_kernel("stream", 3) == "stream3d"
     assert bench.variant_kernel("stream", 2) == "stream2d"
-    assert bench.variant_kernel("persistent", 2) == "batched"
+    assert bench.variant_kernel("persistent", 2) == "persistent"
     assert bench.variant_kernel("temporal", 3) == "temporal"
 
 
@@ -96,3 +96,29 @@ def test_shared_sum_instruction_model():
     assert bench.shared_sum_instr("heat3d-7pt", "stream", 1) is None
     assert bench.shared_sum_instr("box2d-9pt", "stream", 1) == pytest.approx(4.25)
     assert bench.shared_sum_instr("box2d-9pt", "temporal", 4) == pytest.approx(6 * 255 / 252)
+
+
+def test_instruction_count_lookup_prefers_the_tb_keyed_record(tmp_path, monkeypatch):
+    """A Tb-fused kernel's count (its halo recompute included) is keyed
+    "<workload>@tb<Tb>" and wins over the plain key; a record taken on other
+    sources reads as stale, a missing one as unrecorded."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "fp64_instr.txt").write_text(
+        "# kernel workload count hash\n"
+        "persistent heat2d-5pt 5.000 aaaa\n"
+        "persistent heat2d-5pt@tb4 6.500 aaaa\n"
+        "temporal heat1d-3pt@tb8 3.100 bbbb\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda k: "aaaa")
+    assert bench.recorded_instr_state("persistent", "heat2d-5pt@tb4") == (6.5, "current")
+    assert bench.recorded_instr_state("temporal", "heat1d-3pt@tb8") == (None, "stale")
+    assert bench.recorded_instr_state("stream3d", "heat3d-7pt") == (None, "none")
+    r4 = bench.roofline("heat2d-5pt", 256 * 256, 100, 1.0, 1, 1.256, "persistent", Tb=4)
+    assert r4["fp64_instr_per_cell"] == 6.5 and r4["fp64_instr_source"].startswith("ncu count")
+    r1 = bench.roofline("heat2d-5pt", 256 * 256, 100, 1.0, 1, 1.256, "persistent", Tb=1)
+    assert r1["fp64_instr_per_cell"] == 5.0
+    r8 = bench.roofline("heat1d-3pt", 10 ** 7, 8, 1.0, 1, 1.256, "temporal", Tb=8)
+    assert r8["fp64_instr_source"] == "table (kernel changed since the ncu count)"
+    rs = bench.roofline("heat3d-7pt", 64 ** 3, 1, 1.0, 1, 1.256, "stream3d")
+    assert rs["fp64_instr_source"] == "table (no ncu count recorded)"
