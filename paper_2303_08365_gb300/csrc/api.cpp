@@ -358,8 +358,34 @@ int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
   return kVariantDirect;
 }
 
+// The kernel for a fused step count Tb > 1 that the caller fixed without a
+// variant: the exchange kernel (no recomputed halo) for 3D radius-1 grids
+// its tiling covers, the persistent temporal kernel for the small 2D grids
+// it serves by default, else the overlapped temporal kernel (1D, 2D and 3D
+// radius 1; other plans have no fused kernel and the run reports that).
+int fused_variant(const stencil_plan_s* p) {
+  if (p->ndim == 3 && p->radius == 1) {
+    int ty, tx;
+    return exchange_tiling(p->ndim, p->radius, p->g, sm_count(), &ty, &tx) ? kVariantExchange
+                                                                           : kVariantTemporal;
+  }
+  if (p->ndim == 2 && p->radius == 1 && p->cells() <= ((int64_t)1 << 18) && (p->taps.n == 5 || p->taps.n == 9))
+    return kVariantPersistent;
+  return kVariantTemporal;
+}
+
 bool persistent_eligible(const stencil_plan_s* p) {
   return p->ndim == 2 && p->radius == 1 && p->shape == Shape::kStar && p->taps.n == 5;
+}
+
+// The kernel for one step per launch (Tb = 1 fixed without a variant): the
+// default where it is a one-step kernel, else the streaming or direct sweep.
+int one_step_variant(const stencil_plan_s* p) {
+  const int v = default_variant(p);
+  if (v == kVariantTemporal) return kVariantDirect;  // 1D: fused by default
+  if (v == kVariantPersistent && !persistent_eligible(p))
+    return stream2d_shape_ok(p->ndim, p->radius, p->boundary, p->g) ? kVariantStream : kVariantDirect;
+  return v;
 }
 
 // Resolved (Tb, variant, streaming tile height; 0 = the kernel's default) for
@@ -368,7 +394,7 @@ void choose(const stencil_plan_s* p, int& Tb, int& variant, int& tile_y) {
   tile_y = p->user_tile_y;
   if (p->user_Tb > 0 || p->user_variant > 0) {
     Tb = p->user_Tb > 0 ? p->user_Tb : 1;
-    variant = p->user_variant > 0 ? p->user_variant : default_variant(p);
+    variant = p->user_variant > 0 ? p->user_variant : Tb > 1 ? fused_variant(p) : one_step_variant(p);
     return;
   }
   if (p->tuned_Tb > 0) {
@@ -597,7 +623,11 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   tune_on_first_run(p, d_grid, s);
   int Tb, variant, tile_y;
   choose(p, Tb, variant, tile_y);
-  const bool forced = p->user_Tb > 0 || p->user_variant > 0;
+  // a variant the caller named is an error when the grid cannot use it; a
+  // Tb > 1 fixed without a variant is an error when no fused kernel covers
+  // the plan; any other choice falls back quietly
+  const bool v_user = p->user_variant > 0;
+  const bool tb_user = p->user_Tb > 1 && !v_user;
   int rc = ensure(&p->d_tmp, (size_t)p->cells(), "allocating the ping-pong buffer");
   if (rc) return rc;
   rc = ensure_status(p);
@@ -616,7 +646,7 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
                                                  p->d_tmp, tile_y)
                              : stream2d_eligible(p->ndim, p->radius, p->boundary, p->g, d_grid, p->d_tmp);
   if (variant == kVariantStream && !stream_ok) {
-    if (forced)
+    if (p->user_variant == kVariantStream)
       return fail(STENCIL_ERR_UNSUPPORTED,
                   "the streaming kernel needs a 2D or 3D radius-1 plan, even nx, 16-byte aligned "
                   "buffers and, for periodic grids, nx %% 64 == 0 and ny a multiple of the tile "
@@ -626,17 +656,16 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
   if (variant == kVariantPersistent && Tb > 1) {
     if (p->ndim == 2 && p->radius == 1 && (p->taps.n == 5 || p->taps.n == 9) && Tb <= 8)
       return run_persistent_tb(p, d_grid, T, Tb, s);
-    if (forced) return fail(STENCIL_ERR_UNSUPPORTED, "the persistent temporal kernel covers 2D radius-1 plans");
-    variant = kVariantDirect;
-    Tb = 1;
+    if (v_user) return fail(STENCIL_ERR_UNSUPPORTED, "the persistent temporal kernel covers 2D radius-1 plans");
+    variant = kVariantTemporal;  // keeps Tb where the overlapped kernel covers the plan (checked next)
   }
   if (variant == kVariantPersistent) {
     if (persistent_eligible(p) && T <= (1 << 30)) return run_persistent_step(p, d_grid, T, s);
-    if (forced) return fail(STENCIL_ERR_UNSUPPORTED, "the persistent kernel covers 2D 5-point star plans");
-    variant = kVariantDirect;
+    if (v_user) return fail(STENCIL_ERR_UNSUPPORTED, "the persistent kernel covers 2D 5-point star plans");
+    variant = stream_ok ? kVariantStream : kVariantDirect;
   }
   if (variant == kVariantTemporal && !temporal_supported(p->ndim, p->radius, Tb)) {
-    if (forced)
+    if (v_user || tb_user)
       return fail(STENCIL_ERR_UNSUPPORTED,
                   "temporal blocking covers 2D and 3D radius-1 plans with Tb in {2, 4, 8}, "
                   "and 1D plans of radius 1 or 2 with Tb in {2, 4, 8}");
@@ -647,12 +676,17 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
     const bool ok = Tb >= 2 && Tb <= 8 && exchange_tiling(p->ndim, p->radius, p->g, sm_count(), &ty, &tx) &&
                     ((uintptr_t)d_grid & 15) == 0 && ((uintptr_t)p->d_tmp & 15) == 0;
     if (!ok) {
-      if (forced)
+      if (v_user)
         return fail(STENCIL_ERR_UNSUPPORTED,
                     "the exchange kernel covers 3D radius-1 plans with Tb in {2, 4, 8}, nx a multiple of "
                     "64, at most %d tile columns and tiles of at most 32 rows, on 16-byte aligned buffers",
                     sm_count());
-      variant = stream_ok ? kVariantStream : kVariantDirect;
+      // a Tb fixed without a variant keeps its Tb on the overlapped kernel;
+      // a tuned choice falls back to one step per launch
+      if (tb_user && temporal_supported(p->ndim, p->radius, Tb))
+        variant = kVariantTemporal;
+      else
+        variant = stream_ok ? kVariantStream : kVariantDirect;
     }
   }
   if (variant != kVariantTemporal && variant != kVariantExchange) Tb = 1;

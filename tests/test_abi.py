@@ -169,3 +169,26 @@ def test_old_four_field_tuning_records_are_read(tmp_path):
     if out.stdout.split() == ["1", "2"]:
         pytest.skip("a CUDA device is visible: the key carries its name")
     assert out.stdout.split() == ["4", "3"]
+
+
+def test_fixed_tb_without_variant_keeps_its_tb(stencil):
+    """set_tuning(Tb, 0) keeps the Tb: a fused kernel for Tb > 1 (the
+    exchange kernel where its tiling fits -- on a host without a GPU the SM
+    count reads as 1, so the overlapped kernel), a one-step kernel for Tb = 1."""
+    heat2 = np.array([0, .1, 0, .1, .6, .1, 0, .1, 0])
+    heat3 = np.zeros(27)
+    heat3[[4, 10, 12, 13, 14, 16, 22]] = [.1, .1, .1, .4, .1, .1, .1]
+    cases = [((24, 64, 128), heat3, 1, 4, (stencil.VARIANT_TEMPORAL, stencil.VARIANT_EXCHANGE)),
+             ((10, 20, 70), heat3, 0, 2, (stencil.VARIANT_TEMPORAL,)),       # nx off the 64-column tiles
+             ((96, 96), heat2, 0, 8, (stencil.VARIANT_PERSISTENT,)),        # small 2D grid
+             ((1024, 1024), heat2, 0, 4, (stencil.VARIANT_TEMPORAL,)),
+             ((5000,), np.array([.25, .5, .25]), 0, 2, (stencil.VARIANT_TEMPORAL,)),
+             ((5000,), np.array([.25, .5, .25]), 0, 1, (stencil.VARIANT_DIRECT,)),
+             ((8, 9), np.ones(9) / 9, 1, 1, (stencil.VARIANT_DIRECT,)),         # odd nx: no streaming
+             ((96, 96), heat2, 0, 1, (stencil.VARIANT_PERSISTENT,))]          # one-step persistent
+    for dims, w, bnd, tb, want in cases:
+        h = stencil.stencil_create(dims, 1, w, bnd)
+        stencil.stencil_set_tuning(h, tb, 0)
+        got_tb, got_v = stencil.stencil_get_tuning(h)
+        assert got_tb == tb and got_v in want, (dims, tb, got_tb, got_v)
+        stencil.stencil_destroy(h)

@@ -470,6 +470,64 @@ def test_temporal_unsupported_tb_is_rejected(st):
     p.close()
 
 
+FIXED_TB_CASES = [
+    # shape, radius, boundary, kind, Tb, T, the kernel the library picks
+    ((24, 64, 128), 1, PERIODIC, "heat", 4, 9, "exchange"),
+    ((10, 20, 70), 1, DIRICHLET, "box_rand", 2, 5, "temporal"),     # nx off the 64-column tiles
+    ((96, 96), 1, DIRICHLET, "heat", 8, 19, "persistent"),
+    ((600, 520), 1, PERIODIC, "star_rand", 4, 10, "temporal"),
+    ((5000,), 2, PERIODIC, "star_rand", 2, 7, "temporal"),
+    ((5000,), 1, DIRICHLET, "heat", 1, 3, "direct"),
+]
+
+
+@pytest.mark.parametrize("shape,radius,boundary,kind,Tb,T,want", FIXED_TB_CASES)
+def test_fixed_tb_without_variant_runs_a_fused_kernel(st, shape, radius, boundary, kind, Tb, T, want):
+    """set_tuning(Tb, 0): the library keeps the Tb and picks the kernel;
+    bitwise equal to single direct steps (the same per-cell FMA chain) and
+    within the bar of the oracle."""
+    import torch
+    w = weights_for(kind, len(shape), radius, 900 + Tb)
+    u0 = synth.normal(17, shape)
+    g = torch.from_numpy(u0.copy()).cuda()
+    p = st.Plan(shape, radius, w, boundary)
+    p.set_tuning(Tb, 0)
+    assert p.get_tuning() == (Tb, {"exchange": st.VARIANT_EXCHANGE, "temporal": st.VARIANT_TEMPORAL,
+                                   "persistent": st.VARIANT_PERSISTENT, "direct": st.VARIANT_DIRECT}[want])
+    l0 = st.stencil_launch_count()
+    p.run(g, T)
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    if Tb > 1 and want != "persistent":
+        assert st.stencil_launch_count() - l0 < T     # Tb steps per launch
+    a = g.cpu().numpy()
+    p.close()
+    b = gpu_run(st, u0, w, radius, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+    assert normwise_rel(a, oracle.run(u0, w, radius, boundary, T, nthreads=0)) <= TOL
+
+
+def test_fixed_tb_without_a_fused_kernel_is_refused(st):
+    """A 2D radius-2 plan has no fused kernel: set_tuning(4, 0) makes the run
+    report STENCIL_ERR_UNSUPPORTED instead of dropping the Tb; the automatic
+    choice runs again after set_tuning(0, 0)."""
+    import torch
+    w = weights_for("star_rand", 2, 2, 5)
+    u0 = synth.uniform(3, (64, 64))
+    g = torch.from_numpy(u0.copy()).cuda()
+    p = st.Plan(u0.shape, 2, w, PERIODIC)
+    p.set_tuning(4, 0)
+    with pytest.raises(st.StencilError) as ei:
+        p.run(g, 8)
+    assert ei.value.code == st.ERR_UNSUPPORTED
+    assert np.array_equal(g.cpu().numpy(), u0)      # nothing ran
+    p.set_tuning(0, 0)
+    p.run(g, 8)
+    assert p.status() == 0
+    assert normwise_rel(g.cpu().numpy(), oracle.run(u0, w, 2, PERIODIC, 8, nthreads=0)) <= TOL
+    p.close()
+
+
 def test_autotune_picks_a_candidate_and_keeps_results(st):
     import torch
     shape = (24, 48, 128)
