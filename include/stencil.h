@@ -246,10 +246,13 @@ typedef enum {
                                      intermediate time levels handed between
                                      tiles through an L2-resident ring of
                                      (Tb-1) x 5 grid planes (plan-owned).
-                                     Needs nx a multiple of 64, at most one
-                                     tile column per SM and tiles of at most
-                                     32 rows (a y-x plane of up to about
-                                     32 x 64 cells per SM) */
+                                     Needs nx a multiple of 64 and at most
+                                     one tile column per SM.  A plane taller
+                                     than the co-resident tiles cover (32
+                                     rows each) runs as bands of rows, one
+                                     launch each, every band with a margin of
+                                     Tb-1 rows toward each neighbouring band
+                                     that both bands compute */
 } stencil_variant;
 
 /* Fixes the fused step count Tb (1, 2, 4 or 8) and kernel variant (a

@@ -364,11 +364,8 @@ int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
 // it serves by default, else the overlapped temporal kernel (1D, 2D and 3D
 // radius 1; other plans have no fused kernel and the run reports that).
 int fused_variant(const stencil_plan_s* p) {
-  if (p->ndim == 3 && p->radius == 1) {
-    int ty, tx;
-    return exchange_tiling(p->ndim, p->radius, p->g, sm_count(), &ty, &tx) ? kVariantExchange
-                                                                           : kVariantTemporal;
-  }
+  if (p->ndim == 3 && p->radius == 1)
+    return exchange_fits(p->ndim, p->radius, p->g, sm_count()) ? kVariantExchange : kVariantTemporal;
   if (p->ndim == 2 && p->radius == 1 && p->cells() <= ((int64_t)1 << 18) && (p->taps.n == 5 || p->taps.n == 9))
     return kVariantPersistent;
   return kVariantTemporal;
@@ -526,9 +523,10 @@ int run_persistent_step(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream
   return batch_enqueue(hit, s);
 }
 
-// The exchange kernel's ring and progress counters for Tb (grown on demand).
-int ensure_exchange(stencil_plan_s* p, int Tb, int ntiles) {
-  const size_t cells = exchange_ring_cells(p->g, Tb);
+// The exchange kernel's ring (for bands of up to band_rows rows) and
+// progress counters for Tb (grown on demand).
+int ensure_exchange(stencil_plan_s* p, int Tb, int band_rows, int ntiles) {
+  const size_t cells = exchange_ring_cells(p->g, Tb, band_rows);
   if (p->ring_cells < cells) {
     cudaFree(p->d_ring);
     p->d_ring = nullptr;
@@ -547,16 +545,23 @@ int ensure_exchange(stencil_plan_s* p, int Tb, int ntiles) {
   return STENCIL_OK;
 }
 
-// One Tb-step launch of the exchange kernel from a to b.
+// One Tb-step block of the exchange kernel from a to b: one launch per band
+// of rows (one band unless the plane is taller than the co-resident tiles
+// cover), each after clearing the progress counters.
 int launch_exchange_block(stencil_plan_s* p, const double* a, double* b, int Tb, cudaStream_t s) {
-  ExchangeLaunch L;
-  if (!exchange_tiling(p->ndim, p->radius, p->g, sm_count(), &L.tiles_y, &L.tiles_x))
+  const int sms = sm_count();
+  if (!exchange_fits(p->ndim, p->radius, p->g, sms))
     return fail(STENCIL_ERR_UNSUPPORTED, "the grid does not fit the exchange kernel's tiling");
-  const int ntiles = L.tiles_y * L.tiles_x;
-  int rc = ensure_exchange(p, Tb, ntiles);
+  const std::vector<ExchangeBand> bands = exchange_bands(p->g, p->boundary == kPeriodic, Tb, sms);
+  ExchangeLaunch L;
+  L.tiles_x = (int)(p->g.nx / 64);
+  int max_rows = 0, max_ty = 0;
+  for (const ExchangeBand& band : bands) {
+    max_rows = std::max(max_rows, band.rows);
+    max_ty = std::max(max_ty, band.tiles_y);
+  }
+  int rc = ensure_exchange(p, Tb, max_rows, max_ty * L.tiles_x);
   if (rc) return rc;
-  CUDA_TRY(cudaMemsetAsync(p->d_xcnt, 0, exchange_counter_words(ntiles) * sizeof(unsigned int), s),
-           "clearing the exchange counters");
   L.g = p->g;
   L.src = a;
   L.dst = b;
@@ -566,8 +571,14 @@ int launch_exchange_block(stencil_plan_s* p, const double* a, double* b, int Tb,
   L.wdev = p->d_w;
   L.Tb = Tb;
   L.spin_limit = kSpinLimitNs;
-  cudaError_t e = launch_exchange(p->shape, p->boundary, L, s);
-  if (e != cudaSuccess) return cuda_fail(e, "launching the exchange kernel");
+  for (const ExchangeBand& band : bands) {
+    CUDA_TRY(cudaMemsetAsync(p->d_xcnt, 0, exchange_counter_words(band.tiles_y * L.tiles_x) * sizeof(unsigned int),
+                             s),
+             "clearing the exchange counters");
+    L.band = band;
+    cudaError_t e = launch_exchange(p->shape, p->boundary, L, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launching the exchange kernel");
+  }
   return STENCIL_OK;
 }
 
@@ -672,15 +683,13 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
     variant = default_variant(p) == kVariantStream && stream_ok ? kVariantStream : kVariantDirect;
   }
   if (variant == kVariantExchange) {
-    int ty, tx;
-    const bool ok = Tb >= 2 && Tb <= 8 && exchange_tiling(p->ndim, p->radius, p->g, sm_count(), &ty, &tx) &&
+    const bool ok = Tb >= 2 && Tb <= 8 && exchange_fits(p->ndim, p->radius, p->g, sm_count()) &&
                     ((uintptr_t)d_grid & 15) == 0 && ((uintptr_t)p->d_tmp & 15) == 0;
     if (!ok) {
       if (v_user)
         return fail(STENCIL_ERR_UNSUPPORTED,
                     "the exchange kernel covers 3D radius-1 plans with Tb in {2, 4, 8}, nx a multiple of "
-                    "64, at most %d tile columns and tiles of at most 32 rows, on 16-byte aligned buffers",
-                    sm_count());
+                    "64 and at most %d tile columns of 64, on 16-byte aligned buffers", sm_count());
       // a Tb fixed without a variant keeps its Tb on the overlapped kernel;
       // a tuned choice falls back to one step per launch
       if (tb_user && temporal_supported(p->ndim, p->radius, Tb))

@@ -119,6 +119,13 @@ struct XParams {
   int* status;
   const double* wdev;
   int nz, ny, nx;
+  // the band of rows this launch covers: band row b is grid row yb + b
+  // (periodic grids wrap, so yb may be negative), b in [0, nyb); rows
+  // [own_lo, own_hi) go to the output, the others are a margin that the
+  // neighbouring band owns.  The ring holds band rows; ring_wrap: the band is
+  // the whole periodic grid, so band rows wrap too (else a row outside the
+  // band reads as zero: only margin rows depend on it)
+  int yb, nyb, own_lo, own_hi, ring_wrap;
   int tiles_x, h_lo, h_extra;  // tile row j: h_lo + (j < h_extra) rows
   int tiles_y;
   int Tb, iters, qoff;
@@ -251,48 +258,35 @@ __device__ __forceinline__ bool wait_counters(const XParams& P, const int (&nb)[
   return verdict > 0;
 }
 
-// Posts the TMA boxes of plane j of a unit: smem rows ra .. rb (global rows
-// y0-1+ra .. y0-1+rb, wrapped for periodic grids: at most three contiguous
-// segments), each segment as one box of its exact height when the maps have
-// one, else row by row.  `z` is the plane's coordinate in the input grid
-// (s == 1) or its ring slot (-1: a plane of zeros) and `st` the ring stage.
-template <bool PERIODIC>
+// Posts the TMA boxes of plane j of a unit: smem rows ra .. rb hold source
+// rows ytop + ra .. ytop + rb (grid rows of the input, s == 1; band rows of
+// the ring).  With wrap > 0 those rows wrap modulo wrap (a periodic axis):
+// contiguous segments split at the wrap, at most three since a unit spans at
+// most wrap + 2 rows.  Each segment is one box of its exact height when the
+// maps have one (and it fits the source's `limit` rows), else row by row.
+// Rows outside a source that does not wrap read as zeros (TMA out-of-bounds
+// fill).  `z` is the plane's coordinate in the input grid (s == 1) or its
+// ring slot (-1: a plane of zeros) and `st` the ring stage.
 __device__ __forceinline__ void post_plane(const XParams& P, XSlot& sl, uint64_t* bar, int j, int ra, int rb,
-                                           int y0, int x0, int s, int z, int st, uint64_t keep) {
-  int seg_r[3], seg_y[3], seg_n[3], nseg = 0;
-  int a = ra, b = rb;
-  if (PERIODIC && y0 - 1 + a < 0) {  // the row above the grid: the last row
-    seg_r[nseg] = a;
-    seg_y[nseg] = P.ny - 1;
-    seg_n[nseg++] = 1;
-    ++a;
-  }
-  int tail = -1;
-  if (PERIODIC && b >= a && y0 - 1 + b >= P.ny) {  // the row below the grid: the first row
-    tail = b;
-    --b;
-  }
-  if (b >= a) {
-    seg_r[nseg] = a;
-    seg_y[nseg] = y0 - 1 + a;
-    seg_n[nseg++] = b - a + 1;
-  }
-  if (tail >= 0) {
-    seg_r[nseg] = tail;
-    seg_y[nseg] = 0;
-    seg_n[nseg++] = 1;
-  }
-  for (int g = 0; g < nseg; ++g) {
-    int r = seg_r[g], y = seg_y[g], n = seg_n[g];
+                                           int ytop, int wrap, int limit, int x0, int s, int z, int st,
+                                           uint64_t keep) {
+  for (int a = ra; a <= rb;) {
+    int y = ytop + a;
+    int n = rb - a + 1;
+    if (wrap > 0) {
+      y = wrapi(y, wrap);
+      n = min(n, wrap - y);
+    }
     const int k = n - P.h_lo + 1;  // the box of exactly n rows, if there is one
-    const bool whole = n > 1 && k >= 1 && k < kMaps && n <= P.ny;
+    const bool whole = n > 1 && k >= 1 && k < kMaps && n <= limit;
     for (int e = 0; e < (whole ? 1 : n); ++e) {
       const int which = whole ? k : 0;
       if (s == 1)
-        tma_load_3d(&sl.plane[j][r + e][0], &P.map_in[which], x0, y + e, z, bar);
+        tma_load_3d(&sl.plane[j][a + e][0], &P.map_in[which], x0, y + e, z, bar);
       else  // ring lines stay in L2 until their slot is rewritten
-        tma_load_4d_hint(&sl.plane[j][r + e][0], &P.map_ring[which], x0, y + e, z, st, bar, keep);
+        tma_load_4d_hint(&sl.plane[j][a + e][0], &P.map_ring[which], x0, y + e, z, st, bar, keep);
     }
+    a += n;
   }
 }
 
@@ -304,7 +298,8 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tx = blockIdx.x % P.tiles_x, ty = blockIdx.x / P.tiles_x;
   const int x0 = tx * kXW;
-  const int y0 = ty * P.h_lo + min(ty, P.h_extra);
+  const int yl0 = ty * P.h_lo + min(ty, P.h_extra);  // band row of the tile's first row
+  const int y0 = P.yb + yl0;                           // its grid row (periodic margins: may lie outside)
   const int h = P.h_lo + (ty < P.h_extra ? 1 : 0);
   const int Tb = P.Tb;
   if (threadIdx.x == 0) {
@@ -336,12 +331,10 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
       for (int dx = -1; dx <= 1; ++dx) {
         if ((dy == 0 && dx == 0) || (!BOX && dy != 0 && dx != 0)) continue;
         int jy = ty + dy, jx = tx + dx;
-        if (PERIODIC) {
-          jy = wrapi(jy, P.tiles_y);
-          jx = wrapi(jx, P.tiles_x);
-        } else if (jy < 0 || jy >= P.tiles_y || jx < 0 || jx >= P.tiles_x) {
-          continue;
-        }
+        if (PERIODIC) jx = wrapi(jx, P.tiles_x);
+        else if (jx < 0 || jx >= P.tiles_x) continue;
+        if (P.ring_wrap) jy = wrapi(jy, P.tiles_y);
+        else if (jy < 0 || jy >= P.tiles_y) continue;  // the band's edge: no tile beyond it
         nb[nnb++] = jy * P.tiles_x + jx;
       }
     }
@@ -403,7 +396,11 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
             z = exists ? wrapi(qq, K) : -1;
           }
           const int ra = (BOX || j == 1) ? 0 : 1, rb = (BOX || j == 1) ? h + 1 : h;
-          post_plane<PERIODIC>(P, sl, &S.full[slot], j, ra, rb, y0, x0, s, z, s - 2, keep);
+          if (s == 1)
+            post_plane(P, sl, &S.full[slot], j, ra, rb, y0 - 1, PERIODIC ? P.ny : 0, P.ny, x0, s, z, 0, keep);
+          else
+            post_plane(P, sl, &S.full[slot], j, ra, rb, yl0 - 1, P.ring_wrap ? P.nyb : 0, P.nyb, x0, s, z, s - 2,
+                       keep);
         }
         // x-halo pairs: box: every plane and row; star: plane q at the tile's rows
         const int hrows = BOX ? 3 * (h + 2) : h;
@@ -413,23 +410,22 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
           const int j = BOX ? k / (h + 2) : 1;
           const int r = BOX ? k % (h + 2) : k + 1;
           const int qq = q - 1 + j;
-          int y = y0 - 1 + r;
           int x = side ? x0 + kXW : x0 - 2;
           bool valid = true;
-          if (PERIODIC) {
-            y = wrapi(y, P.ny);
-            x = wrapi(x, P.nx);
-          } else {
-            valid = y >= 0 && y < P.ny && x >= 0 && x < P.nx && qq >= 0 && qq < P.nz;
-          }
+          if (PERIODIC) x = wrapi(x, P.nx);
+          else valid = x >= 0 && x < P.nx && qq >= 0 && qq < P.nz;
           const double* g = P.src;
-          if (valid) {
-            if (s == 1) {
-              const int zc = PERIODIC ? wrapi(qq, P.nz) : qq;
-              g = P.src + ((int64_t)zc * P.ny + y) * P.nx + x;
-            } else {
-              g = P.ring + (((int64_t)(s - 2) * K + wrapi(qq, K)) * P.ny + y) * P.nx + x;
-            }
+          if (s == 1) {
+            int y = y0 - 1 + r;
+            if (PERIODIC) y = wrapi(y, P.ny);
+            else valid = valid && y >= 0 && y < P.ny;
+            const int zc = PERIODIC ? wrapi(qq, P.nz) : qq;
+            if (valid) g = P.src + ((int64_t)zc * P.ny + y) * P.nx + x;
+          } else {
+            int y = yl0 - 1 + r;
+            if (P.ring_wrap) y = wrapi(y, P.nyb);
+            else valid = valid && y >= 0 && y < P.nyb;
+            if (valid) g = P.ring + (((int64_t)(s - 2) * K + wrapi(qq, K)) * P.nyb + y) * P.nx + x;
           }
           if (s == 1)
             cp_async16_cg(&sl.halo[j][r][side], g, valid);
@@ -517,26 +513,29 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
       int r0 = warp - rot;
       if (r0 < 0) r0 += kWarps;
       const bool last = s == Tb;
-      double* out = last ? P.dst + (int64_t)q * P.ny * P.nx
-                         : P.ring + ((int64_t)(s - 1) * K + wrapi(q, K)) * P.ny * P.nx;
-      out += x0 + 2 * lane;
+      // stage Tb: the output, grid rows (only the band's own); else the ring, band rows
+      // (element offset of the tile's row 0; a margin tile's may be negative
+      // in the output, whose rows it does not write)
+      const int64_t base = (last ? ((int64_t)q * P.ny + y0) * P.nx
+                                 : (((int64_t)(s - 1) * K + wrapi(q, K)) * P.nyb + yl0) * P.nx) +
+                           x0 + 2 * lane;
       if (r0 + kWarps < h) {
         const int rr[2] = {r0, r0 + kWarps};
         double a[2][2];
         unit_rows<NT, BOX, 2>(sl, W, rr, lane, a);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-          double* o = out + (int64_t)(y0 + rr[k]) * P.nx;
-          if (last) st_global_v2_cs(o, a[k][0], a[k][1]);
-          else st_global_v2_hint(o, a[k][0], a[k][1], keep);
+          const int64_t off = base + (int64_t)rr[k] * P.nx;
+          if (!last) st_global_v2_hint(P.ring + off, a[k][0], a[k][1], keep);
+          else if (y0 + rr[k] >= P.own_lo && y0 + rr[k] < P.own_hi) st_global_v2_cs(P.dst + off, a[k][0], a[k][1]);
         }
       } else if (r0 < h) {
         const int rr[1] = {r0};
         double a[1][2];
         unit_rows<NT, BOX, 1>(sl, W, rr, lane, a);
-        double* o = out + (int64_t)(y0 + r0) * P.nx;
-        if (last) st_global_v2_cs(o, a[0][0], a[0][1]);
-        else st_global_v2_hint(o, a[0][0], a[0][1], keep);
+        const int64_t off = base + (int64_t)r0 * P.nx;
+        if (!last) st_global_v2_hint(P.ring + off, a[0][0], a[0][1], keep);
+        else if (y0 + r0 >= P.own_lo && y0 + r0 < P.own_hi) st_global_v2_cs(P.dst + off, a[0][0], a[0][1]);
       }
       // this thread's share of unit (i, s) is written (stage Tb: the output).
       // Its stores are generic-proxy writes that TMA (the async proxy) reads
@@ -566,12 +565,13 @@ bool encode_in(CUtensorMap* map, const double* base, const Geom& g, int rows) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool encode_ring(CUtensorMap* map, const double* base, const Geom& g, int K, int stages, int rows) {
+// The ring: {nx, band rows, K slots, stages}.
+bool encode_ring(CUtensorMap* map, const double* base, int nx, int nyb, int K, int stages, int rows) {
   auto enc = tensor_map_encoder();
   if (!enc) return false;
-  cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)K, (cuuint64_t)stages};
-  cuuint64_t strides[3] = {(cuuint64_t)g.nx * sizeof(double), (cuuint64_t)g.nx * g.ny * sizeof(double),
-                           (cuuint64_t)K * g.nx * g.ny * sizeof(double)};
+  cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)nyb, (cuuint64_t)K, (cuuint64_t)stages};
+  cuuint64_t strides[3] = {(cuuint64_t)nx * sizeof(double), (cuuint64_t)nx * nyb * sizeof(double),
+                           (cuuint64_t)K * nx * nyb * sizeof(double)};
   cuuint32_t box[4] = {(cuuint32_t)kXW, (cuuint32_t)rows, 1, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<double*>(base), dims, strides, box, estr,
@@ -598,13 +598,19 @@ cudaError_t launch_x(const ExchangeLaunch& L, cudaStream_t stream) {
   if (x_occupancy<NT, BOX, PERIODIC>() < 1) return cudaErrorInvalidConfiguration;
   XParams P;
   const Geom& g = L.g;
+  const ExchangeBand& b = L.band;
+  if (b.tiles_y < 1 || b.rows < 1 || (b.rows + b.tiles_y - 1) / b.tiles_y > kHMax || b.own_lo < 0 ||
+      b.own_hi > g.ny || b.own_lo >= b.own_hi || b.own_lo < b.y_base || b.own_hi > b.y_base + b.rows ||
+      (b.whole && (b.y_base != 0 || b.rows != g.ny)))
+    return cudaErrorInvalidValue;
   const int stages = L.Tb - 1 > 0 ? L.Tb - 1 : 1;
+  const int h_lo = b.rows / b.tiles_y;
   for (int k = 0; k < kMaps; ++k) {
-    // a box taller than the grid is never used (the kernel checks n <= ny)
-    int rows = k == 0 ? 1 : g.ny / L.tiles_y + k - 1;
-    if (rows > g.ny) rows = 1;
-    if (!encode_in(&P.map_in[k], L.src, g, rows) ||
-        !encode_ring(&P.map_ring[k], L.ring, g, ring_k<BOX>(), stages, rows))
+    // a box taller than its tensor is never used (the kernel checks n against
+    // the grid's rows for the input and the band's rows for the ring)
+    const int rows = k == 0 ? 1 : h_lo + k - 1;
+    if (!encode_in(&P.map_in[k], L.src, g, rows > g.ny ? 1 : rows) ||
+        !encode_ring(&P.map_ring[k], L.ring, g.nx, b.rows, ring_k<BOX>(), stages, rows > b.rows ? 1 : rows))
       return cudaErrorInvalidValue;
   }
   P.src = L.src;
@@ -616,16 +622,21 @@ cudaError_t launch_x(const ExchangeLaunch& L, cudaStream_t stream) {
   P.nz = g.nz;
   P.ny = g.ny;
   P.nx = g.nx;
+  P.yb = b.y_base;
+  P.nyb = b.rows;
+  P.own_lo = b.own_lo;
+  P.own_hi = b.own_hi;
+  P.ring_wrap = PERIODIC && b.whole ? 1 : 0;
   P.tiles_x = L.tiles_x;
-  P.tiles_y = L.tiles_y;
-  P.h_lo = g.ny / L.tiles_y;
-  P.h_extra = g.ny % L.tiles_y;
+  P.tiles_y = b.tiles_y;
+  P.h_lo = h_lo;
+  P.h_extra = b.rows % b.tiles_y;
   P.Tb = L.Tb;
   P.qoff = PERIODIC ? -(L.Tb - 1) : 0;
   P.iters = PERIODIC ? g.nz + 3 * L.Tb - 3 : g.nz + 2 * L.Tb - 2;
   P.spin_limit = L.spin_limit;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(L.tiles_x * L.tiles_y), 1, 1);
+  cfg.gridDim = dim3((unsigned)(L.tiles_x * b.tiles_y), 1, 1);
   cfg.blockDim = dim3(kThreadsX, 1, 1);
   cfg.dynamicSmemBytes = sizeof(XSmem);
   cfg.stream = stream;
@@ -641,26 +652,43 @@ cudaError_t launch_x(const ExchangeLaunch& L, cudaStream_t stream) {
 
 }  // namespace
 
-bool exchange_tiling(int ndim, int radius, const Geom& g, int sms, int* tiles_y, int* tiles_x) {
-  if (ndim != 3 || radius != 1 || g.nx % kXW != 0) return false;
+bool exchange_fits(int ndim, int radius, const Geom& g, int sms) {
+  return ndim == 3 && radius == 1 && g.nx % kXW == 0 && g.nx / kXW <= sms && g.ny >= 1 && g.nz >= 1;
+}
+
+std::vector<ExchangeBand> exchange_bands(const Geom& g, bool periodic, int Tb, int sms) {
+  std::vector<ExchangeBand> out;
   const int tx = g.nx / kXW;
-  if (tx > sms) return false;
-  const int ty = g.ny < sms / tx ? g.ny : sms / tx;
-  if (ty < 1 || (g.ny + ty - 1) / ty > kHMax) return false;
-  *tiles_x = tx;
-  *tiles_y = ty;
-  return true;
+  const int ty_max = sms / tx;                 // tile rows that are co-resident with every column
+  const int max_rows = ty_max * kHMax;
+  if (g.ny <= max_rows) {
+    out.push_back({0, g.ny, 0, g.ny, g.ny < ty_max ? g.ny : ty_max, true});
+    return out;
+  }
+  // interior bands carry a margin of Tb - 1 rows on each side (radius 1:
+  // stage s reads rows one further out than stage s-1 wrote; the first stage
+  // reads the input, which holds every row)
+  const int H = Tb - 1;
+  const int room = max_rows - 2 * H;          // owned rows of a band with two margins (>= 18)
+  const int nb = (g.ny + room - 1) / room;
+  for (int k = 0; k < nb; ++k) {
+    const int lo = (int)((int64_t)k * g.ny / nb), hi = (int)((int64_t)(k + 1) * g.ny / nb);
+    const int top = periodic || k > 0 ? H : 0, bot = periodic || k < nb - 1 ? H : 0;
+    const int rows = hi - lo + top + bot;
+    out.push_back({lo - top, rows, lo, hi, rows < ty_max ? rows : ty_max, false});
+  }
+  return out;
 }
 
 int exchange_counter_words(int tiles) { return tiles * kMaxStages; }
 
-size_t exchange_ring_cells(const Geom& g, int Tb) {
-  return (size_t)(Tb > 1 ? Tb - 1 : 1) * ring_k<true>() * (size_t)g.ny * (size_t)g.nx;
+size_t exchange_ring_cells(const Geom& g, int Tb, int band_rows) {
+  return (size_t)(Tb > 1 ? Tb - 1 : 1) * ring_k<true>() * (size_t)band_rows * (size_t)g.nx;
 }
 
 cudaError_t launch_exchange(Shape shape, int boundary, const ExchangeLaunch& L, cudaStream_t stream) {
   const bool per = boundary == kPeriodic;
-  if (L.Tb < 2 || L.Tb > kMaxStages || L.tiles_x < 1 || L.tiles_y < 1) return cudaErrorInvalidValue;
+  if (L.Tb < 2 || L.Tb > kMaxStages || L.tiles_x < 1 || L.band.tiles_y < 1) return cudaErrorInvalidValue;
   if (shape == Shape::kBox)
     return per ? launch_x<27, true, true>(L, stream) : launch_x<27, true, false>(L, stream);
   return per ? launch_x<7, false, true>(L, stream) : launch_x<7, false, false>(L, stream);

@@ -107,24 +107,38 @@ cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int
                             cudaStream_t stream, bool equal = false);
 
 // Temporal blocking without recomputation (3D radius 1, star or box, Tb >= 2):
-// one co-resident CTA per 64-column tile of the (y, x) plane, intermediate
-// time levels handed between tiles through a ring of Tb-1 x 5 grid planes.
+// one co-resident CTA per 64-column tile of a band of rows of the (y, x)
+// plane, intermediate time levels handed between tiles through a ring of
+// Tb-1 x 5 (box: 6) band planes.  A plane taller than the co-resident tiles
+// cover (32 rows each) is cut into bands, one launch each, every band with a
+// margin of Tb-1 rows toward each neighbouring band: the rows its last stage
+// may get wrong at an edge whose neighbour rows it does not compute.
+struct ExchangeBand {
+  int y_base;          // grid row of the band's first row (periodic: may be negative)
+  int rows;            // rows of the band, margins included
+  int own_lo, own_hi;  // grid rows the band writes to the output
+  int tiles_y;         // tile rows (tiles of at most 32 rows)
+  bool whole;          // the band is the whole plane (periodic rows wrap within it)
+};
 struct ExchangeLaunch {
   Geom g;
   const double* src;       // time t (16-byte aligned)
   double* dst;             // time t + Tb (16-byte aligned, not src)
-  double* ring;            // exchange_ring_cells(g, Tb) doubles
+  double* ring;            // exchange_ring_cells(g, Tb, band.rows) doubles
   unsigned int* counters;  // exchange_counter_words(tiles) words, zero before the launch
   int* status;
   const double* wdev;
   int Tb;
-  int tiles_y, tiles_x;    // from exchange_tiling
+  int tiles_x;             // nx / 64
+  ExchangeBand band;
   long long spin_limit;    // ns
 };
-// The tile grid for `sms` co-resident CTAs; false when the shape does not fit
-// the kernel (not 3D radius 1, nx not a multiple of 64, tiles taller than 32).
-bool exchange_tiling(int ndim, int radius, const Geom& g, int sms, int* tiles_y, int* tiles_x);
-size_t exchange_ring_cells(const Geom& g, int Tb);
+// True when the kernel takes the shape: 3D radius 1, nx a multiple of 64, at
+// most `sms` tile columns.
+bool exchange_fits(int ndim, int radius, const Geom& g, int sms);
+// The bands of a shape that fits, for `sms` co-resident CTAs and Tb steps.
+std::vector<ExchangeBand> exchange_bands(const Geom& g, bool periodic, int Tb, int sms);
+size_t exchange_ring_cells(const Geom& g, int Tb, int band_rows);
 int exchange_counter_words(int tiles);
 cudaError_t launch_exchange(Shape shape, int boundary, const ExchangeLaunch& L, cudaStream_t stream);
 

@@ -388,6 +388,13 @@ EXCHANGE_CASES = [
     ((7, 150, 64), PERIODIC, "heat", 4, 4),         # 150 one-row tiles in one column
     ((6, 400, 128), DIRICHLET, "box_rand", 2, 7),   # tiles of 5 and 6 rows
     ((31, 64, 256), PERIODIC, "star_rand", 4, 12),
+    # planes taller than 152 co-resident tiles of 32 rows cover: bands of rows,
+    # one launch each, with Tb - 1 margin rows toward each neighbouring band
+    ((6, 300, 2432), PERIODIC, "heat", 2, 5),        # 38 tile columns: 3 bands, margins wrap
+    ((5, 150, 4864), DIRICHLET, "box_rand", 8, 17),  # 76 tile columns: 3 bands of 57-64 rows
+    ((4, 40, 9728), PERIODIC, "box_rand", 8, 16),    # one tile row per band, margins of 7 rows
+    ((9, 100, 9728), DIRICHLET, "heat", 4, 9),       # 4 bands
+    ((12, 70, 4864), PERIODIC, "star_rand", 4, 12),  # 2 bands, each the other's neighbour twice
 ]
 
 
@@ -407,7 +414,7 @@ def test_exchange_kernel_matches_single_steps_bitwise(st, shape, boundary, kind,
 
 def test_exchange_kernel_rejects_shapes_it_cannot_take(st):
     import torch
-    for shape, radius in (((9, 30, 100), 1), ((40, 128), 1), ((9, 30, 64), 2)):
+    for shape, radius in (((9, 30, 100), 1), ((40, 128), 1), ((9, 30, 64), 2), ((3, 4, 64 * 160), 1)):
         w = np.zeros((2 * radius + 1,) * len(shape))
         w[(radius,) * len(shape)] = 1.0
         p = st.Plan(shape, radius, w, PERIODIC)
@@ -417,6 +424,42 @@ def test_exchange_kernel_rejects_shapes_it_cannot_take(st):
             p.run(g, 4)
         assert e.value.code == st.ERR_UNSUPPORTED
         p.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("boundary", [PERIODIC, DIRICHLET])
+def test_exchange_bands_at_the_1024_plane(st, boundary):
+    """Table 1's 3D plane (1024 x 1024) on fewer planes: four bands per
+    Tb-block.  Bitwise equal to single direct steps over the whole grid, and
+    oracle windows at band edges (rows 253-259 straddle the first interior
+    edge at Tb = 4) and at the grid's corners."""
+    import torch
+    shape = (24, 1024, 1024)
+    w = weights_for("star_rand", 3, 1, 41)
+    u0 = synth.normal(41, shape)
+    g = torch.empty(shape, dtype=torch.float64, device="cuda")
+    ref = torch.empty_like(g)
+    p = st.Plan(shape, 1, w, boundary)
+    q = st.Plan(shape, 1, w, boundary)
+    q.set_tuning(1, st.VARIANT_DIRECT)
+    for Tb in (4, 8):
+        T = 2 * Tb + 1
+        p.set_tuning(Tb, st.VARIANT_EXCHANGE)
+        g.copy_(torch.from_numpy(u0))
+        l0 = st.stencil_launch_count()
+        p.run(g, T)
+        assert p.status() == 0
+        assert st.stencil_launch_count() - l0 >= 2 * 4      # four bands per block
+        ref.copy_(torch.from_numpy(u0))
+        q.run(ref, T)
+        assert torch.equal(g, ref), Tb
+        for lo, hi in [((0, 248, 0), (3, 264, 70)), ((10, 500, 960), (14, 520, 1024)),
+                       ((21, 1016, 0), (24, 1024, 8)), ((0, 0, 1000), (2, 6, 1024))]:
+            want = oracle.run_window(u0, w, 1, boundary, T, lo, hi)
+            sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+            assert normwise_rel(g[sl].cpu().numpy(), want) <= TOL, (Tb, lo, hi)
+    p.close()
+    q.close()
 
 
 @pytest.mark.slow
