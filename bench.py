@@ -16,6 +16,7 @@ prints one JSON line.
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -164,11 +165,20 @@ KERNEL_SOURCES = {"stream3d": ["stream.cu", "ptx.cuh", "taps.cuh"],
                   "adjoint": ["varcoef.cu", "taps.cuh"]}
 
 
+def _code_only(text):
+    """C++/CUDA source without its comments and blank lines (a comment edit
+    leaves the recorded counters valid)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def kernel_source_hash(kernel):
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2303_08365_gb300", "csrc")
     for f in KERNEL_SOURCES.get(kernel, []):
-        h.update(open(os.path.join(cs, f), "rb").read())
+        with open(os.path.join(cs, f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -428,30 +438,44 @@ def shared_sum_instr(name, variant, Tb):
     return None
 
 
-def form_forced(st, name, shape, radius, weights, boundary, T, u0, stream, peak, Tb, variant, reps=1):
+def form_forced(st, name, shape, radius, weights, boundary, T, u0, stream, peak, Tb, variant, reps=1,
+                traffic_key=None):
     """One constant-weight workload on a forced (Tb, variant), with its roofline:
-    FP64 instructions per cell include the periodic z-halo the exchange kernel
-    recomputes ((Tb-1)/nz of the planes)."""
+    FP64 instructions per cell include what the exchange kernel computes
+    twice (the periodic z-halo, (Tb-1)/nz of the planes, and the margin rows
+    of a plane cut into bands).  `u0`: the initial grid, or a seed for a
+    uniform grid drawn on the device."""
     import torch
-    grid = torch.from_numpy(u0).cuda()
+    if isinstance(u0, np.ndarray):
+        grid = torch.from_numpy(u0).cuda()
+    else:  # a seed: the grid is drawn on the device (large grids)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(int(u0))
+        grid = torch.rand(shape, dtype=torch.float64, device="cuda", generator=gen)
     plan = st.Plan(shape, radius, weights, boundary)
     plan.set_tuning(Tb, variant)
     ms, launches = time_plan(st, plan, grid, T, reps, stream)
     assert plan.status() == 0
+    vname = st.stencil_variant_name(variant)
+    bands = plan.exchange_layout(Tb) if vname == "exchange" else None
     plan.close()
     del grid
     torch.cuda.empty_cache()
     cells = int(np.prod(shape))
-    vname = st.stencil_variant_name(variant)
     counted = recorded_instr(variant_kernel(vname, len(shape)), name)
     instr = INSTR[name] if counted is None else counted
-    if vname == "exchange" and boundary == 1:
-        instr *= 1 + (Tb - 1) / shape[0]  # the stage skew's extra planes
-    return {"workload": f"{name} {'x'.join(map(str, shape))} T={T} {'periodic' if boundary else 'dirichlet0'}",
-            "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3), "Tb": Tb,
-            "variant": vname, "launches": launches,
-            "roofline": roofline(name, cells, T, ms, launches, peak, variant_kernel(vname, len(shape)), Tb=Tb,
-                                 instr=instr)}
+    if vname == "exchange":
+        if boundary == 1:
+            instr *= 1 + (Tb - 1) / shape[0]  # the stage skew's extra planes
+        instr *= bands[1] / shape[1]          # margin rows that two bands both compute
+    out = {"workload": f"{name} {'x'.join(map(str, shape))} T={T} {'periodic' if boundary else 'dirichlet0'}",
+           "gstencil_per_s": round(cells * T / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3), "Tb": Tb,
+           "variant": vname, "launches": launches,
+           "roofline": roofline(name, cells, T, ms, launches, peak, variant_kernel(vname, len(shape)), Tb=Tb,
+                                instr=instr, traffic_key=traffic_key)}
+    if bands is not None:
+        out["bands"] = {"count": bands[0], "rows_computed": bands[1], "rows": shape[1]}
+    return out
 
 
 # The paper's eight benchmark stencils at its own problem sizes (Table 1),
@@ -999,6 +1023,15 @@ def main():
                 forms[f"temporal_tb{tb}"] = form_forced(st, "heat3d-7pt", HEADLINE["shape"], 1,
                                                         synth.heat_weights(3, HEADLINE["alpha"]), 1, HEADLINE["T"],
                                                         h["u0"], stream, peak_tflops, tb, st.VARIANT_EXCHANGE)
+        if "temporal" in want:
+            # Table 1's Heat-3D grid size (1024^3; periodic, as the headline):
+            # 1024^2 planes are cut into four bands of rows per Tb-block; 40 steps
+            shp = (1024, 1024, 1024)
+            for tb in (4, 8):
+                forms[f"temporal_1024_tb{tb}"] = form_forced(
+                    st, "heat3d-7pt", shp, 1, synth.heat_weights(3, HEADLINE["alpha"]), 1, 40,
+                    synth.SEED_HEAT3D + 300, stream, peak_tflops, tb, st.VARIANT_EXCHANGE,
+                    traffic_key=f"heat3d-7pt-1024cube@tb{tb}")
         if "box2d" in want:
             shp = (16384, 16384)
             forms["box2d"] = form_const(st, "box2d-9pt", shp, 1, synth.box_weights(2, 1.0 / 9.0), 1, 1000,

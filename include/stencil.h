@@ -288,6 +288,15 @@ int stencil_set_tile(stencil_plan p, int tile_x, int tile_y);
  * choice. */
 int stencil_get_tile(stencil_plan p, int* tile_x, int* tile_y);
 
+/* How the exchange kernel (STENCIL_VARIANT_EXCHANGE) cuts p's (y, x) plane
+ * for Tb (2, 4 or 8) on the current device: *nbands receives the number of
+ * bands of rows (one launch each per Tb-step block) and *rows_computed the
+ * rows the bands compute in total -- ny, plus the Tb-1 margin rows that two
+ * neighbouring bands both compute.  Errors: STENCIL_ERR_ARG for a NULL
+ * argument or another Tb; STENCIL_ERR_UNSUPPORTED when the kernel does not
+ * take the plan. */
+int stencil_exchange_layout(stencil_plan p, int Tb, int* nbands, int64_t* rows_computed);
+
 /* Times the candidate (Tb, variant) pairs -- and, for the 3D streaming
  * kernel, each tile height -- on d_grid (device, contents are destroyed) for
  * probe_steps steps each, after a warm-up, and keeps the fastest for p (and

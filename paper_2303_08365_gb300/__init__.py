@@ -73,6 +73,7 @@ SIGNATURES = [
     ("stencil_get_tuning", ctypes.c_int, [_VP, _IP, _IP]),
     ("stencil_set_tile", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("stencil_get_tile", ctypes.c_int, [_VP, _IP, _IP]),
+    ("stencil_exchange_layout", ctypes.c_int, [_VP, ctypes.c_int, _IP, ctypes.POINTER(ctypes.c_int64)]),
     ("stencil_autotune", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _DP]),
     ("stencil_variant_name", ctypes.c_char_p, [ctypes.c_int]),
     ("stencil_last_error", ctypes.c_char_p, []),
@@ -335,6 +336,12 @@ def stencil_selftest_barrier_timeout(limit_ms=20.0, stream=None):
     return lib().stencil_selftest_barrier_timeout(float(limit_ms), _stream(stream))
 
 
+def stencil_exchange_layout(h, Tb):
+    nb, rows = ctypes.c_int(0), ctypes.c_int64(0)
+    _check(lib().stencil_exchange_layout(h, int(Tb), ctypes.byref(nb), ctypes.byref(rows)))
+    return nb.value, rows.value
+
+
 def stencil_launch_count():
     return int(lib().stencil_launch_count())
 
@@ -393,6 +400,10 @@ class Plan:
 
     def get_tuning(self):
         return stencil_get_tuning(self.handle)
+
+    def exchange_layout(self, Tb):
+        """(bands, rows computed) of the exchange kernel for Tb on this device."""
+        return stencil_exchange_layout(self.handle, Tb)
 
     def autotune(self, scratch_grid, probe_steps=4, stream=None):
         return stencil_autotune(self.handle, scratch_grid, probe_steps, stream)

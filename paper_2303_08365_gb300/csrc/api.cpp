@@ -1219,6 +1219,21 @@ int stencil_get_tuning(stencil_plan p, int* Tb, int* variant) {
   return STENCIL_OK;
 }
 
+int stencil_exchange_layout(stencil_plan p, int Tb, int* nbands, int64_t* rows_computed) {
+  g_err.clear();
+  if (!p || !nbands || !rows_computed) return fail(STENCIL_ERR_ARG, "NULL argument");
+  if (Tb != 2 && Tb != 4 && Tb != 8) return fail(STENCIL_ERR_ARG, "Tb must be 2, 4 or 8 (got %d)", Tb);
+  const int sms = sm_count();
+  if (p->varcoef || !exchange_fits(p->ndim, p->radius, p->g, sms))
+    return fail(STENCIL_ERR_UNSUPPORTED, "the exchange kernel does not take this plan");
+  const std::vector<ExchangeBand> bands = exchange_bands(p->g, p->boundary == kPeriodic, Tb, sms);
+  int64_t rows = 0;
+  for (const ExchangeBand& b : bands) rows += b.rows;
+  *nbands = (int)bands.size();
+  *rows_computed = rows;
+  return STENCIL_OK;
+}
+
 int stencil_autotune(stencil_plan p, double* d_grid, int64_t probe_steps, void* cuda_stream,
                      double* best_gstencils) {
   g_err.clear();

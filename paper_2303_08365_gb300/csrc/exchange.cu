@@ -11,8 +11,8 @@
 // hand each other their intermediate time levels through L2:
 //
 //   - one persistent CTA per tile of the (y, x) plane (64 columns by h rows,
-//     h near-equal over the tile rows), all CTAs co-resident (cooperative
-//     launch), each streaming its whole z column once;
+//     h near-equal over the tile rows, h <= 32), all CTAs co-resident
+//     (cooperative launch), each streaming its whole z column once;
 //   - stage s = 1 .. Tb holds time level t+s.  In iteration i stage s computes
 //     plane q_s(i) = i + qoff - 2(s-1) of its tile from planes q-1, q, q+1 of
 //     stage s-1 (the input grid for s = 1); stage s < Tb writes its plane to
@@ -44,6 +44,14 @@
 //     together, four FMA chains per lane), rotating rows over the warps from
 //     unit to unit, and store with 16-byte st.global.v2 (ring planes with an
 //     L2 evict-last policy, the output as streaming stores);
+//   - a plane taller than the co-resident tiles cover (at most 32 rows each)
+//     is cut into bands of rows, one launch each.  A band carries Tb - 1
+//     margin rows toward each neighbouring band: rows it computes but does
+//     not write to the output.  The ring holds the band's rows only, and a
+//     row beyond the band's edge reads as zero; stage s reads one row further
+//     out than stage s - 1 wrote (stage 1 reads the input, which has every
+//     row), so the zeros reach at most Tb - 1 rows into the last stage, all
+//     of them margin rows;
 //   - periodic z: each stage also computes Tb - s extra planes beyond each
 //     end of the z column (from wrapped input planes), so no stage needs a
 //     plane computed at the other end of the sweep: (Tb-1)/nz of the work

@@ -192,3 +192,42 @@ def test_fixed_tb_without_variant_keeps_its_tb(stencil):
         got_tb, got_v = stencil.stencil_get_tuning(h)
         assert got_tb == tb and got_v in want, (dims, tb, got_tb, got_v)
         stencil.stencil_destroy(h)
+
+
+def _bands_rows(ny, nx, periodic, Tb, sms):
+    """The band cut the exchange kernel documents: one band when 32-row
+    tiles over sms // (nx / 64) tile rows cover the plane, else near-equal
+    owned ranges with Tb - 1 margin rows on each side toward a neighbour."""
+    ty_max = sms // (nx // 64)
+    max_rows = ty_max * 32
+    if ny <= max_rows:
+        return 1, ny
+    H = Tb - 1
+    nb = -(-ny // (max_rows - 2 * H))
+    margins = H * (2 * nb if periodic else 2 * (nb - 1))
+    return nb, ny + margins
+
+
+def test_exchange_layout_reports_the_band_cut(stencil):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count if torch.cuda.is_available() else 1
+    heat3 = np.zeros(27)
+    heat3[[4, 10, 12, 13, 14, 16, 22]] = [.1, .1, .1, .4, .1, .1, .1]
+    for dims, bnd in [((4, 100, 64), 0), ((4, 100, 64), 1), ((3, 1024, 1024), 0), ((3, 1024, 1024), 1),
+                      ((2, 40, 64 * 152), 1), ((5, 7, 128), 1)]:
+        h = stencil.stencil_create(dims, 1, heat3, bnd)
+        for Tb in (2, 4, 8):
+            if dims[2] // 64 > sms:
+                with pytest.raises(stencil.StencilError) as ei:
+                    stencil.stencil_exchange_layout(h, Tb)
+                assert ei.value.code == stencil.ERR_UNSUPPORTED
+                continue
+            assert stencil.stencil_exchange_layout(h, Tb) == _bands_rows(dims[1], dims[2], bnd == 1, Tb, sms)
+        with pytest.raises(stencil.StencilError):
+            stencil.stencil_exchange_layout(h, 3)
+        stencil.stencil_destroy(h)
+    h2 = stencil.stencil_create((64, 64), 1, np.ones(9) / 9, 1)
+    with pytest.raises(stencil.StencilError) as ei:
+        stencil.stencil_exchange_layout(h2, 4)
+    assert ei.value.code == stencil.ERR_UNSUPPORTED
+    stencil.stencil_destroy(h2)

@@ -122,3 +122,12 @@ def test_instruction_count_lookup_prefers_the_tb_keyed_record(tmp_path, monkeypa
     assert r8["fp64_instr_source"] == "table (kernel changed since the ncu count)"
     rs = bench.roofline("heat3d-7pt", 64 ** 3, 1, 1.0, 1, 1.256, "stream3d")
     assert rs["fp64_instr_source"] == "table (no ncu count recorded)"
+
+
+def test_source_hash_ignores_comments_only():
+    """A comment edit keeps the recorded counters; a code edit does not."""
+    a = "int f(int x) {  // doubles x\n  return 2 * x; /* twice */\n}\n"
+    b = "// header\nint f(int x) {\n\n  return 2 * x;\n}\n"
+    c = "int f(int x) {\n  return 3 * x;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
