@@ -245,7 +245,9 @@ typedef enum {
                                      one co-resident CTA per 64-column tile,
                                      intermediate time levels handed between
                                      tiles through an L2-resident ring of
-                                     (Tb-1) x 5 grid planes (plan-owned).
+                                     (Tb-1) x K grid planes (plan-owned; K =
+                                     5 for a star, 6 for a box, 7 / 8 at
+                                     Tb = 2).
                                      Needs nx a multiple of 64 and at most
                                      one tile column per SM.  A plane taller
                                      than the co-resident tiles cover (32

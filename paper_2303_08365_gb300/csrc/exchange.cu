@@ -14,12 +14,13 @@
 //     h near-equal over the tile rows, h <= 32), all CTAs co-resident
 //     (cooperative launch), each streaming its whole z column once;
 //   - stage s = 1 .. Tb holds time level t+s.  In iteration i stage s computes
-//     plane q_s(i) = i + qoff - 2(s-1) of its tile from planes q-1, q, q+1 of
+//     plane q_s(i) = i + qoff - L(s-1) of its tile from planes q-1, q, q+1 of
 //     stage s-1 (the input grid for s = 1); stage s < Tb writes its plane to
 //     an L2-resident ring of K planes per stage (the whole grid plane, so
 //     neighbouring tiles can read their halo from it), stage Tb writes the
-//     output grid.  The stage skew of two planes means a stage only reads
-//     planes written in earlier iterations;
+//     output grid.  The stage skew of L >= 2 planes (2; 3 at Tb = 2) means a
+//     stage only reads planes written in earlier iterations: unit (i, s)
+//     needs unit (i-L+1, s-1);
 //   - a consumer thread fences its stores into the async proxy and bumps its
 //     warp's shared-memory count of stage s (release) once it has written its
 //     share of unit (i, s), s < Tb (the levels other tiles
@@ -33,9 +34,11 @@
 //     units need no poll; bounded by wall time) that the CTA itself and every
 //     neighbour whose cells the tile's halo touches have published i for
 //     stage s-1 (the TMA reads its own rows back through L2 too).  A level is
-//     published Tb units before it is needed (units (i-1, s+1 .. Tb) and
-//     (i, 1 .. s) lie in between; stage 1 reads the caller's grid, which is
-//     prefetched into L2 an iteration ahead), which covers the hand-over;
+//     published (L-1) Tb units before it is needed (L = 2: units
+//     (i-1, s+1 .. Tb) and (i, 1 .. s) lie in between; at Tb = 2 those would
+//     be two units only, hence L = 3 there; stage 1 reads the caller's grid,
+//     which is prefetched into L2 an iteration ahead), which covers the
+//     hand-over;
 //   - the producer warp fills a 4-slot shared-memory ring of "stage units"
 //     (three planes of tile + halo rows, each one TMA box of its exact height,
 //     with x-halo column pairs by 16-byte cp.async through L2) under mbarrier
@@ -58,12 +61,14 @@
 //     (1.4% at 512 planes, Tb = 8).  Dirichlet: planes outside the grid are
 //     zero at every level (TMA out-of-bounds fill), nothing extra is computed;
 //   - ring slot reuse: plane p of stage s, written in iteration j, is read in
-//     iterations j+1 .. j+3 (by other tiles up to j+2 for the star, whose
-//     plane q-1 is read at the tile's own cells only) and rewritten in j+K.
-//     Unit (i, s), s >= 2, is posted once every neighbour has finished
-//     (i-1, s-1), so all of iteration i-2; unit (i, 1) after the wait of the
-//     last such unit of iteration i-1, so all of iteration i-3: K = 5 planes
-//     (star) or 6 (box) keep every read ahead of the rewrite.
+//     iterations j+L-1 .. j+L+1 (by other tiles up to j+L for the star, whose
+//     plane q-1 is read at the tile's own cells only; the tile's own reads
+//     precede its own later writes) and rewritten in j+K.  Unit (i, s),
+//     s >= 2, is posted once every neighbour has finished (i-L+1, s-1), so all
+//     of iteration i-L; unit (i, 1) after the wait of the last such unit of
+//     iteration i-1, so all of iteration i-L-1: K = 2L+1 planes (star) or
+//     2L+2 (box) keep every read ahead of the rewrite (5 / 6 at L = 2, 7 / 8
+//     at L = 3).
 // Each cell applies its taps in the direct kernel's lexicographic order with
 // register-resident weights, so a Tb-fused sweep is bitwise equal to Tb
 // single steps.  Every wait is bounded (2 s of wall time): a CTA that gives up
@@ -92,9 +97,11 @@ constexpr int kThreadsX = (kWarps + 2) * 32;
 constexpr int kMaps = 5;           // TMA box heights: 1, h_lo, h_lo+1, h_lo+2, h_lo+3 rows
 constexpr int kMaxStages = 8;      // largest Tb; progress counters per CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;
-// ring planes per stage (see the slot-reuse rule above)
-template <bool BOX>
-constexpr int ring_k() { return BOX ? 6 : 5; }
+// Stage skew L in planes: 3 at Tb = 2 (a level is published 2 Tb units
+// before it is needed instead of Tb), else 2.
+inline int stage_lag(int Tb) { return Tb == 2 ? 3 : 2; }
+// Ring planes per stage for skew L (see the slot-reuse rule above).
+inline int ring_k(bool box, int lag) { return box ? 2 * lag + 2 : 2 * lag + 1; }
 
 // One stage unit: planes q-1, q, q+1 of the previous stage over the tile's
 // rows and the y-halo rows (row r <-> y0 - 1 + r), and the x-halo column
@@ -137,6 +144,7 @@ struct XParams {
   int tiles_x, h_lo, h_extra;  // tile row j: h_lo + (j < h_extra) rows
   int tiles_y;
   int Tb, iters, qoff;
+  int lag, K;  // stage skew in planes; ring planes per stage
   long long spin_limit;
 };
 
@@ -300,7 +308,7 @@ __device__ __forceinline__ void post_plane(const XParams& P, XSlot& sl, uint64_t
 
 template <int NT, bool BOX, bool PERIODIC>
 __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_constant__ XParams P) {
-  constexpr int K = ring_k<BOX>();
+  const int K = P.K;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   XSmem& S = *reinterpret_cast<XSmem*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
     for (int k = 0; k < kMaxStages; ++k) ready[k] = 0;
     for (int i = 0; i < P.iters && !failed; ++i) {
       for (int s = 1; s <= Tb; ++s) {
-        const int q = i + P.qoff - 2 * (s - 1);
+        const int q = i + P.qoff - P.lag * (s - 1);
         int lo, hi;
         stage_range(P, PERIODIC, s, lo, hi);
         if (q < lo || q > hi) continue;
@@ -473,7 +481,7 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
             }
           }
           if (late) break;
-          const int q = i + P.qoff - 2 * (s - 1);
+          const int q = i + P.qoff - P.lag * (s - 1);
           int lo, hi;
           stage_range(P, PERIODIC, s, lo, hi);
           if (q >= lo && q <= hi) {  // the unit wrote a plane
@@ -501,7 +509,7 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
   int rot = 0;
   for (int i = 0; i < P.iters; ++i) {
     for (int s = 1; s <= Tb; ++s) {
-      const int q = i + P.qoff - 2 * (s - 1);
+      const int q = i + P.qoff - P.lag * (s - 1);
       int lo, hi;
       stage_range(P, PERIODIC, s, lo, hi);
       if (q < lo || q > hi) {
@@ -618,7 +626,8 @@ cudaError_t launch_x(const ExchangeLaunch& L, cudaStream_t stream) {
     // the grid's rows for the input and the band's rows for the ring)
     const int rows = k == 0 ? 1 : h_lo + k - 1;
     if (!encode_in(&P.map_in[k], L.src, g, rows > g.ny ? 1 : rows) ||
-        !encode_ring(&P.map_ring[k], L.ring, g.nx, b.rows, ring_k<BOX>(), stages, rows > b.rows ? 1 : rows))
+        !encode_ring(&P.map_ring[k], L.ring, g.nx, b.rows, ring_k(BOX, stage_lag(L.Tb)), stages,
+                     rows > b.rows ? 1 : rows))
       return cudaErrorInvalidValue;
   }
   P.src = L.src;
@@ -640,8 +649,12 @@ cudaError_t launch_x(const ExchangeLaunch& L, cudaStream_t stream) {
   P.h_lo = h_lo;
   P.h_extra = b.rows % b.tiles_y;
   P.Tb = L.Tb;
+  P.lag = stage_lag(L.Tb);
+  P.K = ring_k(BOX, P.lag);
   P.qoff = PERIODIC ? -(L.Tb - 1) : 0;
-  P.iters = PERIODIC ? g.nz + 3 * L.Tb - 3 : g.nz + 2 * L.Tb - 2;
+  // the last stage reaches its last plane (nz - 1, periodic: plus none) in
+  // iteration nz - 1 - qoff + lag (Tb - 1)
+  P.iters = g.nz - P.qoff + P.lag * (L.Tb - 1);
   P.spin_limit = L.spin_limit;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(L.tiles_x * b.tiles_y), 1, 1);
@@ -691,7 +704,7 @@ std::vector<ExchangeBand> exchange_bands(const Geom& g, bool periodic, int Tb, i
 int exchange_counter_words(int tiles) { return tiles * kMaxStages; }
 
 size_t exchange_ring_cells(const Geom& g, int Tb, int band_rows) {
-  return (size_t)(Tb > 1 ? Tb - 1 : 1) * ring_k<true>() * (size_t)band_rows * (size_t)g.nx;
+  return (size_t)(Tb > 1 ? Tb - 1 : 1) * ring_k(true, stage_lag(Tb)) * (size_t)band_rows * (size_t)g.nx;
 }
 
 cudaError_t launch_exchange(Shape shape, int boundary, const ExchangeLaunch& L, cudaStream_t stream) {
