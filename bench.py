@@ -357,11 +357,16 @@ def headline(st, steps, warmup, world, stream):
     e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
     e2e_clocks = e2e_sampler.stop()
     e2e_ms = barrier_max(world, e2e_ms)
+    # the copies alone, for the record: the same pinned buffer to and from
+    # the device (CUDA events on the stream), GB/s each way
+    copy_ms = {"h2d": cuda_time(lambda: grid.copy_(host, non_blocking=True), stream),
+               "d2h": cuda_time(lambda: host.copy_(grid, non_blocking=True), stream)}
+    copy_gbs = {k: round(h2d / (v * 1e-3) / 1e9, 1) for k, v in copy_ms.items()}
     plan.close()
     del grid
     torch.cuda.empty_cache()
     return dict(ms=ms / steps, launches=launches, clocks=clocks, e2e_ms=e2e_ms, e2e_clocks=e2e_clocks,
-                h2d=h2d, d2h=h2d,
+                h2d=h2d, d2h=h2d, copy_gbs=copy_gbs,
                 Tb=tb, variant=st.stencil_variant_name(variant), u0=u0, checks=checks)
 
 
@@ -977,6 +982,7 @@ def main():
         "fp64_peak_tflops_measured": round(peak_tflops, 4),
         "e2e": {"value": round(e2e_value, 4), "unit": "GStencil/s",
                 "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"],
+                "copy_gbs_pinned": h["copy_gbs"],
                 "clocks": h["e2e_clocks"]},
         "gpu_launches": int(h["launches"]),
         "clocks": h["clocks"],

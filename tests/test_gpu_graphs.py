@@ -39,6 +39,7 @@ CASES = [
     ((37, 70), "box", DIRICHLET, 1, "direct", 5),
     ((24, 64, 128), "heat", PERIODIC, 4, "exchange", 9),
     ((16, 40, 64), "box", DIRICHLET, 8, "exchange", 17),
+    ((6, 150, 4864), "heat", PERIODIC, 4, "exchange", 9),   # 3 bands: 3 launches per block
 ]
 
 

@@ -395,6 +395,8 @@ EXCHANGE_CASES = [
     ((4, 40, 9728), PERIODIC, "box_rand", 8, 16),    # one tile row per band, margins of 7 rows
     ((9, 100, 9728), DIRICHLET, "heat", 4, 9),       # 4 bands
     ((12, 70, 4864), PERIODIC, "star_rand", 4, 12),  # 2 bands, each the other's neighbour twice
+    ((7, 130, 4864), PERIODIC, "box_rand", 4, 9),    # 3 bands, box halo across the margins
+    ((5, 300, 2432), DIRICHLET, "heat", 2, 6),       # 3 bands, one margin row each side
 ]
 
 
