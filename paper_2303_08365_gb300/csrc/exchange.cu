@@ -110,6 +110,26 @@ struct __align__(1024) XSlot {
   double plane[3][kRows][kXW];
   double2 halo[3][kRows][2];
 };
+// The copies of one unit that do not change from unit to unit, worked out
+// once per launch by the producer warp (it shares its issue slots with FP64
+// consumer warps, so per-unit integer work delays the copies).  A segment:
+// smem rows r .. r+n-1 from source rows y .. y+n-1, one box of map `map`
+// (its exact height), or n one-row boxes of map 0 when map == 0.
+struct XSeg {
+  int r, y, n, map;
+};
+// One x-halo pair: slot element dst (double2 index into halo), plane j, the
+// source row in the input grid (yin) and in the ring band (yring), column x;
+// flags bit 0 / 1: the pair exists in the input / the ring (Dirichlet edges,
+// band edges).
+struct XHalo {
+  int yin, yring, x;
+  short dst;
+  unsigned char j, flags;
+};
+constexpr int kSegMax = 4;           // a unit spans at most ny + 2 rows: three segments
+constexpr int kHaloMax = 2 * 3 * kRows;
+
 struct XSmem {
   XSlot slot[kSlots];
   uint64_t full[kSlots];
@@ -119,6 +139,10 @@ struct XSmem {
   // count one warp's unit (i+1, s) in place of another's (i, s)
   unsigned int done[kMaxStages][kWarps];
   int abort;
+  // producer tables: [source: 0 input, 1 ring][rows: 0 = 1 .. h, 1 = 0 .. h+1]
+  XSeg seg[2][2][kSegMax];
+  int nseg[2][2];
+  XHalo hal[kHaloMax];
 };
 
 struct XParams {
@@ -274,18 +298,16 @@ __device__ __forceinline__ bool wait_counters(const XParams& P, const int (&nb)[
   return verdict > 0;
 }
 
-// Posts the TMA boxes of plane j of a unit: smem rows ra .. rb hold source
-// rows ytop + ra .. ytop + rb (grid rows of the input, s == 1; band rows of
-// the ring).  With wrap > 0 those rows wrap modulo wrap (a periodic axis):
-// contiguous segments split at the wrap, at most three since a unit spans at
-// most wrap + 2 rows.  Each segment is one box of its exact height when the
-// maps have one (and it fits the source's `limit` rows), else row by row.
-// Rows outside a source that does not wrap read as zeros (TMA out-of-bounds
-// fill).  `z` is the plane's coordinate in the input grid (s == 1) or its
-// ring slot (-1: a plane of zeros) and `st` the ring stage.
-__device__ __forceinline__ void post_plane(const XParams& P, XSlot& sl, uint64_t* bar, int j, int ra, int rb,
-                                           int ytop, int wrap, int limit, int x0, int s, int z, int st,
-                                           uint64_t keep) {
+// The segments of smem rows ra .. rb, which hold source rows ytop + ra ..
+// ytop + rb (grid rows of the input; band rows of the ring).  With wrap > 0
+// those rows wrap modulo wrap (a periodic axis): contiguous segments split
+// at the wrap, at most three since a unit spans at most wrap + 2 rows.  Each
+// segment is one box of its exact height when the maps have one (and it
+// fits the source's `limit` rows), else row by row.  Rows outside a source
+// that does not wrap read as zeros (TMA out-of-bounds fill).  Returns the
+// count, or -1 if the segments do not fit the table.
+__device__ int build_segs(const XParams& P, int ra, int rb, int ytop, int wrap, int limit, XSeg* out) {
+  int ns = 0;
   for (int a = ra; a <= rb;) {
     int y = ytop + a;
     int n = rb - a + 1;
@@ -293,17 +315,13 @@ __device__ __forceinline__ void post_plane(const XParams& P, XSlot& sl, uint64_t
       y = wrapi(y, wrap);
       n = min(n, wrap - y);
     }
+    if (ns == kSegMax) return -1;
     const int k = n - P.h_lo + 1;  // the box of exactly n rows, if there is one
     const bool whole = n > 1 && k >= 1 && k < kMaps && n <= limit;
-    for (int e = 0; e < (whole ? 1 : n); ++e) {
-      const int which = whole ? k : 0;
-      if (s == 1)
-        tma_load_3d(&sl.plane[j][a + e][0], &P.map_in[which], x0, y + e, z, bar);
-      else  // ring lines stay in L2 until their slot is rewritten
-        tma_load_4d_hint(&sl.plane[j][a + e][0], &P.map_ring[which], x0, y + e, z, st, bar, keep);
-    }
+    out[ns++] = XSeg{a, y, n, whole ? k : 0};
     a += n;
   }
+  return ns;
 }
 
 template <int NT, bool BOX, bool PERIODIC>
@@ -354,8 +372,40 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
         nb[nnb++] = jy * P.tiles_x + jx;
       }
     }
+    // the unit-invariant part of every copy
+    if (lane < 4) {
+      const int src = lane >> 1, kind = lane & 1;
+      const int ra = kind ? 0 : 1, rb = kind ? h + 1 : h;
+      S.nseg[src][kind] = src == 0 ? build_segs(P, ra, rb, y0 - 1, PERIODIC ? P.ny : 0, P.ny, S.seg[0][kind])
+                                   : build_segs(P, ra, rb, yl0 - 1, P.ring_wrap ? P.nyb : 0, P.nyb, S.seg[1][kind]);
+    }
+    // x-halo pairs: box: every plane and row; star: plane q at the tile's rows
+    const int nh = 2 * (BOX ? 3 * (h + 2) : h);
+    for (int e = lane; e < nh; e += 32) {
+      const int side = e & 1;
+      const int k = e >> 1;
+      const int j = BOX ? k / (h + 2) : 1;
+      const int r = BOX ? k % (h + 2) : k + 1;
+      int x = side ? x0 + kXW : x0 - 2;
+      bool xv = true;
+      if (PERIODIC) x = wrapi(x, P.nx);
+      else xv = x >= 0 && x < P.nx;
+      int yin = y0 - 1 + r, yring = yl0 - 1 + r;
+      bool vin = xv, vring = xv;
+      if (PERIODIC) yin = wrapi(yin, P.ny);
+      else vin = vin && yin >= 0 && yin < P.ny;
+      if (P.ring_wrap) yring = wrapi(yring, P.nyb);
+      else vring = vring && yring >= 0 && yring < P.nyb;
+      S.hal[e] = XHalo{yin, yring, x, (short)((j * kRows + r) * 2 + side), (unsigned char)j,
+                       (unsigned char)((vin ? 1 : 0) | (vring ? 2 : 0))};
+    }
+    // the next input plane's rows for the L2 prefetch of stage-1 units
+    const int pf_y = PERIODIC ? wrapi(y0 - 1, P.ny) : y0 - 1;
+    const bool pf_whole = (pf_y + h + 2 <= P.ny || !PERIODIC) && h + 2 <= P.ny;
+    __syncwarp();
     uint32_t u = 0;
-    bool failed = false;
+    bool failed = __any_sync(0xffffffffu, lane < 4 && S.nseg[lane >> 1][lane & 1] < 0);
+    if (failed && lane == 0) atomicCAS(P.status, 0, -2 /* STENCIL_ERR_UNSUPPORTED */);
     const uint64_t keep = policy_evict_last();
     unsigned int ready[kMaxStages];  // lane 0: acquired minimum of the counters per stage
 #pragma unroll
@@ -393,60 +443,54 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
           const int qn = q + 2;
           if (PERIODIC || (qn >= 0 && qn < P.nz)) {
             const int zn = PERIODIC ? wrapi(qn, P.nz) : qn;
-            const int ya = PERIODIC ? wrapi(y0 - 1, P.ny) : y0 - 1;
-            if ((ya + h + 2 <= P.ny || !PERIODIC) && h + 2 <= P.ny) {
-              tma_prefetch_3d(&P.map_in[h - P.h_lo + 3], x0, ya, zn);  // h + 2 rows
+            if (pf_whole) {
+              tma_prefetch_3d(&P.map_in[h - P.h_lo + 3], x0, pf_y, zn);  // h + 2 rows
             } else {
               for (int r = 0; r < h + 2; ++r) tma_prefetch_3d(&P.map_in[0], x0, wrapi(y0 - 1 + r, P.ny), zn);
             }
           }
         }
+        // planes q-1, q, q+1 of the previous stage: z in the input (s == 1) or
+        // ring slot (-1: a plane of zeros outside a Dirichlet grid)
+        auto plane_z = [&](int j) {
+          const int qq = q - 1 + j;
+          const bool exists = PERIODIC || (qq >= 0 && qq < P.nz);
+          return s == 1 ? (PERIODIC ? wrapi(qq, P.nz) : qq) : (exists ? wrapi(qq, K) : -1);
+        };
+        const int z0 = plane_z(0), z1 = plane_z(1), z2 = plane_z(2);
+        // (selected, not indexed: a register array indexed by a lane-dependent
+        // value would live in local memory)
+        auto zsel = [&](int j) { return j == 0 ? z0 : j == 1 ? z1 : z2; };
         if (lane < 3) {
           const int j = lane;
-          const int qq = q - 1 + j;
-          int z;
-          if (s == 1) {
-            z = PERIODIC ? wrapi(qq, P.nz) : qq;
-          } else {
-            const bool exists = PERIODIC || (qq >= 0 && qq < P.nz);
-            z = exists ? wrapi(qq, K) : -1;
+          const int src = s == 1 ? 0 : 1, kind = (BOX || j == 1) ? 1 : 0;
+          const int nsg = S.nseg[src][kind];
+          for (int g = 0; g < nsg; ++g) {
+            const XSeg sg = S.seg[src][kind][g];
+            for (int e = 0; e < (sg.map ? 1 : sg.n); ++e) {
+              if (s == 1)
+                tma_load_3d(&sl.plane[j][sg.r + e][0], &P.map_in[sg.map], x0, sg.y + e, zsel(j), &S.full[slot]);
+              else  // ring lines stay in L2 until their slot is rewritten
+                tma_load_4d_hint(&sl.plane[j][sg.r + e][0], &P.map_ring[sg.map], x0, sg.y + e, zsel(j), s - 2,
+                                 &S.full[slot], keep);
+            }
           }
-          const int ra = (BOX || j == 1) ? 0 : 1, rb = (BOX || j == 1) ? h + 1 : h;
-          if (s == 1)
-            post_plane(P, sl, &S.full[slot], j, ra, rb, y0 - 1, PERIODIC ? P.ny : 0, P.ny, x0, s, z, 0, keep);
-          else
-            post_plane(P, sl, &S.full[slot], j, ra, rb, yl0 - 1, P.ring_wrap ? P.nyb : 0, P.nyb, x0, s, z, s - 2,
-                       keep);
         }
-        // x-halo pairs: box: every plane and row; star: plane q at the tile's rows
-        const int hrows = BOX ? 3 * (h + 2) : h;
-        for (int e = lane; e < 2 * hrows; e += 32) {
-          const int side = e & 1;
-          const int k = e >> 1;
-          const int j = BOX ? k / (h + 2) : 1;
-          const int r = BOX ? k % (h + 2) : k + 1;
-          const int qq = q - 1 + j;
-          int x = side ? x0 + kXW : x0 - 2;
-          bool valid = true;
-          if (PERIODIC) x = wrapi(x, P.nx);
-          else valid = x >= 0 && x < P.nx && qq >= 0 && qq < P.nz;
-          const double* g = P.src;
+        double2* const hbase = &sl.halo[0][0][0];
+        for (int e = lane; e < nh; e += 32) {
+          const XHalo t = S.hal[e];
+          const int qq = q - 1 + t.j;
+          const bool zv = PERIODIC || (qq >= 0 && qq < P.nz);
           if (s == 1) {
-            int y = y0 - 1 + r;
-            if (PERIODIC) y = wrapi(y, P.ny);
-            else valid = valid && y >= 0 && y < P.ny;
-            const int zc = PERIODIC ? wrapi(qq, P.nz) : qq;
-            if (valid) g = P.src + ((int64_t)zc * P.ny + y) * P.nx + x;
+            const bool valid = (t.flags & 1) && zv;
+            const double* g = valid ? P.src + ((int64_t)zsel(t.j) * P.ny + t.yin) * P.nx + t.x : P.src;
+            cp_async16_cg(hbase + t.dst, g, valid);
           } else {
-            int y = yl0 - 1 + r;
-            if (P.ring_wrap) y = wrapi(y, P.nyb);
-            else valid = valid && y >= 0 && y < P.nyb;
-            if (valid) g = P.ring + (((int64_t)(s - 2) * K + wrapi(qq, K)) * P.nyb + y) * P.nx + x;
+            const bool valid = (t.flags & 2) && zv;
+            const double* g =
+                valid ? P.ring + (((int64_t)(s - 2) * K + zsel(t.j)) * P.nyb + t.yring) * P.nx + t.x : P.src;
+            cp_async16_cg_hint(hbase + t.dst, g, valid, keep);
           }
-          if (s == 1)
-            cp_async16_cg(&sl.halo[j][r][side], g, valid);
-          else
-            cp_async16_cg_hint(&sl.halo[j][r][side], g, valid, keep);
         }
         cp_async_arrive_noinc(&S.full[slot]);
         ++u;
