@@ -144,6 +144,7 @@ struct XSmem {
   int nseg[2][2];
   XHalo hal[kHaloMax];
 };
+static_assert(sizeof(XSmem) <= 227 * 1024, "the unit ring and tables exceed the shared memory of one CTA");
 
 struct XParams {
   // boxes of 64 columns by 1, h_lo, h_lo+1, h_lo+2 and h_lo+3 rows: every
