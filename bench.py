@@ -65,6 +65,7 @@ class ClockSampler:
         self.uuid = uuid
         self.proc = None
         self.lines = []
+        self.first = threading.Event()
 
     def start(self):
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -79,10 +80,15 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # nvidia-smi's start-up holds the driver for a while (launches and
+        # copies from this process wait): time nothing until its first sample
+        self.first.wait(timeout=10.0)
 
     def _read(self):
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
+            self.first.set()
+        self.first.set()
 
     def stop(self):
         if self.proc is None:
