@@ -328,7 +328,7 @@ def headline(st, steps, warmup, world, stream):
     barrier(world)
     uuid = None
     try:
-        uuid = str(torch.cuda.get_device_properties(0).uuid)
+        uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         uuid = None
