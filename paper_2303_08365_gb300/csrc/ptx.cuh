@@ -89,16 +89,8 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// The same with an L2 cache policy for the lines read (see policy_evict_last).
+// A 4D box {c0, c1, c2, c3} with an L2 cache policy for the lines read (see
+// policy_evict_last).
 __device__ __forceinline__ void tma_load_4d_hint(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
                                                  int c3, uint64_t* bar, uint64_t policy) {
   asm volatile(
@@ -135,14 +127,6 @@ __device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Relaxed load of a 32-bit word at GPU scope (a poll that may see a
-// value written by another CTA; follow it with fence_acq_rel_gpu).
-__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // Relaxed 16-byte load of four 32-bit words at GPU scope (address 16-byte aligned).
 __device__ __forceinline__ uint4 ld_relaxed_gpu_v4(const unsigned int* p) {
   uint4 v;
@@ -167,13 +151,6 @@ __device__ __forceinline__ void red_release_cta_shared_add(unsigned int* p, unsi
 __device__ __forceinline__ unsigned int ld_acquire_cta_shared(const unsigned int* p) {
   unsigned int v;
   asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
-  return v;
-}
-
-// Acquire load of a 32-bit word at GPU scope.
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
