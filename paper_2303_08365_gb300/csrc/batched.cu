@@ -278,23 +278,36 @@ __global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) 
       const int y0 = cut(ty, ny, L.tiles_y), x0 = cut(tx, nx, L.tiles_x);
       const int th = cut(ty + 1, ny, L.tiles_y) - y0, tw = cut(tx + 1, nx, L.tiles_x) - x0;
       if (blk > 0 && !wait_reach<PERIODIC>(L, ty, tx, (unsigned int)blk)) return;
-      // load the tile with a halo of tb cells (region offset TB - tb inside the buffer)
+      // load the tile with a halo of tb cells (region offset TB - tb inside the
+      // buffer): every load of this thread first, then the shared-memory
+      // stores, so the loads' L2 round trips overlap
       const int off = TB - tb;
       const int lh = th + 2 * tb, lw = tw + 2 * tb;
+      constexpr int KL = (RH * RW + kPThreads - 1) / kPThreads;
+      double lv[KL];
+      int li[KL];
       FlatWalk lwk(threadIdx.x, kPThreads, lw);
-      for (int c = threadIdx.x; c < lh * lw; c += kPThreads, lwk.next()) {
-        const int ry = lwk.r, rx = lwk.c;
-        int y = y0 - tb + ry, x = x0 - tb + rx;
-        double v = 0.0;
-        if (PERIODIC) {
-          y = wrap_into(y, ny);
-          x = wrap_into(x, nx);
-          v = __ldcg(src + (int64_t)y * nx + x);
-        } else if ((unsigned)y < (unsigned)ny && (unsigned)x < (unsigned)nx) {
-          v = __ldcg(src + (int64_t)y * nx + x);
+#pragma unroll
+      for (int k = 0; k < KL; ++k, lwk.next()) {
+        const int c = threadIdx.x + k * kPThreads;
+        lv[k] = 0.0;
+        li[k] = -1;
+        if (c < lh * lw) {
+          const int ry = lwk.r, rx = lwk.c;
+          int y = y0 - tb + ry, x = x0 - tb + rx;
+          if (PERIODIC) {
+            y = wrap_into(y, ny);
+            x = wrap_into(x, nx);
+            lv[k] = __ldcg(src + (int64_t)y * nx + x);
+          } else if ((unsigned)y < (unsigned)ny && (unsigned)x < (unsigned)nx) {
+            lv[k] = __ldcg(src + (int64_t)y * nx + x);
+          }
+          li[k] = (off + ry) * RW + off + rx;
         }
-        buf[0][(off + ry) * RW + off + rx] = v;
       }
+#pragma unroll
+      for (int k = 0; k < KL; ++k)
+        if (li[k] >= 0) buf[0][li[k]] = lv[k];
       __syncthreads();
       int cur = 0;
       for (int s = 1; s <= tb; ++s) {
