@@ -269,14 +269,21 @@ __global__ void __launch_bounds__(kPThreads, 2) k_persist_tb(PersistTbLaunch L) 
   const int ny = L.ny, nx = L.nx;
   const int ntiles = L.tiles_y * L.tiles_x;
   const long long nblk = (L.T + TB - 1) / TB;
+  // the geometry of this CTA's first tile, worked out once: most CTAs own one
+  // tile, and its divisions sit on the path between two blocks
+  const int fty = blockIdx.x / L.tiles_x, ftx = blockIdx.x % L.tiles_x;
+  const int fy0 = cut(fty, ny, L.tiles_y), fx0 = cut(ftx, nx, L.tiles_x);
+  const int fth = cut(fty + 1, ny, L.tiles_y) - fy0, ftw = cut(ftx + 1, nx, L.tiles_x) - fx0;
   for (long long blk = 0; blk < nblk; ++blk) {
     const int tb = (int)(L.T - blk * TB < TB ? L.T - blk * TB : TB);
     const double* src = (blk & 1) ? L.b : L.a;
     double* dst = (blk & 1) ? L.a : L.b;
     for (int j = blockIdx.x; j < ntiles; j += G) {
-      const int ty = j / L.tiles_x, tx = j % L.tiles_x;
-      const int y0 = cut(ty, ny, L.tiles_y), x0 = cut(tx, nx, L.tiles_x);
-      const int th = cut(ty + 1, ny, L.tiles_y) - y0, tw = cut(tx + 1, nx, L.tiles_x) - x0;
+      const bool first = j == (int)blockIdx.x;
+      const int ty = first ? fty : j / L.tiles_x, tx = first ? ftx : j % L.tiles_x;
+      const int y0 = first ? fy0 : cut(ty, ny, L.tiles_y), x0 = first ? fx0 : cut(tx, nx, L.tiles_x);
+      const int th = first ? fth : cut(ty + 1, ny, L.tiles_y) - y0;
+      const int tw = first ? ftw : cut(tx + 1, nx, L.tiles_x) - x0;
       if (blk > 0 && !wait_reach<PERIODIC>(L, ty, tx, (unsigned int)blk)) return;
       // load the tile with a halo of tb cells (region offset TB - tb inside the
       // buffer): every load of this thread first, then the shared-memory
