@@ -246,7 +246,7 @@ typedef enum {
                                      intermediate time levels handed between
                                      tiles through an L2-resident ring of
                                      (Tb-1) x K grid planes (plan-owned; K =
-                                     5 for a star, 6 for a box, 7 / 8 at
+                                     5 for a star, 6 for a box, 9 / 10 at
                                      Tb = 2).
                                      Needs nx a multiple of 64 and at most
                                      one tile column per SM.  A plane taller

@@ -18,7 +18,7 @@
 //     stage s-1 (the input grid for s = 1); stage s < Tb writes its plane to
 //     an L2-resident ring of K planes per stage (the whole grid plane, so
 //     neighbouring tiles can read their halo from it), stage Tb writes the
-//     output grid.  The stage skew of L >= 2 planes (2; 3 at Tb = 2) means a
+//     output grid.  The stage skew of L >= 2 planes (2; 4 at Tb = 2) means a
 //     stage only reads planes written in earlier iterations: unit (i, s)
 //     needs unit (i-L+1, s-1);
 //   - a consumer thread fences its stores into the async proxy and bumps its
@@ -32,11 +32,11 @@
 //     producer makes sure (one lane: relaxed loads of every stage's counters
 //     at once, then an acquire fence; the minimum per stage is kept, so most
 //     units need no poll; bounded by wall time) that the CTA itself and every
-//     neighbour whose cells the tile's halo touches have published i for
+//     neighbour whose cells the tile's halo touches have published i-L+2 for
 //     stage s-1 (the TMA reads its own rows back through L2 too).  A level is
 //     published (L-1) Tb units before it is needed (L = 2: units
 //     (i-1, s+1 .. Tb) and (i, 1 .. s) lie in between; at Tb = 2 those would
-//     be two units only, hence L = 3 there; stage 1 reads the caller's grid,
+//     be two units only, hence L = 4 there; stage 1 reads the caller's grid,
 //     which is prefetched into L2 an iteration ahead), which covers the
 //     hand-over;
 //   - the producer warp fills a 4-slot shared-memory ring of "stage units"
@@ -67,8 +67,8 @@
 //     s >= 2, is posted once every neighbour has finished (i-L+1, s-1), so all
 //     of iteration i-L; unit (i, 1) after the wait of the last such unit of
 //     iteration i-1, so all of iteration i-L-1: K = 2L+1 planes (star) or
-//     2L+2 (box) keep every read ahead of the rewrite (5 / 6 at L = 2, 7 / 8
-//     at L = 3).
+//     2L+2 (box) keep every read ahead of the rewrite (5 / 6 at L = 2, 9 / 10
+//     at L = 4).
 // Each cell applies its taps in the direct kernel's lexicographic order with
 // register-resident weights, so a Tb-fused sweep is bitwise equal to Tb
 // single steps.  Every wait is bounded (2 s of wall time): a CTA that gives up
@@ -97,9 +97,10 @@ constexpr int kThreadsX = (kWarps + 2) * 32;
 constexpr int kMaps = 5;           // TMA box heights: 1, h_lo, h_lo+1, h_lo+2, h_lo+3 rows
 constexpr int kMaxStages = 8;      // largest Tb; progress counters per CTA
 constexpr unsigned long long kWaitNs = 2000000000ull;
-// Stage skew L in planes: 3 at Tb = 2 (a level is published 2 Tb units
-// before it is needed instead of Tb), else 2.
-inline int stage_lag(int Tb) { return Tb == 2 ? 3 : 2; }
+// Stage skew L in planes: 4 at Tb = 2 (a level is published 3 Tb units
+// before it is needed instead of Tb), else 2 (a skew of 3 measured the same
+// at Tb = 4 and 8, with a larger ring).
+inline int stage_lag(int Tb) { return Tb == 2 ? 4 : 2; }
 // Ring planes per stage for skew L (see the slot-reuse rule above).
 inline int ring_k(bool box, int lag) { return box ? 2 * lag + 2 : 2 * lag + 1; }
 
@@ -418,8 +419,10 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
         stage_range(P, PERIODIC, s, lo, hi);
         if (q < lo || q > hi) continue;
         if (s >= 2) {
-          // stage s-1 of iteration i-1 is written here and at every neighbour
-          if (!wait_counters(P, nb, nnb, s - 1, (unsigned int)i, ready)) {
+          // plane q+1 of stage s-1 (iteration i-L+1) is written here and at
+          // every neighbour: its counter has reached i-L+2
+          const int need = i - P.lag + 2;
+          if (need > 0 && !wait_counters(P, nb, nnb, s - 1, (unsigned int)need, ready)) {
             failed = true;
             break;
           }

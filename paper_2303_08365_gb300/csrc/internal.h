@@ -109,7 +109,7 @@ cudaError_t launch_temporal(int ndim, int radius, Shape shape, int boundary, int
 // Temporal blocking without recomputation (3D radius 1, star or box, Tb >= 2):
 // one co-resident CTA per 64-column tile of a band of rows of the (y, x)
 // plane, intermediate time levels handed between tiles through a ring of
-// Tb-1 x K band planes (K = 5 / 6 for the star / box; 7 / 8 at Tb = 2).  A
+// Tb-1 x K band planes (K = 5 / 6 for the star / box; 9 / 10 at Tb = 2).  A
 // plane taller than the co-resident tiles cover (32 rows each) is cut into
 // bands, one launch each, every band with a margin of Tb-1 rows toward each
 // neighbouring band: the rows its last stage may get wrong at an edge whose
