@@ -448,10 +448,12 @@ def test_exchange_bands_at_the_1024_plane(st, boundary):
         T = 2 * Tb + 1
         p.set_tuning(Tb, st.VARIANT_EXCHANGE)
         g.copy_(torch.from_numpy(u0))
+        nbands, rows = p.exchange_layout(Tb)
+        assert nbands == 4 and rows > 1024                   # four bands, margins computed twice
         l0 = st.stencil_launch_count()
         p.run(g, T)
         assert p.status() == 0
-        assert st.stencil_launch_count() - l0 >= 2 * 4      # four bands per block
+        assert st.stencil_launch_count() - l0 == 2 * nbands + 1  # two blocks of four bands, one single step
         ref.copy_(torch.from_numpy(u0))
         q.run(ref, T)
         assert torch.equal(g, ref), Tb
