@@ -428,6 +428,33 @@ def test_exchange_kernel_rejects_shapes_it_cannot_take(st):
         p.close()
 
 
+def _random_exchange_cases(n, seed):
+    """Seeded shapes for the exchange kernel: nx a multiple of 64 up to 76
+    tile columns (so planes of a few hundred rows are cut into bands), any
+    ny and nz, either boundary, star or box weights, every Tb."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        nx = 64 * int(rng.choice([1, 3, 8, 19, 38, 76]))
+        ny = int(rng.integers(1, 420))
+        nz = int(rng.integers(1, 14))
+        Tb = int(rng.choice([2, 4, 8]))
+        T = int(rng.integers(Tb, 3 * Tb + 2))
+        out.append(((nz, ny, nx), int(rng.integers(0, 2)), str(rng.choice(["star_rand", "box_rand"])), Tb, T))
+    return out
+
+
+@pytest.mark.parametrize("shape,boundary,kind,Tb,T", _random_exchange_cases(20, 2303))
+def test_exchange_kernel_random_shapes_bitwise(st, shape, boundary, kind, Tb, T):
+    """Random shapes (bands included where the plane is taller than the
+    co-resident tiles cover): bitwise equal to single direct steps."""
+    w = weights_for(kind, 3, 1, 800 + Tb)
+    u0 = synth.normal(29, shape)
+    a = gpu_run(st, u0, w, 1, boundary, T, Tb=Tb, variant=st.VARIANT_EXCHANGE)
+    b = gpu_run(st, u0, w, 1, boundary, T, Tb=1, variant=st.VARIANT_DIRECT)
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("boundary", [PERIODIC, DIRICHLET])
 def test_exchange_bands_at_the_1024_plane(st, boundary):
