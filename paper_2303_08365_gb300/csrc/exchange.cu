@@ -16,8 +16,9 @@
 //   - stage s = 1 .. Tb holds time level t+s.  In iteration i stage s computes
 //     plane q_s(i) = i + qoff - L(s-1) of its tile from planes q-1, q, q+1 of
 //     stage s-1 (the input grid for s = 1); stage s < Tb writes its plane to
-//     an L2-resident ring of K planes per stage (the whole grid plane, so
-//     neighbouring tiles can read their halo from it), stage Tb writes the
+//     an L2-resident ring of K planes per stage (the whole plane of the band
+//     of rows the launch covers, so neighbouring tiles can read their halo
+//     from it), stage Tb writes the
 //     output grid.  The stage skew of L >= 2 planes (2; 4 at Tb = 2) means a
 //     stage only reads planes written in earlier iterations: unit (i, s)
 //     needs unit (i-L+1, s-1);
