@@ -248,8 +248,9 @@ typedef enum {
                                      (Tb-1) x K grid planes (plan-owned; K =
                                      5 for a star, 6 for a box, 9 / 10 at
                                      Tb = 2).
-                                     Needs nx a multiple of 64 and at most
-                                     one tile column per SM.  A plane taller
+                                     Needs nx even (a multiple of 64 on a
+                                     periodic grid) and at most one 64-column
+                                     tile column per SM.  A plane taller
                                      than the co-resident tiles cover (32
                                      rows each) runs as bands of rows, one
                                      launch each, every band with a margin of
@@ -260,14 +261,14 @@ typedef enum {
 /* Fixes the fused step count Tb (1, 2, 4 or 8) and kernel variant (a
  * stencil_variant; 0 = let the library choose) for later runs of p.
  * Tb = 0 returns the plan to the tuned / default choice.  With variant 0 the
- * library keeps the Tb: for Tb > 1 the exchange kernel (3D radius 1, nx a
- * multiple of 64 and at most 64 columns per SM), the persistent temporal
- * kernel (2D radius 1 up to 2^18 cells) or the overlapped temporal kernel;
- * for Tb = 1 a one-step kernel.  A run reports STENCIL_ERR_UNSUPPORTED when the plan has no fused
- * kernel for the Tb (2D and 3D radius 2), and when a variant named here
- * cannot take the grid (the kernels' limits are listed with
- * stencil_variant): neither a named variant nor a fixed Tb is dropped
- * silently. */
+ * library keeps the Tb: for Tb > 1 the exchange kernel (3D radius 1, nx
+ * even -- a multiple of 64 when periodic -- and at most 64 columns per SM),
+ * the persistent temporal kernel (2D radius 1 up to 2^18 cells) or the
+ * overlapped temporal kernel; for Tb = 1 a one-step kernel.  A run reports
+ * STENCIL_ERR_UNSUPPORTED when the plan has no fused kernel for the Tb (2D
+ * and 3D radius 2), and when a variant named here cannot take the grid (the
+ * kernels' limits are listed with stencil_variant): neither a named variant
+ * nor a fixed Tb is dropped silently. */
 int stencil_set_tuning(stencil_plan p, int Tb, int variant);
 
 /* Reports the Tb and variant the next stencil_run of p will use. */

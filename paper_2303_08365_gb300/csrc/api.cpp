@@ -365,7 +365,8 @@ int default_variant(const stencil_plan_s* p, int* Tb = nullptr) {
 // radius 1; other plans have no fused kernel and the run reports that).
 int fused_variant(const stencil_plan_s* p) {
   if (p->ndim == 3 && p->radius == 1)
-    return exchange_fits(p->ndim, p->radius, p->g, sm_count()) ? kVariantExchange : kVariantTemporal;
+    return exchange_fits(p->ndim, p->radius, p->g, p->boundary == kPeriodic, sm_count()) ? kVariantExchange
+                                                                                            : kVariantTemporal;
   if (p->ndim == 2 && p->radius == 1 && p->cells() <= ((int64_t)1 << 18) && (p->taps.n == 5 || p->taps.n == 9))
     return kVariantPersistent;
   return kVariantTemporal;
@@ -550,11 +551,11 @@ int ensure_exchange(stencil_plan_s* p, int Tb, int band_rows, int ntiles) {
 // cover), each after clearing the progress counters.
 int launch_exchange_block(stencil_plan_s* p, const double* a, double* b, int Tb, cudaStream_t s) {
   const int sms = sm_count();
-  if (!exchange_fits(p->ndim, p->radius, p->g, sms))
+  if (!exchange_fits(p->ndim, p->radius, p->g, p->boundary == kPeriodic, sms))
     return fail(STENCIL_ERR_UNSUPPORTED, "the grid does not fit the exchange kernel's tiling");
   const std::vector<ExchangeBand> bands = exchange_bands(p->g, p->boundary == kPeriodic, Tb, sms);
   ExchangeLaunch L;
-  L.tiles_x = (int)(p->g.nx / 64);
+  L.tiles_x = exchange_tiles_x(p->g);
   int max_rows = 0, max_ty = 0;
   for (const ExchangeBand& band : bands) {
     max_rows = std::max(max_rows, band.rows);
@@ -683,13 +684,14 @@ int run_const(stencil_plan_s* p, double* d_grid, int64_t T, cudaStream_t s) {
     variant = default_variant(p) == kVariantStream && stream_ok ? kVariantStream : kVariantDirect;
   }
   if (variant == kVariantExchange) {
-    const bool ok = Tb >= 2 && Tb <= 8 && exchange_fits(p->ndim, p->radius, p->g, sm_count()) &&
+    const bool ok = Tb >= 2 && Tb <= 8 && exchange_fits(p->ndim, p->radius, p->g, p->boundary == kPeriodic, sm_count()) &&
                     ((uintptr_t)d_grid & 15) == 0 && ((uintptr_t)p->d_tmp & 15) == 0;
     if (!ok) {
       if (v_user)
         return fail(STENCIL_ERR_UNSUPPORTED,
-                    "the exchange kernel covers 3D radius-1 plans with Tb in {2, 4, 8}, nx a multiple of "
-                    "64 and at most %d tile columns of 64, on 16-byte aligned buffers", sm_count());
+                    "the exchange kernel covers 3D radius-1 plans with Tb in {2, 4, 8}, nx even (a "
+                    "multiple of 64 on a periodic grid) and at most %d tile columns of 64, on 16-byte "
+                    "aligned buffers", sm_count());
       // a Tb fixed without a variant keeps its Tb on the overlapped kernel;
       // a tuned choice falls back to one step per launch
       if (tb_user && temporal_supported(p->ndim, p->radius, Tb))
@@ -1224,7 +1226,7 @@ int stencil_exchange_layout(stencil_plan p, int Tb, int* nbands, int64_t* rows_c
   if (!p || !nbands || !rows_computed) return fail(STENCIL_ERR_ARG, "NULL argument");
   if (Tb != 2 && Tb != 4 && Tb != 8) return fail(STENCIL_ERR_ARG, "Tb must be 2, 4 or 8 (got %d)", Tb);
   const int sms = sm_count();
-  if (p->varcoef || !exchange_fits(p->ndim, p->radius, p->g, sms))
+  if (p->varcoef || !exchange_fits(p->ndim, p->radius, p->g, p->boundary == kPeriodic, sms))
     return fail(STENCIL_ERR_UNSUPPORTED, "the exchange kernel does not take this plan");
   const std::vector<ExchangeBand> bands = exchange_bands(p->g, p->boundary == kPeriodic, Tb, sms);
   int64_t rows = 0;

@@ -554,6 +554,9 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
   // the ring is re-read within a few iterations: keep its lines in L2; the
   // output is not re-read: streaming stores
   const uint64_t keep = policy_evict_last();
+  // this lane's cell pair lies in the grid (a ragged last tile column computes
+  // its lanes beyond nx from zeros and stores nothing there)
+  const bool xin = x0 + 2 * lane < P.nx;
   uint32_t u = 0;
   int rot = 0;
   for (int i = 0; i < P.iters; ++i) {
@@ -588,19 +591,25 @@ __global__ void __launch_bounds__(kThreadsX, 1) k_exchange3d(const __grid_consta
         const int rr[2] = {r0, r0 + kWarps};
         double a[2][2];
         unit_rows<NT, BOX, 2>(sl, W, rr, lane, a);
+        if (xin) {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int64_t off = base + (int64_t)rr[k] * P.nx;
-          if (!last) st_global_v2_hint(P.ring + off, a[k][0], a[k][1], keep);
-          else if (y0 + rr[k] >= P.own_lo && y0 + rr[k] < P.own_hi) st_global_v2_cs(P.dst + off, a[k][0], a[k][1]);
+          for (int k = 0; k < 2; ++k) {
+            const int64_t off = base + (int64_t)rr[k] * P.nx;
+            if (!last) st_global_v2_hint(P.ring + off, a[k][0], a[k][1], keep);
+            else if (y0 + rr[k] >= P.own_lo && y0 + rr[k] < P.own_hi) st_global_v2_cs(P.dst + off, a[k][0], a[k][1]);
+          }
         }
       } else if (r0 < h) {
         const int rr[1] = {r0};
         double a[1][2];
         unit_rows<NT, BOX, 1>(sl, W, rr, lane, a);
         const int64_t off = base + (int64_t)r0 * P.nx;
-        if (!last) st_global_v2_hint(P.ring + off, a[0][0], a[0][1], keep);
-        else if (y0 + r0 >= P.own_lo && y0 + r0 < P.own_hi) st_global_v2_cs(P.dst + off, a[0][0], a[0][1]);
+        if (!xin) {
+        } else if (!last) {
+          st_global_v2_hint(P.ring + off, a[0][0], a[0][1], keep);
+        } else if (y0 + r0 >= P.own_lo && y0 + r0 < P.own_hi) {
+          st_global_v2_cs(P.dst + off, a[0][0], a[0][1]);
+        }
       }
       // this thread's share of unit (i, s) is written (stage Tb: the output).
       // Its stores are generic-proxy writes that TMA (the async proxy) reads
@@ -722,13 +731,19 @@ cudaError_t launch_x(const ExchangeLaunch& L, cudaStream_t stream) {
 
 }  // namespace
 
-bool exchange_fits(int ndim, int radius, const Geom& g, int sms) {
-  return ndim == 3 && radius == 1 && g.nx % kXW == 0 && g.nx / kXW <= sms && g.ny >= 1 && g.nz >= 1;
+int exchange_tiles_x(const Geom& g) { return (int)((g.nx + kXW - 1) / kXW); }
+
+bool exchange_fits(int ndim, int radius, const Geom& g, bool periodic, int sms) {
+  // a ragged last tile column reads zeros beyond nx (TMA out-of-bounds fill),
+  // which is the Dirichlet ghost but not the periodic wrap; rows must start
+  // on 16 bytes (nx even) for the paired stores
+  return ndim == 3 && radius == 1 && g.nx % 2 == 0 && (!periodic || g.nx % kXW == 0) &&
+         exchange_tiles_x(g) <= sms && g.ny >= 1 && g.nz >= 1;
 }
 
 std::vector<ExchangeBand> exchange_bands(const Geom& g, bool periodic, int Tb, int sms) {
   std::vector<ExchangeBand> out;
-  const int tx = g.nx / kXW;
+  const int tx = exchange_tiles_x(g);
   const int ty_max = sms / tx;                 // tile rows that are co-resident with every column
   const int max_rows = ty_max * kHMax;
   if (g.ny <= max_rows) {

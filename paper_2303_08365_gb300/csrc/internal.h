@@ -130,13 +130,14 @@ struct ExchangeLaunch {
   int* status;
   const double* wdev;
   int Tb;
-  int tiles_x;             // nx / 64
+  int tiles_x;             // exchange_tiles_x(g): ceil(nx / 64)
   ExchangeBand band;
   long long spin_limit;    // ns
 };
-// True when the kernel takes the shape: 3D radius 1, nx a multiple of 64, at
-// most `sms` tile columns.
-bool exchange_fits(int ndim, int radius, const Geom& g, int sms);
+// True when the kernel takes the shape: 3D radius 1, nx even (a multiple of
+// 64 on a periodic grid), at most `sms` tile columns of 64.
+bool exchange_fits(int ndim, int radius, const Geom& g, bool periodic, int sms);
+int exchange_tiles_x(const Geom& g);
 // The bands of a shape that fits, for `sms` co-resident CTAs and Tb steps.
 std::vector<ExchangeBand> exchange_bands(const Geom& g, bool periodic, int Tb, int sms);
 size_t exchange_ring_cells(const Geom& g, int Tb, int band_rows);

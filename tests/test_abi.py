@@ -179,7 +179,8 @@ def test_fixed_tb_without_variant_keeps_its_tb(stencil):
     heat3 = np.zeros(27)
     heat3[[4, 10, 12, 13, 14, 16, 22]] = [.1, .1, .1, .4, .1, .1, .1]
     cases = [((24, 64, 128), heat3, 1, 4, (stencil.VARIANT_TEMPORAL, stencil.VARIANT_EXCHANGE)),
-             ((10, 20, 70), heat3, 0, 2, (stencil.VARIANT_TEMPORAL,)),       # nx off the 64-column tiles
+             ((10, 20, 70), heat3, 0, 2, (stencil.VARIANT_TEMPORAL, stencil.VARIANT_EXCHANGE)),  # ragged nx
+             ((10, 20, 70), heat3, 1, 2, (stencil.VARIANT_TEMPORAL,)),       # periodic, nx off the tiles
              ((96, 96), heat2, 0, 8, (stencil.VARIANT_PERSISTENT,)),        # small 2D grid
              ((1024, 1024), heat2, 0, 4, (stencil.VARIANT_TEMPORAL,)),
              ((5000,), np.array([.25, .5, .25]), 0, 2, (stencil.VARIANT_TEMPORAL,)),
@@ -198,7 +199,7 @@ def _bands_rows(ny, nx, periodic, Tb, sms):
     """The band cut the exchange kernel documents: one band when 32-row
     tiles over sms // (nx / 64) tile rows cover the plane, else near-equal
     owned ranges with Tb - 1 margin rows on each side toward a neighbour."""
-    ty_max = sms // (nx // 64)
+    ty_max = sms // -(-nx // 64)
     max_rows = ty_max * 32
     if ny <= max_rows:
         return 1, ny
@@ -214,10 +215,13 @@ def test_exchange_layout_reports_the_band_cut(stencil):
     heat3 = np.zeros(27)
     heat3[[4, 10, 12, 13, 14, 16, 22]] = [.1, .1, .1, .4, .1, .1, .1]
     for dims, bnd in [((4, 100, 64), 0), ((4, 100, 64), 1), ((3, 1024, 1024), 0), ((3, 1024, 1024), 1),
-                      ((2, 40, 64 * 152), 1), ((5, 7, 128), 1)]:
+                      ((2, 40, 64 * 152), 1), ((5, 7, 128), 1), ((4, 300, 1000), 0), ((4, 300, 1000), 1),
+                      ((4, 30, 99), 0)]:
         h = stencil.stencil_create(dims, 1, heat3, bnd)
         for Tb in (2, 4, 8):
-            if dims[2] // 64 > sms:
+            # nx even (a multiple of 64 when periodic), at most one 64-column tile column per SM
+            fits = dims[2] % 2 == 0 and (bnd == 0 or dims[2] % 64 == 0) and -(-dims[2] // 64) <= sms
+            if not fits:
                 with pytest.raises(stencil.StencilError) as ei:
                     stencil.stencil_exchange_layout(h, Tb)
                 assert ei.value.code == stencil.ERR_UNSUPPORTED

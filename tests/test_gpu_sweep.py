@@ -397,6 +397,11 @@ EXCHANGE_CASES = [
     ((12, 70, 4864), PERIODIC, "star_rand", 4, 12),  # 2 bands, each the other's neighbour twice
     ((7, 130, 4864), PERIODIC, "box_rand", 4, 9),    # 3 bands, box halo across the margins
     ((5, 300, 2432), DIRICHLET, "heat", 2, 6),       # 3 bands, one margin row each side
+    # nx not a multiple of 64 (Dirichlet): the last tile column is ragged
+    ((9, 70, 1000), DIRICHLET, "box_rand", 4, 9),
+    ((6, 33, 130), DIRICHLET, "star_rand", 2, 5),    # a last column of two cells
+    ((5, 300, 2400), DIRICHLET, "heat", 8, 17),      # ragged and cut into bands
+    ((3, 20, 2), DIRICHLET, "box_rand", 2, 4),       # one cell pair wide
 ]
 
 
@@ -416,10 +421,11 @@ def test_exchange_kernel_matches_single_steps_bitwise(st, shape, boundary, kind,
 
 def test_exchange_kernel_rejects_shapes_it_cannot_take(st):
     import torch
-    for shape, radius in (((9, 30, 100), 1), ((40, 128), 1), ((9, 30, 64), 2), ((3, 4, 64 * 160), 1)):
+    for shape, radius, bnd in (((9, 30, 100), 1, PERIODIC), ((40, 128), 1, PERIODIC), ((9, 30, 64), 2, PERIODIC),
+                               ((3, 4, 64 * 160), 1, PERIODIC), ((9, 30, 99), 1, DIRICHLET)):
         w = np.zeros((2 * radius + 1,) * len(shape))
         w[(radius,) * len(shape)] = 1.0
-        p = st.Plan(shape, radius, w, PERIODIC)
+        p = st.Plan(shape, radius, w, bnd)
         p.set_tuning(4, st.VARIANT_EXCHANGE)
         g = torch.zeros(shape, dtype=torch.float64, device="cuda")
         with pytest.raises(st.StencilError) as e:
@@ -440,7 +446,10 @@ def _random_exchange_cases(n, seed):
         nz = int(rng.integers(1, 14))
         Tb = int(rng.choice([2, 4, 8]))
         T = int(rng.integers(Tb, 3 * Tb + 2))
-        out.append(((nz, ny, nx), int(rng.integers(0, 2)), str(rng.choice(["star_rand", "box_rand"])), Tb, T))
+        bnd = int(rng.integers(0, 2))
+        if bnd == DIRICHLET and rng.integers(0, 2):
+            nx -= 2 * int(rng.integers(1, 32))  # a ragged last tile column
+        out.append(((nz, ny, nx), bnd, str(rng.choice(["star_rand", "box_rand"])), Tb, T))
     return out
 
 
@@ -547,7 +556,8 @@ def test_temporal_unsupported_tb_is_rejected(st):
 FIXED_TB_CASES = [
     # shape, radius, boundary, kind, Tb, T, the kernel the library picks
     ((24, 64, 128), 1, PERIODIC, "heat", 4, 9, "exchange"),
-    ((10, 20, 70), 1, DIRICHLET, "box_rand", 2, 5, "temporal"),     # nx off the 64-column tiles
+    ((10, 20, 70), 1, DIRICHLET, "box_rand", 2, 5, "exchange"),     # a ragged last tile column
+    ((10, 20, 70), 1, PERIODIC, "box_rand", 2, 5, "temporal"),      # periodic: nx off the 64-column tiles
     ((96, 96), 1, DIRICHLET, "heat", 8, 19, "persistent"),
     ((600, 520), 1, PERIODIC, "star_rand", 4, 10, "temporal"),
     ((5000,), 2, PERIODIC, "star_rand", 2, 7, "temporal"),
