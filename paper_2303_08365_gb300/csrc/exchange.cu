@@ -12,7 +12,10 @@
 //
 //   - one persistent CTA per tile of the (y, x) plane (64 columns by h rows,
 //     h near-equal over the tile rows, h <= 32), all CTAs co-resident
-//     (cooperative launch), each streaming its whole z column once;
+//     (cooperative launch), each streaming its whole z column once.  On a
+//     Dirichlet grid whose nx is not a multiple of 64 the last tile column is
+//     ragged: its lanes beyond nx read zeros (TMA out-of-bounds fill, the
+//     ghost value) and store nothing;
 //   - stage s = 1 .. Tb holds time level t+s.  In iteration i stage s computes
 //     plane q_s(i) = i + qoff - L(s-1) of its tile from planes q-1, q, q+1 of
 //     stage s-1 (the input grid for s = 1); stage s < Tb writes its plane to
