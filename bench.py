@@ -358,8 +358,11 @@ def headline(st, steps, warmup, world, stream):
     e2e_sampler = ClockSampler(uuid)
     e2e_sampler.start()
     t0 = time.perf_counter()
+    e2e_calls = []
     for _ in range(steps):
+        t1 = time.perf_counter()
         plan.run_host(host, T, stream=stream)
+        e2e_calls.append(round((time.perf_counter() - t1) * 1e3, 2))
     e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
     e2e_clocks = e2e_sampler.stop()
     e2e_ms = barrier_max(world, e2e_ms)
@@ -372,7 +375,7 @@ def headline(st, steps, warmup, world, stream):
     del grid
     torch.cuda.empty_cache()
     return dict(ms=ms / steps, launches=launches, clocks=clocks, e2e_ms=e2e_ms, e2e_clocks=e2e_clocks,
-                h2d=h2d, d2h=h2d, copy_gbs=copy_gbs,
+                h2d=h2d, d2h=h2d, copy_gbs=copy_gbs, e2e_calls=e2e_calls,
                 Tb=tb, variant=st.stencil_variant_name(variant), u0=u0, checks=checks)
 
 
@@ -988,7 +991,7 @@ def main():
         "fp64_peak_tflops_measured": round(peak_tflops, 4),
         "e2e": {"value": round(e2e_value, 4), "unit": "GStencil/s",
                 "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"],
-                "copy_gbs_pinned": h["copy_gbs"],
+                "copy_gbs_pinned": h["copy_gbs"], "ms_per_call": h["e2e_calls"],
                 "clocks": h["e2e_clocks"]},
         "gpu_launches": int(h["launches"]),
         "clocks": h["clocks"],
