@@ -66,6 +66,11 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.first = threading.Event()
+        self.start_line = 0
+
+    def mark(self):
+        """Count only the samples taken from now on (the timed region)."""
+        self.start_line = len(self.lines)
 
     def start(self):
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -101,7 +106,7 @@ class ClockSampler:
         self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.start_line:]:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -322,18 +327,21 @@ def headline(st, steps, warmup, world, stream):
     grid = torch.from_numpy(u0).cuda()
     plan = st.Plan(shape, 1, synth.heat_weights(3, HEADLINE["alpha"]), st.PERIODIC)
     tb, variant = plan.get_tuning()
-    for _ in range(warmup):
-        plan.run(grid, T, stream=stream)
-    torch.cuda.synchronize()
-    barrier(world)
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         uuid = None
+    # the clock sampler starts before the warm-ups (nvidia-smi's start-up
+    # idles the GPU for a moment); only the timed region's samples count
     sampler = ClockSampler(uuid)
     sampler.start()
+    for _ in range(warmup):
+        plan.run(grid, T, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.mark()
     l0 = st.stencil_launch_count()
     ms = cuda_time(lambda: [plan.run(grid, T, stream=stream) for _ in range(steps)], stream)
     launches = st.stencil_launch_count() - l0
@@ -346,17 +354,21 @@ def headline(st, steps, warmup, world, stream):
               "mean_drift_rel": abs(float(grid.mean()) - m0) / abs(m0),
               "within_initial_range": bool(float(grid.min()) >= float(u0.min()) and
                                            float(grid.max()) <= float(u0.max()))}
-    # end to end through the host-buffer entry point (pinned memory): one
-    # untimed call (the plan's staging buffer is allocated there), then
-    # `steps` timed calls, each copying the grid in, sweeping T steps and
-    # copying the result out
+    # end to end through the host-buffer entry point (pinned memory): the
+    # clock sampler first (the GPU idles while nvidia-smi starts, and a GPU
+    # that has idled runs the next seconds slower), then two untimed calls
+    # (the plan's staging buffer is allocated in the first) that bring it
+    # back to its steady state, then `steps` timed calls, each copying the
+    # grid in, sweeping T steps and copying the result out
     host = torch.from_numpy(u0).pin_memory()
     h2d = host.numel() * 8
-    plan.run_host(host, T, stream=stream)
-    torch.cuda.synchronize()
-    barrier(world)
     e2e_sampler = ClockSampler(uuid)
     e2e_sampler.start()
+    for _ in range(2):
+        plan.run_host(host, T, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_sampler.mark()
     t0 = time.perf_counter()
     e2e_calls = []
     for _ in range(steps):
